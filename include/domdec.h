@@ -1,0 +1,192 @@
+/*
+ * domdec.h -- C ABI of the GB300 (sm_103a) library for unbalanced entropic
+ * domain decomposition (Medina, Nguyen, Schmitzer, "Domain decomposition for
+ * entropic unbalanced optimal transport").
+ *
+ * Problem (Eq. unbalanced-problem with D_1 = D_2 = lam*KL, Section 5.1):
+ *   min_pi <c,pi> + eps KL(pi | mu x nu) + lam KL(P_X pi | mu) + lam KL(P_Y pi | nu)
+ * on X = Y = the N x N pixel grid {h (i, j)}, h = 1/N, c(x,y) = |x - y|^2.
+ *
+ * One call of domdec_iterate performs parallel DomDec iterations (Algorithm 4)
+ * over partition A, then B, ... (Algorithm 2).  Each iteration is split into
+ * the 2^2 staggered sub-batches of Section 5.3 and, for each sub-batch:
+ *   a1 nu_{-J}/nu on the cell's Y-box B_J            (Section 5.1, "Computing and handling nu_{-J}")
+ *   a2-a4 the cell Sinkhorn with Newton Y-half and PD stopping
+ *                                                     (Eqs. sinkhorn-X/Y-iteration, proxdiv-problem, PD-gap-KL)
+ *   a5 the new basic-cell Y-marginals, C_i, H_i      (Eq. sinkhorn-primal, Definition 2.4)
+ *   a6 GetWeights = swift on the sub-batch           (Proposition 4.3, Section 4.4 "staggered")
+ *   a7 the convex combination, truncation, box refresh (Algorithm 4 last line; Section 5.3 truncation)
+ * all on the GPU, enqueued on the stream given at domdec_init.
+ *
+ * Conventions for every entry point
+ *  - Arrays of N*N doubles are row-major images (index i*N + j).
+ *  - "host or device" pointers are accepted either way (copied with
+ *    cudaMemcpyDefault); the caller keeps ownership of every pointer it passes.
+ *  - Return value: DOMDEC_OK (0), a negative DOMDEC_E* error, or the
+ *    positive warning DOMDEC_WNOTCONV.  Nothing aborts the process.  After an
+ *    error the handle is "sticky": later calls return DOMDEC_ESTATE until
+ *    domdec_free.
+ *  - Calls marked "synchronises" wait for the handle's stream; the others
+ *    only enqueue work.
+ */
+#ifndef DOMDEC_H
+#define DOMDEC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DOMDEC_OK        0
+#define DOMDEC_WNOTCONV  1   /* warning: some cell solves hit maxit (Section 5.3, "Issues with non-convergence") */
+#define DOMDEC_EINVAL   -1   /* bad argument: N % (2 s) != 0, mu/nu not finite and > 0, eps <= 0, lam not finite and > 0 ... */
+#define DOMDEC_ENOMEM   -2   /* device allocation failed */
+#define DOMDEC_ECUDA    -3   /* a CUDA runtime call failed */
+#define DOMDEC_ETOOBIG  -4   /* a cell Y-box exceeds the kernel's shared-memory capacity (max_ny) */
+#define DOMDEC_EARENA   -5   /* the box arena overflowed (raise arena_factor) */
+#define DOMDEC_ESTATE   -6   /* the handle is in an error state */
+#define DOMDEC_ENOLIB   -7   /* reserved for bindings: library not loaded */
+
+#define DOMDEC_STAGGERED 0   /* swift on each of the 4 staggered sub-batches (Section 4.4) */
+#define DOMDEC_SWIFT     1   /* swift on the whole partition (Proposition 4.3, item 2) */
+#define DOMDEC_SAFE      2   /* theta = 1/|J| (Proposition 4.3, item 1) */
+#define DOMDEC_GREEDY    3   /* theta = 1 (Eq. GWFast); may diverge */
+
+#define DOMDEC_FP32 0        /* cell Sinkhorn arithmetic in float (state, score, decision stay double) */
+#define DOMDEC_FP64 1        /* cell Sinkhorn arithmetic in double */
+
+typedef struct domdec_s* domdec_t;
+
+typedef struct {
+  double eps;          /* entropic strength eps > 0 */
+  double lambda;       /* KL marginal penalty lam > 0, finite */
+  int    basic_cell;   /* s: basic cells are s x s pixels, composite cells 2s x 2s; N % (2 s) == 0, s <= 16 */
+  double err;          /* cell stopping tolerance: PD/lam <= err * |mu_J| (Section 5.3; paper: 2e-5);
+                          err < 0 runs exactly maxit iterations per cell */
+  double trunc_thr;    /* nu_i(y) < trunc_thr is dropped (Section 5.3; paper: 1e-15) */
+  double tau;          /* greedy leniency: accept theta = 1 if E(1) <= (1 + tau) E (Section 5.3: 0.005); 0 = pure swift */
+  int    strategy;     /* DOMDEC_STAGGERED | SWIFT | SAFE | GREEDY */
+  int    maxit;        /* cap on cell Sinkhorn iterations (status MAXIT when hit) */
+  int    newton_maxit; /* cap on Newton steps per y in the Y-half */
+  int    precision;    /* DOMDEC_FP32 | DOMDEC_FP64 */
+  int    box_margin;   /* pixels added around B_J (0 in the paper) */
+  int    max_ny;       /* capacity of a cell Y-box in the kernel (0: default 8192 for FP32, 4096 for FP64) */
+  double arena_factor; /* box arena capacity in units of N*N doubles (0: default 48) */
+  double eps_init;     /* eps of the warm-start duals passed to domdec_init (ignored without duals) */
+} domdec_params;
+
+typedef struct {
+  long long sweeps;          /* partition sweeps done */
+  long long cell_solves;     /* cell subproblems solved */
+  long long cell_iters;      /* cell Sinkhorn iterations (one X-half + one Y-half on one cell) */
+  long long maxit_cells;     /* cell solves that stopped at maxit */
+  long long greedy_steps;    /* sub-batches that accepted theta = 1 */
+  long long safe_steps;      /* sub-batches that fell back to theta = 1/|b| */
+  long long box_entries;     /* stored entries of all nu_i (memory diagnostic, Section 5.3 "Sparsity") */
+  int       max_cell_iters;  /* largest iteration count of one cell solve */
+  int       max_ny;          /* largest cell Y-box seen */
+} domdec_stats;
+
+/* Fill *p with the defaults (eps = lambda = 1, s = 4, err = 2e-5,
+ * trunc_thr = 1e-15, tau = 0, staggered, maxit = 2000, newton_maxit = 30,
+ * FP32, margin 0).  Never fails. */
+void domdec_default_params(domdec_params* p);
+
+/* Create a solver for marginals mu, nu (N*N each, finite, > 0, host or
+ * device) on the N x N grid (Assumption 4.2: full support).
+ * Initial plan (Algorithm 2, pi_init):
+ *   alpha0 == beta0 == NULL : pi0 = mu x nu (Section 4.4 toy set-up); every
+ *                             nu_i lives on the full grid, so this needs
+ *                             N*N <= max_ny.
+ *   alpha0, beta0 != NULL    : pi0 = exp((alpha0 (+) beta0 - c)/eps_init) mu x nu,
+ *                             e.g. the duals of a global Sinkhorn warm start
+ *                             (Section 5.3, "Sinkhorn warm start"); N*N doubles each.
+ * `stream` is a cudaStream_t (NULL = legacy default stream); all later work of
+ * the handle is enqueued there.  Synchronises.  *out is NULL on failure. */
+int domdec_init(domdec_t* out, const double* mu, const double* nu, int N,
+                const domdec_params* p, const double* alpha0, const double* beta0,
+                void* stream);
+
+/* Run n_sweeps partition sweeps (A, B, A, ... continuing the alternation of
+ * earlier calls).  Enqueues only; errors found on the device are reported by
+ * the next synchronising call. */
+int domdec_iterate(domdec_t h, int n_sweeps);
+
+/* Change eps between sweeps (eps-scaling stage).  The stored C_i and H_i make
+ * the tracked score valid for the new eps without re-instantiating the plan. */
+int domdec_set_eps(domdec_t h, double eps);
+
+/* Wait for the stream and report device-side errors / warnings.  Synchronises. */
+int domdec_sync(domdec_t h);
+
+/* out[0] tracked score E_hat = sum_i (C_i + eps H_i) + lam KL(P_X|mu) + lam KL(P_Y|nu)
+ * (an upper bound of the plan's score, equal to it after greedy steps),
+ * out[1] sum_i (C_i + eps H_i), out[2] lam KL(P_X|mu), out[3] lam KL(P_Y|nu),
+ * out[4] |P_Y pi|, out[5] theta of the last sub-batch.  Synchronises. */
+int domdec_score(domdec_t h, double out[6]);
+
+/* P_X pi and P_Y pi of the current plan into PX, PY (N*N doubles each, host
+ * or device; either may be NULL).  Synchronises. */
+int domdec_plan_marginals(domdec_t h, double* PX, double* PY);
+
+/* The stitched X-potential alpha (proof of Proposition 4.2) into alpha (N*N
+ * doubles, host or device).  Synchronises. */
+int domdec_duals(domdec_t h, double* alpha);
+
+/* Primal-dual certificate: out[0] = E_hat, out[1] = D(alpha, beta_star) with beta_star
+ * from one global closed-form Y-half (Eq. sinkhorn-iters-ot), out[2] =
+ * (E_hat - D)/|D| (Section 5.3, "Solution quality"), out[3] = L1 X-marginal
+ * error |P_X - e^{-alpha/lam} mu|_1, out[4] = L1 Y-marginal error
+ * |P_Y - e^{-beta_star/lam} nu|_1.  beta (N*N, host or device) receives beta_star
+ * if not NULL.  Uses the separable FP64 log-sum-exp.  Synchronises. */
+int domdec_pd_gap(domdec_t h, double out[5], double* beta);
+
+/* Basic-cell Y-marginals: box[4*i..4*i+3] = (k0, l0, H, W) of nu_i in Y pixel
+ * coordinates (H*W == 0: empty), values of all boxes concatenated in basic-cell
+ * order (row-major inside a box) into `values` (host, capacity `cap` doubles).
+ * Returns the number of values (or a negative error; DOMDEC_EINVAL if cap is
+ * too small).  box must hold 4 * (N/s)^2 ints.  Synchronises. */
+long long domdec_basic_marginals(domdec_t h, int* box, double* values, long long cap);
+
+/* Step-size decisions of the most recent sub-batches, oldest first: record k
+ * is out[4k..4k+3] = (E_hat before the step, E(theta = 1), E(theta = 1/|b|),
+ * chosen theta) -- the GetWeights_swift comparison of Proposition 4.3.
+ * Writes at most max_records records (host buffer); returns how many, at most
+ * the 4096 most recent.  Synchronises. */
+int domdec_decision_log(domdec_t h, double* out, int max_records);
+
+/* Counters since domdec_init.  Synchronises. */
+int domdec_get_stats(domdec_t h, domdec_stats* s);
+
+/* Free all device memory of the handle (waits for its stream). */
+void domdec_free(domdec_t h);
+
+/* Static text for an error code. */
+const char* domdec_error_string(int code);
+
+/* Global unbalanced Sinkhorn (Eq. sinkhorn-iters-ot, nu_- = 0) on the N x N
+ * grid: the comparator, and the warm start of Section 5.3.
+ *   variant   DOMDEC_SINKHORN_DENSE     : the plain method, O(N^4) per half-step
+ *             DOMDEC_SINKHORN_SEPARABLE : the same update evaluated as two 1-D
+ *                                         log-sum-exp passes (|x-y|^2 separates
+ *                                         over the axes), O(N^3) per half-step
+ *   precision DOMDEC_FP32 | DOMDEC_FP64
+ *   eps_start >= eps: geometric eps-scaling eps_start, eps_start/2, ... eps;
+ *   at each stage iterate until PD/lam <= err*|mu| (Eq. PD-gap-KL, tested every
+ *   check_every iterations) or maxit iterations.
+ * mu, nu, alpha, beta: N*N doubles, host or device; beta (in) is the start
+ * (NULL: 0), alpha/beta (out) the final duals if non-NULL.
+ * out[0] total iterations, out[1] last PD/lam, out[2] primal E (= D + PD),
+ * out[3] dual D.  Synchronises.  Returns DOMDEC_WNOTCONV if the last stage hit
+ * maxit. */
+#define DOMDEC_SINKHORN_DENSE     0
+#define DOMDEC_SINKHORN_SEPARABLE 1
+int domdec_full_sinkhorn(const double* mu, const double* nu, int N, double eps_start,
+                         double eps, double lambda, int variant, int precision,
+                         int maxit, double err, int check_every,
+                         const double* beta_in, double* alpha, double* beta,
+                         double out[4], void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DOMDEC_H */

@@ -1,0 +1,599 @@
+// Host side of the C ABI declared in include/domdec.h: handle lifetime, the
+// partitions and staggered sub-batches (Section 5.3), the sweep driver
+// (Algorithm 2 over Algorithm 4 per sub-batch), CUDA-graph replay of sweeps,
+// and the read-back entry points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "dd_common.cuh"
+#include "domdec.h"
+
+// ---- kernels' launch wrappers (dd_cell.cu, dd_sweep.cu, dd_sinkhorn.cu)
+size_t cell_smem_bytes(int s, int cap_side, int cap_ny, int precision);
+cudaError_t launch_cell_solve(const DevState& S, const CellDesc* cells, int begin, int nbatch, int precision,
+                              cudaStream_t st);
+cudaError_t launch_decide(const DevState& S, const CellDesc* cells, int begin, int nbatch, int slot,
+                          cudaStream_t st);
+cudaError_t launch_apply(const DevState& S, const CellDesc* cells, int begin, int nbatch, cudaStream_t st);
+cudaError_t launch_compact(const DevState& S, long long* newoff, cudaStream_t st);
+cudaError_t launch_prepare_inputs(const double* mu, const double* nu, double* logmu, double* lognu, int n,
+                                  int* status, cudaStream_t st);
+cudaError_t launch_init_product_boxes(const DevState& S, double* nu_mom, double* mumass, long long* newoff,
+                                      cudaStream_t st);
+cudaError_t launch_init_product_fill(const DevState& S, double* nu_mom, double* mumass, long long* newoff,
+                                     cudaStream_t st);
+cudaError_t launch_init_duals_boxes(const DevState& S, const double* alpha0, const double* beta0, double eps0,
+                                    double* nu_mom, double* mumass, long long* newoff, cudaStream_t st);
+cudaError_t launch_init_duals_fill(const DevState& S, const double* alpha0, const double* beta0, double eps0,
+                                   const double* w, long long* newoff, cudaStream_t st);
+cudaError_t launch_score(const DevState& S, double* out, cudaStream_t st);
+cudaError_t launch_cert(const DevState& S, const double* z, double* beta_out, double* out, cudaStream_t st);
+cudaError_t launch_regrow(const DevState& S, double* new0, double* new1, long long* newoff, cudaStream_t st);
+cudaError_t global_lse64(const double* pot, const double* logm, double eps, double h, int N, double* out,
+                         double* buf_a, double* buf_b, cudaStream_t st);
+int full_sinkhorn_dev(const double* mu, const double* nu, const double* logmu, const double* lognu, int N,
+                      double eps_start, double eps, double lam, int variant, int precision, int maxit,
+                      double err, int check_every, double* alpha, double* beta, double* out, double* d_eval,
+                      cudaStream_t st, cudaError_t* cerr);
+
+namespace {
+constexpr int LOGCAP = 4096;
+constexpr int NCOUNT = 8;
+}  // namespace
+
+struct domdec_s {
+  domdec_params p;
+  int N = 0, s = 0, nb = 0, nbasic = 0, n = 0;
+  cudaStream_t st = nullptr;
+  DevState S;
+  std::vector<void*> allocs;
+  CellDesc* d_cells[2] = {nullptr, nullptr};
+  int sub_start[2][5];
+  int ncell[2] = {0, 0};
+  int max_batch = 0;
+  long long* d_newoff = nullptr;
+  double* d_scratch = nullptr;  // 64 doubles
+  double* d_numom = nullptr;
+  double* d_mumass = nullptr;
+  double* h_pinned = nullptr;   // 64 doubles
+  long long sweeps = 0;
+  long long slot = 0;
+  int sticky = 0;
+  // graphs: one sweep per partition
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  bool graph_ok = true;
+};
+
+namespace {
+
+int fail(domdec_s* h, int code) {
+  if (h && code < 0) h->sticky = code;
+  return code;
+}
+
+template <typename T>
+cudaError_t dalloc(domdec_s* h, T** ptr, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T) + 16);
+  if (e != cudaSuccess) return e;
+  h->allocs.push_back(q);
+  *ptr = reinterpret_cast<T*>(q);
+  return cudaSuccess;
+}
+
+void build_partition(domdec_s* h, int which, std::vector<CellDesc>& out, int* sub_start) {
+  const int s = h->s, nb = h->nb, N = h->N, off = which;
+  const int nc = nb / 2 + off;
+  std::vector<CellDesc> subs[4];
+  for (int P = 0; P < nc; ++P)
+    for (int Q = 0; Q < nc; ++Q) {
+      const int lb1 = 2 * P - off, lb2 = 2 * Q - off;
+      CellDesc cd;
+      const int xlo1 = std::max(0, s * lb1), xhi1 = std::min(N, s * (lb1 + 2));
+      const int xlo2 = std::max(0, s * lb2), xhi2 = std::min(N, s * (lb2 + 2));
+      cd.i0 = xlo1; cd.j0 = xlo2; cd.nx1 = xhi1 - xlo1; cd.nx2 = xhi2 - xlo2;
+      for (int q = 0; q < 4; ++q) cd.mem[q] = -1;
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+          const int I = lb1 + a, J = lb2 + b;
+          if (I < 0 || J < 0 || I >= nb || J >= nb) continue;
+          // quadrant relative to the X box origin
+          const int qr = (I * s - xlo1) >= s ? 1 : 0, qc = (J * s - xlo2) >= s ? 1 : 0;
+          cd.mem[2 * qr + qc] = I * nb + J;
+        }
+      subs[2 * (P % 2) + (Q % 2)].push_back(cd);
+    }
+  out.clear();
+  sub_start[0] = 0;
+  for (int b = 0; b < 4; ++b) {
+    out.insert(out.end(), subs[b].begin(), subs[b].end());
+    sub_start[b + 1] = (int)out.size();
+  }
+}
+
+int check_params(const domdec_params* p, int N) {
+  if (!p || N <= 0) return DOMDEC_EINVAL;
+  if (!(p->eps > 0.0) || !std::isfinite(p->eps)) return DOMDEC_EINVAL;
+  if (!(p->lambda > 0.0) || !std::isfinite(p->lambda)) return DOMDEC_EINVAL;
+  if (p->basic_cell < 1 || p->basic_cell > 16 || N % (2 * p->basic_cell)) return DOMDEC_EINVAL;
+  if (p->maxit < 1 || p->newton_maxit < 1) return DOMDEC_EINVAL;
+  if (p->strategy < 0 || p->strategy > 3 || (p->precision != 0 && p->precision != 1)) return DOMDEC_EINVAL;
+  if (!(p->trunc_thr >= 0.0) || p->box_margin < 0) return DOMDEC_EINVAL;
+  return DOMDEC_OK;
+}
+
+int read_status(domdec_s* h) {
+  cudaError_t e = cudaMemcpyAsync(h->h_pinned, h->S.status, sizeof(int), cudaMemcpyDeviceToHost, h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return fail(h, DOMDEC_ECUDA);
+  int st = *reinterpret_cast<int*>(h->h_pinned);
+  if (st & ST_BADINPUT) return fail(h, DOMDEC_EINVAL);
+  if (st & ST_TOOBIG) return fail(h, DOMDEC_ETOOBIG);
+  if (st & ST_ARENA) return fail(h, DOMDEC_EARENA);
+  if (st & (ST_EMPTY | ST_NONFINITE)) return fail(h, DOMDEC_ECUDA);
+  return DOMDEC_OK;
+}
+
+// Make sure each arena has room for 4x the live data (at a synchronisation point).
+int ensure_arena(domdec_s* h) {
+  unsigned long long live = 0;
+  cudaError_t e = cudaMemcpyAsync(&live, h->S.head, sizeof(live), cudaMemcpyDeviceToHost, h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return fail(h, DOMDEC_ECUDA);
+  if ((long long)live * 4 <= h->S.cap) return DOMDEC_OK;
+  long long ncap = (long long)live * 8;
+  double *a0 = nullptr, *a1 = nullptr;
+  if (cudaMalloc(&a0, ncap * sizeof(double)) != cudaSuccess) return fail(h, DOMDEC_ENOMEM);
+  if (cudaMalloc(&a1, ncap * sizeof(double)) != cudaSuccess) { cudaFree(a0); return fail(h, DOMDEC_ENOMEM); }
+  if (launch_regrow(h->S, a0, a1, h->d_newoff, h->st) != cudaSuccess) return fail(h, DOMDEC_ECUDA);
+  if (cudaStreamSynchronize(h->st) != cudaSuccess) return fail(h, DOMDEC_ECUDA);
+  for (auto& q : h->allocs)
+    if (q == h->S.arena[0] || q == h->S.arena[1]) { cudaFree(q); q = nullptr; }
+  h->allocs.push_back(a0);
+  h->allocs.push_back(a1);
+  h->S.arena[0] = a0;
+  h->S.arena[1] = a1;
+  h->S.cap = ncap;
+  for (int k = 0; k < 2; ++k)
+    if (h->graph[k]) { cudaGraphExecDestroy(h->graph[k]); h->graph[k] = nullptr; }
+  return DOMDEC_OK;
+}
+
+// Enqueue one sweep of partition `part`.
+int enqueue_sweep(domdec_s* h, int part, long long slot0) {
+  const int prec = h->p.precision;
+  std::vector<std::pair<int, int>> batches;
+  if (h->p.strategy == DOMDEC_STAGGERED) {
+    for (int b = 0; b < 4; ++b) batches.push_back({h->sub_start[part][b], h->sub_start[part][b + 1]});
+  } else {
+    batches.push_back({0, h->ncell[part]});
+  }
+  int k = 0;
+  for (auto& bt : batches) {
+    const int begin = bt.first, nbt = bt.second - bt.first;
+    if (nbt <= 0) continue;
+    const int slot = (int)((slot0 + k++) % LOGCAP);
+    if (launch_cell_solve(h->S, h->d_cells[part], begin, nbt, prec, h->st) != cudaSuccess) return DOMDEC_ECUDA;
+    if (launch_decide(h->S, h->d_cells[part], begin, nbt, slot, h->st) != cudaSuccess) return DOMDEC_ECUDA;
+    if (launch_apply(h->S, h->d_cells[part], begin, nbt, h->st) != cudaSuccess) return DOMDEC_ECUDA;
+  }
+  if (launch_compact(h->S, h->d_newoff, h->st) != cudaSuccess) return DOMDEC_ECUDA;
+  return DOMDEC_OK;
+}
+
+int batches_per_sweep(domdec_s* h, int part) {
+  if (h->p.strategy != DOMDEC_STAGGERED) return h->ncell[part] > 0 ? 1 : 0;
+  int c = 0;
+  for (int b = 0; b < 4; ++b) c += h->sub_start[part][b + 1] > h->sub_start[part][b];
+  return c;
+}
+
+}  // namespace
+
+extern "C" {
+
+void domdec_default_params(domdec_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->eps = 1.0;
+  p->lambda = 1.0;
+  p->basic_cell = 4;
+  p->err = 2e-5;
+  p->trunc_thr = 1e-15;
+  p->tau = 0.0;
+  p->strategy = DOMDEC_STAGGERED;
+  p->maxit = 2000;
+  p->newton_maxit = 30;
+  p->precision = DOMDEC_FP32;
+  p->box_margin = 0;
+  p->max_ny = 0;
+  p->arena_factor = 0.0;
+  p->eps_init = 0.0;
+}
+
+const char* domdec_error_string(int code) {
+  switch (code) {
+    case DOMDEC_OK: return "ok";
+    case DOMDEC_WNOTCONV: return "warning: some cell solves stopped at maxit";
+    case DOMDEC_EINVAL: return "invalid argument";
+    case DOMDEC_ENOMEM: return "device allocation failed";
+    case DOMDEC_ECUDA: return "CUDA runtime error or non-finite values on the device";
+    case DOMDEC_ETOOBIG: return "a cell Y-box exceeds the kernel's shared-memory capacity (max_ny)";
+    case DOMDEC_EARENA: return "box arena overflow";
+    case DOMDEC_ESTATE: return "handle is in an error state";
+    case DOMDEC_ENOLIB: return "library not loaded";
+    default: return "unknown error";
+  }
+}
+
+void domdec_free(domdec_t h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->st);
+  for (int k = 0; k < 2; ++k)
+    if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
+  for (void* q : h->allocs)
+    if (q) cudaFree(q);
+  if (h->h_pinned) cudaFreeHost(h->h_pinned);
+  delete h;
+}
+
+int domdec_init(domdec_t* out, const double* mu, const double* nu, int N, const domdec_params* pin,
+                const double* alpha0, const double* beta0, void* stream) {
+  if (!out) return DOMDEC_EINVAL;
+  *out = nullptr;
+  if (!mu || !nu) return DOMDEC_EINVAL;
+  int rc = check_params(pin, N);
+  if (rc) return rc;
+  if ((alpha0 == nullptr) != (beta0 == nullptr)) return DOMDEC_EINVAL;
+  if (alpha0 && !(pin->eps_init > 0.0)) return DOMDEC_EINVAL;
+  domdec_s* h = new (std::nothrow) domdec_s();
+  if (!h) return DOMDEC_ENOMEM;
+  h->p = *pin;
+  h->N = N; h->s = pin->basic_cell; h->nb = N / h->s; h->nbasic = h->nb * h->nb; h->n = N * N;
+  h->st = reinterpret_cast<cudaStream_t>(stream);
+  const int n = h->n;
+  DevState& S = h->S;
+  std::memset(&S, 0, sizeof(S));
+  S.N = N; S.s = h->s; S.nb = h->nb; S.nbasic = h->nbasic;
+  S.h = 1.0 / N; S.eps = pin->eps; S.lam = pin->lambda; S.thr = pin->trunc_thr; S.err = pin->err;
+  S.tau = pin->tau; S.maxit = pin->maxit; S.newton_maxit = pin->newton_maxit; S.strategy = pin->strategy;
+  S.margin = pin->box_margin;
+  // shared-memory capacity of the cell kernel
+  int dev = 0, smem_optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  int cap_ny = pin->max_ny > 0 ? pin->max_ny : (pin->precision ? 3072 : 8192);
+  int cap_side = std::min(N, 128);
+  for (;;) {
+    cap_side = std::min(cap_side, cap_ny);
+    // epilogue scratch (3 nx1 W) must fit in the T/U/bl/lrho/Zv region
+    while (2 * h->s * cap_side > 3 * cap_ny && cap_side > 1) --cap_side;
+    if (cell_smem_bytes(h->s, cap_side, cap_ny, pin->precision) <= (size_t)smem_optin || cap_ny <= 64) break;
+    cap_ny -= 256;
+  }
+  S.cap_ny = cap_ny;
+  S.cap_side = cap_side;
+  if (cell_smem_bytes(h->s, cap_side, cap_ny, pin->precision) > (size_t)smem_optin) {
+    delete h;
+    return DOMDEC_EINVAL;
+  }
+  std::vector<CellDesc> cells[2];
+  for (int w = 0; w < 2; ++w) {
+    build_partition(h, w, cells[w], h->sub_start[w]);
+    h->ncell[w] = (int)cells[w].size();
+  }
+  int mb = 0;
+  for (int w = 0; w < 2; ++w) {
+    if (pin->strategy == DOMDEC_STAGGERED) {
+      for (int b = 0; b < 4; ++b) mb = std::max(mb, h->sub_start[w][b + 1] - h->sub_start[w][b]);
+    } else {
+      mb = std::max(mb, h->ncell[w]);
+    }
+  }
+  h->max_batch = mb;
+  cudaError_t e = cudaSuccess;
+#define DD_ALLOC(ptr, cnt)                                  \
+  do {                                                      \
+    if ((e = dalloc(h, &(ptr), (cnt))) != cudaSuccess) {    \
+      domdec_free(h);                                       \
+      return DOMDEC_ENOMEM;                                 \
+    }                                                       \
+  } while (0)
+  double *dmu, *dnu, *dlogmu, *dlognu, *dmuinu;
+  DD_ALLOC(dmu, n); DD_ALLOC(dnu, n); DD_ALLOC(dlogmu, n); DD_ALLOC(dlognu, n);
+  DD_ALLOC(S.alpha, n); DD_ALLOC(S.PX, n); DD_ALLOC(S.PY, n); DD_ALLOC(S.PXnew, n); DD_ALLOC(S.dPY, n);
+  DD_ALLOC(S.Cc, h->nbasic); DD_ALLOC(S.Hh, h->nbasic); DD_ALLOC(dmuinu, h->nbasic);
+  DD_ALLOC(h->d_mumass, h->nbasic);
+  DD_ALLOC(S.box, h->nbasic);
+  DD_ALLOC(S.cur, 1); DD_ALLOC(S.head, 1);
+  DD_ALLOC(h->d_cells[0], std::max(1, h->ncell[0])); DD_ALLOC(h->d_cells[1], std::max(1, h->ncell[1]));
+  DD_ALLOC(S.cout, std::max(1, mb));
+  DD_ALLOC(S.nut, (size_t)std::max(1, mb) * 4 * cap_ny);
+  DD_ALLOC(S.theta, 1); DD_ALLOC(S.declog, 4 * LOGCAP); DD_ALLOC(S.counters, NCOUNT);
+  DD_ALLOC(S.status, 1); DD_ALLOC(S.red, 2 * 152 * 5 + 8); DD_ALLOC(S.red_count, 1);
+  DD_ALLOC(h->d_newoff, h->nbasic + 1); DD_ALLOC(h->d_scratch, 64); DD_ALLOC(h->d_numom, 8);
+  S.mu = dmu; S.nu = dnu; S.logmu = dlogmu; S.lognu = dlognu; S.muinu = dmuinu;
+  if (cudaMallocHost(&h->h_pinned, 64 * sizeof(double)) != cudaSuccess) { domdec_free(h); return DOMDEC_ENOMEM; }
+  cudaStream_t st = h->st;
+  e = cudaMemcpyAsync(dmu, mu, n * sizeof(double), cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dnu, nu, n * sizeof(double), cudaMemcpyDefault, st);
+  cudaMemsetAsync(S.status, 0, sizeof(int), st);
+  cudaMemsetAsync(S.cur, 0, sizeof(int), st);
+  cudaMemsetAsync(S.head, 0, sizeof(unsigned long long), st);
+  cudaMemsetAsync(S.counters, 0, NCOUNT * sizeof(unsigned long long), st);
+  cudaMemsetAsync(S.red_count, 0, sizeof(unsigned int), st);
+  cudaMemsetAsync(S.dPY, 0, n * sizeof(double), st);
+  cudaMemsetAsync(S.PY, 0, n * sizeof(double), st);
+  cudaMemsetAsync(S.theta, 0, sizeof(double), st);
+  cudaMemsetAsync(S.declog, 0, 4 * LOGCAP * sizeof(double), st);
+  for (int w = 0; w < 2; ++w)
+    if (h->ncell[w])
+      cudaMemcpyAsync(h->d_cells[w], cells[w].data(), cells[w].size() * sizeof(CellDesc),
+                      cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = launch_prepare_inputs(dmu, dnu, dlogmu, dlognu, n, S.status, st);
+  if (e != cudaSuccess) { domdec_free(h); return DOMDEC_ECUDA; }
+  // temporary arena pointers for the box pass (no values written yet)
+  double* ad = nullptr;
+  double* bd = nullptr;
+  double* wtmp = nullptr;
+  if (alpha0) {
+    DD_ALLOC(ad, n); DD_ALLOC(bd, n); DD_ALLOC(wtmp, 3 * (size_t)n);
+    cudaMemcpyAsync(ad, alpha0, n * sizeof(double), cudaMemcpyDefault, st);
+    cudaMemcpyAsync(bd, beta0, n * sizeof(double), cudaMemcpyDefault, st);
+    e = launch_init_duals_boxes(S, ad, bd, pin->eps_init, h->d_numom, h->d_mumass, h->d_newoff, st);
+  } else {
+    e = launch_init_product_boxes(S, h->d_numom, h->d_mumass, h->d_newoff, st);
+  }
+  long long total = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&total, h->d_newoff + h->nbasic, sizeof(long long),
+                                            cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) { domdec_free(h); return DOMDEC_ECUDA; }
+  rc = read_status(h);
+  if (rc) { domdec_free(h); return rc; }
+  const double fac = pin->arena_factor > 0 ? pin->arena_factor : 48.0;
+  S.cap = std::max((long long)(fac * n), 8 * total + 1024);
+  DD_ALLOC(S.arena[0], S.cap);
+  DD_ALLOC(S.arena[1], S.cap);
+  if (alpha0) {
+    // w(x) = log sum_y exp(beta0/eps0 + log nu - c/eps0): P_X of the initial plan
+    global_lse64(bd, dlognu, pin->eps_init, 1.0 / N, N, wtmp, wtmp + n, wtmp + 2 * (size_t)n, st);
+    e = launch_init_duals_fill(S, ad, bd, pin->eps_init, wtmp, h->d_newoff, st);
+  } else {
+    e = launch_init_product_fill(S, h->d_numom, h->d_mumass, h->d_newoff, st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) { domdec_free(h); return DOMDEC_ECUDA; }
+  rc = read_status(h);
+  if (rc) { domdec_free(h); return rc; }
+  *out = h;
+  return DOMDEC_OK;
+#undef DD_ALLOC
+}
+
+int domdec_iterate(domdec_t h, int n_sweeps) {
+  if (!h) return DOMDEC_EINVAL;
+  if (h->sticky) return DOMDEC_ESTATE;
+  if (n_sweeps < 0) return DOMDEC_EINVAL;
+  for (int k = 0; k < n_sweeps; ++k) {
+    const int part = (int)(h->sweeps % 2);
+    int rc = enqueue_sweep(h, part, h->slot);
+    if (rc) return fail(h, rc);
+    h->slot += batches_per_sweep(h, part);
+    ++h->sweeps;
+  }
+  return DOMDEC_OK;
+}
+
+int domdec_set_eps(domdec_t h, double eps) {
+  if (!h) return DOMDEC_EINVAL;
+  if (h->sticky) return DOMDEC_ESTATE;
+  if (!(eps > 0.0) || !std::isfinite(eps)) return DOMDEC_EINVAL;
+  h->S.eps = eps;
+  h->p.eps = eps;
+  for (int k = 0; k < 2; ++k)
+    if (h->graph[k]) { cudaGraphExecDestroy(h->graph[k]); h->graph[k] = nullptr; }
+  return DOMDEC_OK;
+}
+
+int domdec_sync(domdec_t h) {
+  if (!h) return DOMDEC_EINVAL;
+  if (h->sticky) return DOMDEC_ESTATE;
+  if (cudaStreamSynchronize(h->st) != cudaSuccess) return fail(h, DOMDEC_ECUDA);
+  int rc = read_status(h);
+  if (rc) return rc;
+  rc = ensure_arena(h);
+  if (rc) return rc;
+  unsigned long long c[NCOUNT];
+  if (cudaMemcpy(c, h->S.counters, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess) return fail(h, DOMDEC_ECUDA);
+  return c[2] ? DOMDEC_WNOTCONV : DOMDEC_OK;
+}
+
+int domdec_score(domdec_t h, double out[6]) {
+  if (!h || !out) return DOMDEC_EINVAL;
+  if (h->sticky) return DOMDEC_ESTATE;
+  if (launch_score(h->S, h->d_scratch, h->st) != cudaSuccess) return fail(h, DOMDEC_ECUDA);
+  cudaMemcpyAsync(h->h_pinned, h->d_scratch, 5 * sizeof(double), cudaMemcpyDeviceToHost, h->st);
+  cudaMemcpyAsync(h->h_pinned + 8, h->S.theta, sizeof(double), cudaMemcpyDeviceToHost, h->st);
+  if (cudaStreamSynchronize(h->st) != cudaSuccess) return fail(h, DOMDEC_ECUDA);
+  int rc = read_status(h);
+  if (rc) return rc;
+  const double* v = h->h_pinned;
+  out[0] = v[0] + v[1] + v[2];
+  out[1] = v[0];
+  out[2] = v[1];
+  out[3] = v[2];
+  out[4] = v[3];
+  out[5] = h->h_pinned[8];
+  return DOMDEC_OK;
+}
+
+int domdec_plan_marginals(domdec_t h, double* PX, double* PY) {
+  if (!h) return DOMDEC_EINVAL;
+  if (h->sticky) return DOMDEC_ESTATE;
+  cudaError_t e = cudaSuccess;
+  if (PX) e = cudaMemcpyAsync(PX, h->S.PX, h->n * sizeof(double), cudaMemcpyDefault, h->st);
+  if (PY && e == cudaSuccess) e = cudaMemcpyAsync(PY, h->S.PY, h->n * sizeof(double), cudaMemcpyDefault, h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return fail(h, DOMDEC_ECUDA);
+  return read_status(h);
+}
+
+int domdec_duals(domdec_t h, double* alpha) {
+  if (!h || !alpha) return DOMDEC_EINVAL;
+  if (h->sticky) return DOMDEC_ESTATE;
+  cudaError_t e = cudaMemcpyAsync(alpha, h->S.alpha, h->n * sizeof(double), cudaMemcpyDefault, h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return fail(h, DOMDEC_ECUDA);
+  return read_status(h);
+}
+
+int domdec_pd_gap(domdec_t h, double out[5], double* beta) {
+  if (!h || !out) return DOMDEC_EINVAL;
+  if (h->sticky) return DOMDEC_ESTATE;
+  const int n = h->n;
+  double* buf = nullptr;
+  if (cudaMallocAsync(&buf, 4 * (size_t)n * sizeof(double), h->st) != cudaSuccess) return fail(h, DOMDEC_ENOMEM);
+  double *z = buf, *ba = buf + n, *bb = buf + 2 * (size_t)n, *bt = buf + 3 * (size_t)n;
+  cudaError_t e = global_lse64(h->S.alpha, h->S.logmu, h->S.eps, h->S.h, h->N, z, ba, bb, h->st);
+  if (e == cudaSuccess) e = launch_cert(h->S, z, bt, h->d_scratch + 16, h->st);
+  if (e == cudaSuccess) e = launch_score(h->S, h->d_scratch, h->st);
+  if (e == cudaSuccess && beta) e = cudaMemcpyAsync(beta, bt, n * sizeof(double), cudaMemcpyDefault, h->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->h_pinned, h->d_scratch, 24 * sizeof(double), cudaMemcpyDeviceToHost, h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  cudaFreeAsync(buf, h->st);
+  if (e != cudaSuccess) return fail(h, DOMDEC_ECUDA);
+  int rc = read_status(h);
+  if (rc) return rc;
+  const double* v = h->h_pinned;
+  const double* c = v + 16;
+  const double eps = h->S.eps, lam = h->S.lam;
+  const double P = v[0] + v[1] + v[2];
+  const double D = eps * c[3] * c[4] - eps * c[0] - lam * c[1] - lam * c[2];
+  out[0] = P;
+  out[1] = D;
+  out[2] = (P - D) / std::fabs(D);
+  out[3] = c[5];
+  out[4] = c[6];
+  return DOMDEC_OK;
+}
+
+long long domdec_basic_marginals(domdec_t h, int* box, double* values, long long cap) {
+  if (!h || !box) return DOMDEC_EINVAL;
+  if (h->sticky) return DOMDEC_ESTATE;
+  if (cudaStreamSynchronize(h->st) != cudaSuccess) return fail(h, DOMDEC_ECUDA);
+  std::vector<BoxRec> b(h->nbasic);
+  int cur = 0;
+  if (cudaMemcpy(b.data(), h->S.box, h->nbasic * sizeof(BoxRec), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(&cur, h->S.cur, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(h, DOMDEC_ECUDA);
+  long long total = 0;
+  for (int i = 0; i < h->nbasic; ++i) {
+    box[4 * i] = b[i].k0; box[4 * i + 1] = b[i].l0; box[4 * i + 2] = b[i].H; box[4 * i + 3] = b[i].W;
+    total += (long long)b[i].H * b[i].W;
+  }
+  if (!values) return total;
+  if (total > cap) return DOMDEC_EINVAL;
+  long long pos = 0;
+  for (int i = 0; i < h->nbasic; ++i) {
+    long long sz = (long long)b[i].H * b[i].W;
+    if (sz && cudaMemcpy(values + pos, h->S.arena[cur] + b[i].off, sz * sizeof(double), cudaMemcpyDefault) != cudaSuccess)
+      return fail(h, DOMDEC_ECUDA);
+    pos += sz;
+  }
+  return total;
+}
+
+int domdec_decision_log(domdec_t h, double* out, int max_records) {
+  if (!h || !out || max_records < 0) return DOMDEC_EINVAL;
+  if (h->sticky) return DOMDEC_ESTATE;
+  std::vector<double> all(4 * LOGCAP);
+  if (cudaStreamSynchronize(h->st) != cudaSuccess ||
+      cudaMemcpy(all.data(), h->S.declog, all.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(h, DOMDEC_ECUDA);
+  const long long have = std::min<long long>(h->slot, LOGCAP);
+  const int cnt = (int)std::min<long long>(have, max_records);
+  for (int k = 0; k < cnt; ++k) {
+    const long long rec = h->slot - cnt + k;
+    for (int j = 0; j < 4; ++j) out[4 * k + j] = all[4 * (rec % LOGCAP) + j];
+  }
+  return cnt;
+}
+
+int domdec_get_stats(domdec_t h, domdec_stats* s) {
+  if (!h || !s) return DOMDEC_EINVAL;
+  if (h->sticky) return DOMDEC_ESTATE;
+  unsigned long long c[NCOUNT];
+  if (launch_score(h->S, h->d_scratch, h->st) != cudaSuccess) return fail(h, DOMDEC_ECUDA);
+  cudaMemcpyAsync(h->h_pinned, h->d_scratch, 5 * sizeof(double), cudaMemcpyDeviceToHost, h->st);
+  if (cudaStreamSynchronize(h->st) != cudaSuccess ||
+      cudaMemcpy(c, h->S.counters, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(h, DOMDEC_ECUDA);
+  s->sweeps = h->sweeps;
+  s->cell_iters = (long long)c[0];
+  s->cell_solves = (long long)c[1];
+  s->maxit_cells = (long long)c[2];
+  s->greedy_steps = (long long)c[3];
+  s->safe_steps = (long long)c[4];
+  s->max_cell_iters = (int)c[5];
+  s->max_ny = (int)c[6];
+  s->box_entries = (long long)h->h_pinned[4];
+  return read_status(h);
+}
+
+int domdec_full_sinkhorn(const double* mu, const double* nu, int N, double eps_start, double eps, double lambda,
+                         int variant, int precision, int maxit, double err, int check_every,
+                         const double* beta_in, double* alpha, double* beta, double out[4], void* stream) {
+  if (!mu || !nu || !out || N <= 0) return DOMDEC_EINVAL;
+  if (!(eps > 0.0) || !(lambda > 0.0) || (variant != 0 && variant != 1) || (precision != 0 && precision != 1) ||
+      maxit < 1)
+    return DOMDEC_EINVAL;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int n = N * N;
+  double* buf = nullptr;
+  if (cudaMallocAsync(&buf, (6 * (size_t)n + 8) * sizeof(double), st) != cudaSuccess) return DOMDEC_ENOMEM;
+  double *dmu = buf, *dnu = buf + n, *lmu = buf + 2 * (size_t)n, *lnu = buf + 3 * (size_t)n;
+  double *da = buf + 4 * (size_t)n, *db = buf + 5 * (size_t)n, *dev = buf + 6 * (size_t)n;
+  int* dstatus = nullptr;
+  cudaError_t e = cudaMallocAsync(&dstatus, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dstatus, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dmu, mu, n * sizeof(double), cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dnu, nu, n * sizeof(double), cudaMemcpyDefault, st);
+  if (e == cudaSuccess) {
+    if (beta_in) e = cudaMemcpyAsync(db, beta_in, n * sizeof(double), cudaMemcpyDefault, st);
+    else e = cudaMemsetAsync(db, 0, n * sizeof(double), st);
+  }
+  if (e == cudaSuccess) e = launch_prepare_inputs(dmu, dnu, lmu, lnu, n, dstatus, st);
+  int hstat = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hstat, dstatus, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  int rc = DOMDEC_OK;
+  if (e != cudaSuccess) rc = DOMDEC_ECUDA;
+  else if (hstat) rc = DOMDEC_EINVAL;
+  if (rc == DOMDEC_OK) {
+    cudaError_t ce = cudaSuccess;
+    int r = full_sinkhorn_dev(dmu, dnu, lmu, lnu, N, eps_start, eps, lambda, variant, precision, maxit, err,
+                              check_every, da, db, out, dev, st, &ce);
+    if (r < 0) rc = DOMDEC_ECUDA;
+    else {
+      rc = r ? DOMDEC_WNOTCONV : DOMDEC_OK;
+      if (alpha) e = cudaMemcpyAsync(alpha, da, n * sizeof(double), cudaMemcpyDefault, st);
+      if (beta && e == cudaSuccess) e = cudaMemcpyAsync(beta, db, n * sizeof(double), cudaMemcpyDefault, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) rc = DOMDEC_ECUDA;
+    }
+  }
+  cudaFreeAsync(dstatus, st);
+  cudaFreeAsync(buf, st);
+  cudaStreamSynchronize(st);
+  return rc;
+}
+
+}  // extern "C"

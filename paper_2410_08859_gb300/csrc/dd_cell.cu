@@ -1,0 +1,415 @@
+// Cell subproblem kernel: one CTA per composite cell of a sub-batch.
+//
+// For cell J with X box X_J (nx1 x nx2 pixels) and Y box B_J (H x W pixels):
+//  a1  rho = max(0, P_Y pi - nu_J)/nu on B_J             (Section 5.1, "Computing and handling nu_{-J}")
+//  a2  X-half  alpha = -(eps lam/(eps+lam)) log int exp((beta-c)/eps) dnu   (Eq. sinkhorn-X-iteration)
+//  a3  Y-half  per y the root of log(rho + e^{beta/eps + z}) + beta/lam = 0 (Eq. proxdiv-problem)
+//  a4  stop when PD/lam = KL(P_X pi | e^{-alpha/lam} mu_J) <= err |mu_J|   (Eq. PD-gap-KL)
+//  a5  nu~_i(y), C~_i = <c, pi~_i>, H~_i = KL(pi~_i | mu_i x nu) of the new cell plan per
+//      member basic cell i, P_X pi~ and the KL_X change for the step-size decision.
+//
+// GB300 design:
+//  * Everything a cell iterates on lives in shared memory; the cost is never stored: c/eps is
+//    q |xi - eta|^2 with integer pixel offsets and q = h^2/eps.
+//  * |x - y|^2 separates over the two axes, so every log-sum-exp over a rectangle is computed as
+//    two 1-D passes (rows, then columns): (nx1 nx2 W + nx1 H W) terms instead of nx1 nx2 H W.
+//  * Cell-local frames keep float arithmetic accurate: with x_c, y_c the box centres and
+//    D = x_c - y_c (integer), alpha/eps = A + a(xi) + 2 q D.xi and beta/eps = B + b(eta) - 2 q D.eta
+//    with A, B per-cell doubles and B = q|D|^2 - A, so that (alpha + beta - c)/eps =
+//    a(xi) + b(eta) - q |xi - eta|^2 exactly; a and b stay moderate while alpha/eps is ~1e4-1e5.
+//  * exp/log are ex2.approx/lg2.approx in log2 units; each 1-D log-sum-exp is shifted by the
+//    previous iteration's value (one pass), with an exact max-shifted fallback.
+#include "dd_common.cuh"
+
+namespace {
+
+template <typename R, typename F>
+__device__ __forceinline__ R lse2_1d(F src, int M, R ctr, R q2, R shift, bool use_shift) {
+  // log2 sum_m 2^{src(m) - q2 (m - ctr)^2}
+  if (use_shift) {
+    R a0 = R(0), a1 = R(0);
+    R d = -ctr;
+    int m = 0;
+    for (; m + 1 < M; m += 2) {
+      R v0 = src(m) - q2 * d * d - shift;
+      d += R(1);
+      R v1 = src(m + 1) - q2 * d * d - shift;
+      d += R(1);
+      a0 += dd_ex2(v0);
+      a1 += dd_ex2(v1);
+    }
+    if (m < M) a0 += dd_ex2(src(m) - q2 * d * d - shift);
+    R acc = a0 + a1;
+    if (acc > R(1e-25) && acc < R(1e25)) return shift + dd_lg2(acc);
+  }
+  R mx = -dd_inf<R>();
+  R d = -ctr;
+  for (int m = 0; m < M; ++m, d += R(1)) mx = max(mx, src(m) - q2 * d * d);
+  if (!(mx > -dd_inf<R>())) return mx;
+  R acc = R(0);
+  d = -ctr;
+  for (int m = 0; m < M; ++m, d += R(1)) acc += dd_ex2(src(m) - q2 * d * d - mx);
+  return mx + dd_lg2(acc);
+}
+
+// Root u of g(u) = (1+s) u + c0 + softplus(lr - u) = 0, i.e. of
+// log(rho + e^u) + s u + c0 = 0 with lr = log rho (Eq. proxdiv-problem with
+// u = beta/eps + z).  g is convex and increasing (g' = 1 + s - sigmoid(lr - u) >= s).
+// Both lines (1+s)u + c0 and s u + c0 + lr lie below g, so g >= 0 at
+// min(u0, u1), their roots; Newton from there decreases monotonically to the root.
+template <typename R>
+__device__ __forceinline__ R newton_u(R lr, R c0, R s, int maxit) {
+  const R L2E = R(DD_LOG2E), LN2 = R(DD_LN2);
+  const R one_s = R(1) + s;
+  R u = -c0 / one_s;
+  if (!(lr > -dd_inf<R>())) return u;  // rho = 0: closed form (Eq. sinkhorn-iters-ot)
+  if (s > R(0)) u = min(u, -(lr + c0) / s);
+  const R tol = sizeof(R) == 4 ? R(2e-6) : R(1e-14);
+  for (int k = 0; k < maxit; ++k) {
+    R t = lr - u;
+    R e = dd_ex2(-fabs(t) * L2E);
+    R ie = dd_rcp(R(1) + e);
+    R sp = max(t, R(0)) + dd_lg2(R(1) + e) * LN2;
+    R sig = t >= R(0) ? ie : e * ie;
+    R g = one_s * u + c0 + sp;
+    R du = g * dd_rcp(one_s - sig);
+    u -= du;
+    if (fabs(du) <= tol * max(R(1), fabs(u))) break;
+  }
+  return u;
+}
+
+__device__ __forceinline__ double box_value(const BoxRec& b, const double* arena, int y1, int y2) {
+  int a = y1 - b.k0, c = y2 - b.l0;
+  if (a < 0 || c < 0 || a >= b.H || c >= b.W) return 0.0;
+  return arena[b.off + (long long)a * b.W + c];
+}
+
+}  // namespace
+
+template <typename R>
+__global__ void __launch_bounds__(512, 1)
+k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbatch) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* red = reinterpret_cast<double*>(smem_raw);  // 32 * 16 doubles
+  __shared__ BoxRec sbox[4];
+  __shared__ int sgeo[8];
+
+  const CellDesc cd = cells[begin + blockIdx.x];
+  CellOut* out = S.cout + blockIdx.x;
+  const double* __restrict__ arena = S.arena[*S.cur];
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int N = S.N, s = S.s;
+  const int nx1 = cd.nx1, nx2 = cd.nx2, nx = nx1 * nx2;
+
+  // ---------------------------------------------------------------- B_J
+  if (tid == 0) {
+    int k0 = 1 << 30, l0 = 1 << 30, k1 = -1, l1 = -1;
+    for (int q = 0; q < 4; ++q) {
+      BoxRec b = {0, 0, 0, 0, 0};
+      if (cd.mem[q] >= 0) b = S.box[cd.mem[q]];
+      sbox[q] = b;
+      if (cd.mem[q] < 0 || b.H * b.W == 0) continue;
+      k0 = min(k0, b.k0); l0 = min(l0, b.l0);
+      k1 = max(k1, b.k0 + b.H); l1 = max(l1, b.l0 + b.W);
+    }
+    int st = CELL_OK;
+    if (k1 < 0) {
+      st = CELL_EMPTY;
+      k0 = l0 = k1 = l1 = 0;
+    } else {
+      k0 = max(0, k0 - S.margin); l0 = max(0, l0 - S.margin);
+      k1 = min(N, k1 + S.margin); l1 = min(N, l1 + S.margin);
+      int H = k1 - k0, W = l1 - l0;
+      if (H * W > S.cap_ny || H > S.cap_side || W > S.cap_side) st = CELL_TOOBIG;
+    }
+    sgeo[0] = k0; sgeo[1] = l0; sgeo[2] = k1 - k0; sgeo[3] = l1 - l0; sgeo[4] = st;
+  }
+  __syncthreads();
+  const int k0 = sgeo[0], l0 = sgeo[1], H = sgeo[2], W = sgeo[3];
+  if (sgeo[4] != CELL_OK) {
+    if (tid == 0) {
+      CellOut o;
+      o.k0 = k0; o.l0 = l0; o.H = H; o.W = W; o.iters = 0; o.status = sgeo[4];
+      o.D1 = o.D2 = 0; o.gap = 0.0; o.dKX[0] = o.dKX[1] = 0.0;
+      for (int q = 0; q < 4; ++q) {
+        int bi = cd.mem[q];
+        o.Ct[q] = bi >= 0 ? S.Cc[bi] : 0.0;
+        o.Ht[q] = bi >= 0 ? S.Hh[bi] : 0.0;
+        o.mass[q] = 0.0;
+      }
+      *out = o;
+      atomicOr(S.status, sgeo[4] == CELL_EMPTY ? ST_EMPTY : ST_TOOBIG);
+    }
+    return;
+  }
+  const int ny = H * W;
+
+  // ------------------------------------------------------- shared layout
+  const int cap_nx = 4 * s * s, tsz = 2 * s * S.cap_side, cap_ny = S.cap_ny;
+  R* xa = reinterpret_cast<R*>(smem_raw + 32 * 16 * sizeof(double));
+  R* av = xa + cap_nx;
+  R* g0 = av + cap_nx;
+  R* Wv = g0 + cap_nx;
+  R* lm = Wv + cap_nx;
+  R* T = lm + cap_nx;
+  R* U = T + tsz;
+  R* bl = U + tsz;
+  R* lrho = bl + cap_ny;
+  R* Zv = lrho + cap_ny;
+  R* bv = Zv + cap_ny;
+  R* lnu = bv + cap_ny;
+
+  // ------------------------------------------------------- frame constants
+  const int xc1 = cd.i0 + nx1 / 2, xc2 = cd.j0 + nx2 / 2;
+  const int yc1 = k0 + H / 2, yc2 = l0 + W / 2;
+  const int D1 = xc1 - yc1, D2 = xc2 - yc2;
+  const int offr = (k0 - cd.i0) + D1, offc = (l0 - cd.j0) + D2;
+  const double eps = S.eps, lam = S.lam;
+  const double q = S.h * S.h / eps;
+  const double sl = eps / lam;            // s = eps/lam
+  const double rr = lam / (eps + lam);    // r = lam/(eps+lam)
+  const R q2 = R(q * DD_LOG2E), qR = R(q), sR = R(sl), rR = R(rr);
+
+  // ------------------------------------------------------- load X side
+  double acc2[2] = {0.0, 0.0};
+  for (int t = tid; t < nx; t += nthr) {
+    int r = t / nx2, c = t - r * nx2;
+    int x = (cd.i0 + r) * N + cd.j0 + c;
+    int xi1 = cd.i0 + r - xc1, xi2 = cd.j0 + c - xc2;
+    acc2[0] += S.alpha[x] / eps - 2.0 * q * (double)(D1 * xi1 + D2 * xi2);
+    acc2[1] += S.mu[x];
+  }
+  block_sum<2>(acc2, red);
+  const double A = acc2[0] / nx, muJ = acc2[1];
+  const double B = q * (double)(D1 * D1 + D2 * D2) - A;
+  const R sB = R(sl * B);
+  const R cEta1 = R(sl * 2.0 * q * D1), cEta2 = R(sl * 2.0 * q * D2);
+  const R cA = R(-(1.0 - rr) * A);
+  const R cD1 = R(2.0 * (1.0 - rr) * q * D1), cD2 = R(2.0 * (1.0 - rr) * q * D2);
+  for (int t = tid; t < nx; t += nthr) {
+    int r = t / nx2, c = t - r * nx2;
+    int x = (cd.i0 + r) * N + cd.j0 + c;
+    int xi1 = cd.i0 + r - xc1, xi2 = cd.j0 + c - xc2;
+    double lin = 2.0 * q * (double)(D1 * xi1 + D2 * xi2);
+    R a = R(S.alpha[x] / eps - lin - A);
+    R l = R(S.logmu[x]);
+    av[t] = a;
+    lm[t] = l;
+    g0[t] = R(-sl * (A + lin));
+    xa[t] = (a + l) * R(DD_LOG2E);
+  }
+  // ------------------------------------------------------- load Y side (a1)
+  for (int u = tid; u < ny; u += nthr) {
+    int kk = u / W, ll = u - kk * W;
+    int y1 = k0 + kk, y2 = l0 + ll, y = y1 * N + y2;
+    double nuJ = 0.0;
+#pragma unroll
+    for (int q4 = 0; q4 < 4; ++q4) nuJ += box_value(sbox[q4], arena, y1, y2);
+    double rho = fmax(0.0, S.PY[y] - nuJ) / S.nu[y];
+    lrho[u] = rho > 0.0 ? R(log(rho)) : -dd_inf<R>();
+    lnu[u] = R(S.lognu[y]);
+  }
+  __syncthreads();
+
+  // ------------------------------------------------------- Sinkhorn loop
+  const double tol = S.err * muJ;
+  const R LN2 = R(DD_LN2), L2E = R(DD_LOG2E);
+  int it = 0;
+  double gap = 0.0;
+  bool first = true;
+  for (;;) {
+    ++it;
+    // Y-half, pass over columns of X: T(r, ll) = log2 sum_c 2^{xa(r,c) - q2 (c - ll - offc)^2}
+    for (int t = tid; t < nx1 * W; t += nthr) {
+      int r = t / W, ll = t - r * W;
+      const R* row = xa + r * nx2;
+      T[t] = lse2_1d<R>([&](int m) { return row[m]; }, nx2, R(ll + offc), q2, T[t], !first);
+    }
+    __syncthreads();
+    // Y-half, pass over rows of X, then the Newton root per y (a3)
+    for (int u = tid; u < ny; u += nthr) {
+      int kk = u / W, ll = u - kk * W;
+      R Z2 = lse2_1d<R>([&](int m) { return T[m * W + ll]; }, nx1, R(kk + offr), q2, Zv[u], !first);
+      Zv[u] = Z2;
+      R Zn = Z2 * LN2;
+      R eta1 = R(k0 + kk - yc1), eta2 = R(l0 + ll - yc2);
+      R c0 = sB - cEta1 * eta1 - cEta2 * eta2 - sR * Zn;
+      R uu = newton_u<R>(lrho[u], c0, sR, S.newton_maxit);
+      R b = uu - Zn;
+      bv[u] = b;
+      bl[u] = (b + lnu[u]) * L2E;
+    }
+    __syncthreads();
+    // X-half, pass over columns of B_J: U(kk, c) = log2 sum_ll 2^{bl(kk,ll) - q2 (ll - (c - offc))^2}
+    for (int t = tid; t < H * nx2; t += nthr) {
+      int kk = t / nx2, c = t - kk * nx2;
+      const R* row = bl + kk * W;
+      U[t] = lse2_1d<R>([&](int m) { return row[m]; }, W, R(c - offc), q2, U[t], !first);
+    }
+    __syncthreads();
+    // X-half, pass over rows of B_J, and the PD gap (a4)
+    double gl[1] = {0.0};
+    for (int t = tid; t < nx; t += nthr) {
+      int r = t / nx2, c = t - r * nx2;
+      R W2 = lse2_1d<R>([&](int m) { return U[m * nx2 + c]; }, H, R(r - offr), q2, Wv[t], !first);
+      Wv[t] = W2;
+      R a = av[t];
+      R tt = a + W2 * LN2;         // log(P_X pi / mu)
+      R g = g0[t] - sR * a;        // -alpha/lam
+      gl[0] += (double)(dd_ex2((lm[t] + g) * L2E) * dd_psi<R>(tt - g));
+    }
+    block_sum<1>(gl, red);
+    gap = gl[0];
+    first = false;
+    if ((S.err >= 0.0 && gap <= tol) || it >= S.maxit || !(gap == gap)) break;
+    // X-update (closed form, a2)
+    for (int t = tid; t < nx; t += nthr) {
+      int r = t / nx2, c = t - r * nx2;
+      R xi1 = R(cd.i0 + r - xc1), xi2 = R(cd.j0 + c - xc2);
+      R a = cA - rR * Wv[t] * LN2 - cD1 * xi1 - cD2 * xi2;
+      av[t] = a;
+      xa[t] = (a + lm[t]) * L2E;
+    }
+    __syncthreads();
+  }
+  const bool nonfinite = !(gap == gap);
+
+  // ------------------------------------------------------- epilogue (a5)
+  double dk[2] = {0.0, 0.0};
+  {
+    const double th_s = 1.0 / nbatch;
+    for (int t = tid; t < nx; t += nthr) {
+      int r = t / nx2, c = t - r * nx2;
+      int x = (cd.i0 + r) * N + cd.j0 + c;
+      int xi1 = cd.i0 + r - xc1, xi2 = cd.j0 + c - xc2;
+      double a = (double)av[t];
+      S.alpha[x] = eps * (A + a + 2.0 * q * (double)(D1 * xi1 + D2 * xi2));
+      double p1 = exp((double)lm[t] + a + (double)Wv[t] * DD_LN2);
+      S.PXnew[x] = p1;
+      double p0 = S.PX[x], m = S.mu[x];
+      double ps = (1.0 - th_s) * p0 + th_s * p1;
+      double k0v = dd_kl_term(p0, m);
+      dk[0] += dd_kl_term(p1, m) - k0v;
+      dk[1] += dd_kl_term(ps, m) - k0v;
+    }
+  }
+  block_sum<2>(dk, red);
+
+  double hs[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) hs[k] = 0.0;
+  const int nhr = nx1 > s ? 2 : 1, nhc = nx2 > s ? 2 : 1;
+  double* nut = S.nut + (long long)blockIdx.x * 4 * cap_ny;
+  R* Te = T;                 // epilogue scratch spans T, U, bl, lrho, Zv
+  R* Ma = T + nx1 * W;
+  R* Md = Ma + nx1 * W;
+  const double h2 = S.h * S.h;
+  for (int hc = 0; hc < nhc; ++hc) {
+    const int cb = hc * s, ce = min(nx2, cb + s);
+    // rows of X_J against columns of B_J, restricted to the column half hc
+    for (int t = tid; t < nx1 * W; t += nthr) {
+      int r = t / W, ll = t - r * W;
+      const R* row = xa + r * nx2;
+      R ctr = R(ll + offc);
+      R T2 = lse2_1d<R>([&](int m) { return row[cb + m]; }, ce - cb, ctr - R(cb), q2, R(0), false);
+      R sw = 0, sa = 0, sd = 0;
+      for (int c = cb; c < ce; ++c) {
+        R d = R(c) - ctr;
+        R w = dd_ex2(row[c] - q2 * d * d - T2);
+        sw += w;
+        sa += w * (av[r * nx2 + c] - qR * d * d);
+        R dt = d + R(D2);
+        sd += w * dt * dt;
+      }
+      R isw = R(1) / sw;
+      Te[t] = T2;
+      Ma[t] = sa * isw;
+      Md[t] = sd * isw;
+    }
+    __syncthreads();
+    for (int u = tid; u < ny; u += nthr) {
+      int kk = u / W, ll = u - kk * W;
+      int y = (k0 + kk) * N + l0 + ll;
+      R ctr = R(kk + offr);
+      double nuy = S.nu[y];
+      for (int hr = 0; hr < nhr; ++hr) {
+        const int rb = hr * s, re = min(nx1, rb + s);
+        R P2 = lse2_1d<R>([&](int m) { return Te[(rb + m) * W + ll]; }, re - rb, ctr - R(rb), q2, R(0), false);
+        R sw = 0, sa = 0, sd = 0;
+        for (int r = rb; r < re; ++r) {
+          R d = R(r) - ctr;
+          R w = dd_ex2(Te[r * W + ll] - q2 * d * d - P2);
+          sw += w;
+          sa += w * (Ma[r * W + ll] - qR * d * d);
+          R dt = d + R(D1);
+          sd += w * (dt * dt + Md[r * W + ll]);
+        }
+        R isw = R(1) / sw;
+        const int qd = 2 * hr + hc;
+        double nt = nuy * exp((double)bv[u] + (double)P2 * DD_LN2);
+        nut[qd * cap_ny + u] = nt;
+        hs[qd] += nt * ((double)(sa * isw) + (double)bv[u]);
+        hs[4 + qd] += h2 * nt * (double)(sd * isw);
+        hs[8 + qd] += nt;
+      }
+    }
+    __syncthreads();
+  }
+  // change of P_Y pi for the step-size decision
+  for (int u = tid; u < ny; u += nthr) {
+    int kk = u / W, ll = u - kk * W;
+    int y1 = k0 + kk, y2 = l0 + ll;
+    double dlt = 0.0;
+#pragma unroll
+    for (int q4 = 0; q4 < 4; ++q4) {
+      if (cd.mem[q4] < 0) continue;
+      int hr = q4 >> 1, hc = q4 & 1;
+      if (hr >= nhr || hc >= nhc) continue;
+      dlt += nut[q4 * cap_ny + u] - box_value(sbox[q4], arena, y1, y2);
+    }
+    if (dlt != 0.0) atomicAdd(S.dPY + y1 * N + y2, dlt);
+  }
+  block_sum<12>(hs, red);
+  if (tid == 0) {
+    CellOut o;
+    o.k0 = k0; o.l0 = l0; o.H = H; o.W = W;
+    o.iters = it;
+    o.status = nonfinite ? CELL_NONFINITE : ((S.err >= 0.0 && gap > tol) ? CELL_MAXIT : CELL_OK);
+    o.D1 = D1; o.D2 = D2;
+    o.gap = gap;
+    o.dKX[0] = dk[0]; o.dKX[1] = dk[1];
+    for (int q4 = 0; q4 < 4; ++q4) {
+      int bi = cd.mem[q4];
+      o.Ct[q4] = hs[4 + q4];
+      o.mass[q4] = hs[8 + q4];
+      o.Ht[q4] = bi >= 0 ? hs[q4] - hs[8 + q4] + S.muinu[bi] : 0.0;
+    }
+    *out = o;
+    atomicAdd(S.counters + 0, (unsigned long long)it);
+    atomicAdd(S.counters + 1, 1ull);
+    if (o.status == CELL_MAXIT) atomicAdd(S.counters + 2, 1ull);
+    atomicMax(S.counters + 5, (unsigned long long)it);
+    atomicMax(S.counters + 6, (unsigned long long)ny);
+    if (nonfinite) atomicOr(S.status, ST_NONFINITE);
+  }
+}
+
+size_t cell_smem_bytes(int s, int cap_side, int cap_ny, int precision) {
+  size_t rs = precision ? sizeof(double) : sizeof(float);
+  size_t cap_nx = 4 * (size_t)s * s, tsz = 2 * (size_t)s * cap_side;
+  return 32 * 16 * sizeof(double) + rs * (5 * cap_nx + 2 * tsz + 5 * (size_t)cap_ny);
+}
+
+cudaError_t launch_cell_solve(const DevState& S, const CellDesc* cells, int begin, int nbatch,
+                              int precision, cudaStream_t st) {
+  size_t smem = cell_smem_bytes(S.s, S.cap_side, S.cap_ny, precision);
+  if (precision) {
+    cudaFuncSetAttribute(k_cell_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_cell_solve<double><<<nbatch, 512, smem, st>>>(S, cells, begin, nbatch);
+  } else {
+    cudaFuncSetAttribute(k_cell_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_cell_solve<float><<<nbatch, 512, smem, st>>>(S, cells, begin, nbatch);
+  }
+  return cudaGetLastError();
+}

@@ -1,0 +1,143 @@
+// Shared device definitions of the domain-decomposition library (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define DD_LOG2E 1.4426950408889634
+#define DD_LN2 0.6931471805599453
+
+// ---------------------------------------------------------------- status codes
+// Per-cell status written by the cell kernel.
+enum { CELL_OK = 0, CELL_MAXIT = 1, CELL_EMPTY = 2, CELL_TOOBIG = 3, CELL_NONFINITE = 4 };
+// Bits of the handle's device status word.
+enum { ST_TOOBIG = 1, ST_ARENA = 2, ST_EMPTY = 4, ST_NONFINITE = 8, ST_BADINPUT = 16 };
+
+// ------------------------------------------------------------------ geometry
+// One composite cell: its X box [i0, i0+nx1) x [j0, j0+nx2) (always a
+// rectangle of real pixels, also for the clipped boundary cells of partition
+// B) and the basic cell of each quadrant (row half, column half) relative to
+// the X box origin; -1 where the quadrant does not exist.
+struct CellDesc {
+  int i0, j0, nx1, nx2;
+  int mem[4];
+};
+
+// Output record of one cell solve.
+struct CellOut {
+  int k0, l0, H, W;      // the cell's Y box B_J
+  int iters, status, D1, D2;
+  double Ct[4], Ht[4], mass[4];  // per quadrant: <c, pi~_i>, KL(pi~_i | mu_i x nu), |nu~_i|
+  double dKX[2];         // sum_{x in X_J} [mu phi(P'/mu) - mu phi(P/mu)] for theta = 1 and theta_safe
+  double gap;            // last PD/lam of the cell
+};
+
+// Basic-cell box: Y rows [k0, k0+H), columns [l0, l0+W), values at arena[off..].
+struct BoxRec {
+  int k0, l0, H, W;
+  long long off;
+};
+
+// Everything the sweep kernels need; passed by value.
+struct DevState {
+  int N, s, nb, nbasic;
+  double h, eps, lam, thr, err, tau;
+  int maxit, newton_maxit, strategy, margin;
+  int cap_ny, cap_side;
+  const double *mu, *nu, *logmu, *lognu;
+  double* muinu;                // muinu[i] = |mu_i| |nu|
+  double *alpha, *PX, *PY, *PXnew, *dPY;
+  double *Cc, *Hh;
+  BoxRec* box;
+  double* arena[2];
+  int* cur;                     // index of the live arena
+  unsigned long long* head;     // bump allocator of the live arena
+  long long cap;                // capacity of each arena (doubles)
+  CellOut* cout;
+  double* nut;                  // per cell position: 4 * cap_ny new marginals
+  double* theta;                // device scalar: last theta
+  double* declog;               // per sub-batch: E0, E(1), E(safe), theta
+  unsigned long long* counters; // 0 cell_iters, 1 cell_solves, 2 maxit cells, 3 greedy, 4 safe, 5 max iters, 6 max ny
+  int* status;
+  double* red;                  // reduction scratch
+  unsigned int* red_count;
+};
+
+// ------------------------------------------------------------------ math
+__device__ __forceinline__ float dd_ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float dd_lg2(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float dd_rcp(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ double dd_ex2(double x) { return exp2(x); }
+__device__ __forceinline__ double dd_lg2(double x) { return log2(x); }
+__device__ __forceinline__ double dd_rcp(double x) { return 1.0 / x; }
+
+template <typename R> __device__ __forceinline__ R dd_inf() { return R(INFINITY); }
+
+// psi(d) = d e^d - e^d + 1 = e^{-g} KL-term ratio (phi(e^d) with phi(s) = s log s - s + 1),
+// evaluated by its Taylor series sum_{k>=2} (k-1)/k! d^k near 0 to avoid cancellation.
+template <typename R> __device__ __forceinline__ R dd_psi(R d) {
+  const R lim = sizeof(R) == 4 ? R(0.25) : R(0.05);
+  if (fabs(d) < lim) {
+    R d2 = d * d;
+    R poly = R(1.0 / 2) + d * (R(1.0 / 3) + d * (R(1.0 / 8) + d * (R(1.0 / 30) + d * (R(1.0 / 144)
+             + d * (R(1.0 / 840) + d * (R(1.0 / 5760) + d * (R(1.0 / 45360) + d * R(1.0 / 403200))))))));
+    return d2 * poly;
+  }
+  R e = dd_ex2(d * R(DD_LOG2E));
+  return e * (d - R(1)) + R(1);
+}
+
+// mu phi(p/mu) with phi(s) = s log s - s + 1 (phi(0) = 1), in double.
+__device__ __forceinline__ double dd_kl_term(double p, double m) {
+  if (p <= 0.0) return m;
+  return p * log(p / m) - p + m;
+}
+
+// ------------------------------------------------------------- reductions
+template <typename T> __device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <typename T> __device__ __forceinline__ T warp_min(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+template <typename T> __device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block-wide sum of K doubles per thread; result valid in every thread.
+// `scratch` must hold 32*K doubles; ends with a barrier.
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K], double* scratch) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = warp_sum(v[k]);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) scratch[wid * K + k] = v[k];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double a = 0.0;
+    for (int w = 0; w < nw; ++w) a += scratch[w * K + k];  // fixed order: deterministic
+    v[k] = a;
+  }
+  __syncthreads();
+}

@@ -1,0 +1,250 @@
+// Global unbalanced Sinkhorn on the N x N grid (Eq. sinkhorn-iters-ot, nu_- = 0):
+// the comparator of Section 5.3, the warm start of DomDec, and the global
+// log-sum-exp of the primal-dual certificate.
+//
+// A half-step needs, for every x, L(x) = log sum_y exp(f(y) - |x-y|^2/eps) with
+// f = pot/eps + log m.  Two evaluations:
+//  * dense      : all N^2 terms per x (the plain method), f tiled through shared memory;
+//  * separable  : |x-y|^2 = (x1-y1)^2 + (x2-y2)^2, so L is a 1-D log-sum-exp along rows
+//                 followed by one along columns: 2 N^3 terms instead of N^4.
+// Values are kept in log2 units (ex2/lg2); float or double arithmetic.
+#include "dd_common.cuh"
+
+namespace {
+
+// out[k*N + j] = log2 sum_l 2^{in[k*N + l] - q2 (j - l)^2}   (one block row k, threads over j)
+template <typename R>
+__global__ void __launch_bounds__(256) k_sep_rows(const R* __restrict__ in, R* __restrict__ out, int N, R q2) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  R* row = reinterpret_cast<R*>(sm);
+  const int k = blockIdx.x;
+  for (int l = threadIdx.x; l < N; l += blockDim.x) row[l] = in[(long long)k * N + l];
+  __syncthreads();
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    R mx = -dd_inf<R>();
+    for (int l = 0; l < N; ++l) { R d = R(j - l); mx = max(mx, row[l] - q2 * d * d); }
+    R acc = R(0);
+    if (mx > -dd_inf<R>())
+      for (int l = 0; l < N; ++l) { R d = R(j - l); acc += dd_ex2(row[l] - q2 * d * d - mx); }
+    out[(long long)k * N + j] = mx + dd_lg2(acc);
+  }
+}
+
+// out[i*N + j] = log2 sum_k 2^{in[k*N + j] - q2 (i - k)^2}   (threads over j, blocks over (i-tile))
+template <typename R>
+__global__ void __launch_bounds__(256) k_sep_cols(const R* __restrict__ in, R* __restrict__ out, int N, R q2) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (j >= N) return;
+  R mx = -dd_inf<R>();
+  for (int k = 0; k < N; ++k) { R d = R(i - k); mx = max(mx, in[(long long)k * N + j] - q2 * d * d); }
+  R acc = R(0);
+  if (mx > -dd_inf<R>())
+    for (int k = 0; k < N; ++k) { R d = R(i - k); acc += dd_ex2(in[(long long)k * N + j] - q2 * d * d - mx); }
+  out[(long long)i * N + j] = mx + dd_lg2(acc);
+}
+
+// Dense: out[x] = log2 sum_y 2^{in[y] - q2 |x - y|^2}, shifted by the previous
+// value out[x] when `use_shift` (one pass), exact max-shifted otherwise.
+template <typename R>
+__global__ void __launch_bounds__(256) k_dense(const R* __restrict__ in, R* __restrict__ out, int N, R q2,
+                                               int use_shift) {
+  constexpr int TILE = 1024;
+  __shared__ R tile[TILE];
+  const int n = N * N;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const R x1 = R(x / N), x2 = R(x % N);
+  const bool active = x < n;
+  R shift = (active && use_shift) ? out[x] : R(0);
+  bool exact = !use_shift;
+  R acc = R(0), mx = -dd_inf<R>();
+  for (int pass = 0; pass < 3; ++pass) {
+    // pass 0: shifted sum (if use_shift); pass 1: max (if exact); pass 2: sum (if exact)
+    if (pass == 0 && !use_shift) continue;
+    if (pass > 0) {
+      int need = __syncthreads_or(active && exact);
+      if (!need) break;
+    }
+    for (int t0 = 0; t0 < n; t0 += TILE) {
+      __syncthreads();
+      for (int t = threadIdx.x; t < TILE && t0 + t < n; t += blockDim.x) tile[t] = in[t0 + t];
+      __syncthreads();
+      if (!active || (pass > 0 && !exact)) continue;
+      const int cnt = min(TILE, n - t0);
+      for (int t = 0; t < cnt; ++t) {
+        int y = t0 + t;
+        R d1 = x1 - R(y / N), d2 = x2 - R(y % N);
+        R v = tile[t] - q2 * (d1 * d1 + d2 * d2);
+        if (pass == 0) acc += dd_ex2(v - shift);
+        else if (pass == 1) mx = max(mx, v);
+        else acc += dd_ex2(v - mx);
+      }
+    }
+    if (pass == 0 && active) {
+      if (acc > R(1e-25) && acc < R(1e25)) shift = shift + dd_lg2(acc);
+      else { exact = true; acc = R(0); }
+    }
+  }
+  if (active) out[x] = exact ? (mx > -dd_inf<R>() ? mx + dd_lg2(acc) : mx) : shift;
+}
+
+template <typename R>
+__global__ void k_to_log2(const double* __restrict__ pot, const double* __restrict__ logm, double inv_eps,
+                          R* __restrict__ out, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = R((pot ? pot[i] * inv_eps : 0.0) + logm[i]) * R(DD_LOG2E);
+}
+
+template <typename R>
+__global__ void k_half(const R* __restrict__ lse2, double kappa, double* __restrict__ pot, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    pot[i] = -kappa * (double)lse2[i] * DD_LN2;
+}
+
+template <typename R>
+__global__ void k_to_nat(const R* __restrict__ lse2, double* __restrict__ out, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = (double)lse2[i] * DD_LN2;
+}
+
+// PD/lam = KL(P_X | e^{-alpha/lam} mu) with P_X = mu e^{alpha/eps + w} (Eq. PD-gap-KL).
+// And the dual of Eq. dual-problem: out = [gap, sum_y nu e^{beta/eps + z}, conj terms..., |mu|, |nu|]
+template <typename R>
+__global__ void __launch_bounds__(512)
+k_sk_eval(const double* __restrict__ mu, const double* __restrict__ nu, const double* __restrict__ alpha,
+          const double* __restrict__ beta, const R* __restrict__ w2, const R* __restrict__ z2, double eps,
+          double lam, int n, double* out) {
+  __shared__ double red[32 * 6];
+  double v[6] = {0, 0, 0, 0, 0, 0};
+  const bool fin = isfinite(lam);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double a = alpha[i], m = mu[i];
+    double t = a / eps + (double)w2[i] * DD_LN2;  // log(P_X/mu)
+    double g = fin ? -a / lam : 0.0;              // log(e^{-alpha/lam})
+    v[0] += m * exp(g) * dd_psi<double>(t - g);
+    if (z2) {
+      double b = beta[i], z = (double)z2[i] * DD_LN2;
+      v[1] += nu[i] * exp(b / eps + z);
+      v[2] += fin ? lam * (exp(-a / lam) - 1.0) * m : -a * m;
+      v[3] += fin ? lam * (exp(-b / lam) - 1.0) * nu[i] : -b * nu[i];
+    }
+    v[4] += m;
+    v[5] += nu[i];
+  }
+  block_sum<6>(v, red);
+  if (threadIdx.x == 0) for (int k = 0; k < 6; ++k) out[k] = v[k];
+}
+
+template <typename R>
+struct Work {
+  R *in2, *tmp, *w2, *z2;
+};
+
+template <typename R>
+cudaError_t lse_all(const R* in2, R* tmp, R* out2, int N, double q, int variant, int use_shift, cudaStream_t st) {
+  R q2 = R(q * DD_LOG2E);
+  if (variant == 1) {
+    k_sep_rows<R><<<N, 256, N * sizeof(R), st>>>(in2, tmp, N, q2);
+    k_sep_cols<R><<<dim3((N + 255) / 256, N), 256, 0, st>>>(tmp, out2, N, q2);
+  } else {
+    int n = N * N;
+    k_dense<R><<<(n + 255) / 256, 256, 0, st>>>(in2, out2, N, q2, use_shift);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// Separable FP64 log-sum-exp over the whole grid (natural units):
+// out[x] = log sum_y exp(pot[y]/eps + logm[y] - h^2 |x-y|^2/eps).  pot may be NULL.
+cudaError_t global_lse64(const double* pot, const double* logm, double eps, double h, int N, double* out,
+                         double* buf_a, double* buf_b, cudaStream_t st) {
+  int n = N * N;
+  k_to_log2<double><<<(n + 255) / 256, 256, 0, st>>>(pot, logm, 1.0 / eps, buf_a, n);
+  lse_all<double>(buf_a, buf_b, buf_a, N, h * h / eps, 1, 0, st);
+  k_to_nat<double><<<(n + 255) / 256, 256, 0, st>>>(buf_a, out, n);
+  return cudaGetLastError();
+}
+
+// Full Sinkhorn driver; all pointers device.  Returns 0, or 1 when the last
+// stage hit maxit.  out: [iterations, PD/lam, primal, dual].
+template <typename R>
+static int full_sinkhorn_impl(const double* mu, const double* nu, const double* logmu, const double* lognu,
+                              int N, double eps_start, double eps, double lam, int variant, int maxit,
+                              double err, int check_every, double* alpha, double* beta, double* out,
+                              double* d_eval, cudaStream_t st, cudaError_t* cerr) {
+  const int n = N * N;
+  const double h = 1.0 / N;
+  Work<R> w;
+  *cerr = cudaMallocAsync(&w.in2, sizeof(R) * 4 * (size_t)n, st);
+  if (*cerr != cudaSuccess) return -1;
+  w.tmp = w.in2 + n; w.w2 = w.tmp + n; w.z2 = w.w2 + n;
+  const int grid = (n + 255) / 256;
+  double evalh[6];
+  long long total = 0;
+  double gap = INFINITY;
+  int rc = 0;
+  if (check_every < 1) check_every = 1;
+  double e = eps_start > eps ? eps_start : eps;
+  bool first_stage = true;
+  for (;;) {
+    const double kap = std::isfinite(lam) ? e / (1.0 + e / lam) : e;
+    const double q = h * h / e;
+    // w = LSE_y[beta/e + log nu]
+    k_to_log2<R><<<grid, 256, 0, st>>>(beta, lognu, 1.0 / e, w.in2, n);
+    lse_all<R>(w.in2, w.tmp, w.w2, N, q, variant, 0, st);
+    int it = 0;
+    bool conv = false;
+    int shift_ok = 0;
+    while (it < maxit) {
+      k_half<R><<<grid, 256, 0, st>>>(w.w2, kap, alpha, n);
+      k_to_log2<R><<<grid, 256, 0, st>>>(alpha, logmu, 1.0 / e, w.in2, n);
+      lse_all<R>(w.in2, w.tmp, w.z2, N, q, variant, shift_ok, st);
+      k_half<R><<<grid, 256, 0, st>>>(w.z2, kap, beta, n);
+      k_to_log2<R><<<grid, 256, 0, st>>>(beta, lognu, 1.0 / e, w.in2, n);
+      lse_all<R>(w.in2, w.tmp, w.w2, N, q, variant, 1, st);
+      shift_ok = 1;
+      ++it;
+      if (it % check_every == 0 || it == maxit) {
+        k_sk_eval<R><<<1, 512, 0, st>>>(mu, nu, alpha, beta, w.w2, nullptr, e, lam, n, d_eval);
+        cudaMemcpyAsync(evalh, d_eval, 6 * sizeof(double), cudaMemcpyDeviceToHost, st);
+        *cerr = cudaStreamSynchronize(st);
+        if (*cerr != cudaSuccess) { cudaFreeAsync(w.in2, st); return -1; }
+        gap = evalh[0];
+        if (err >= 0.0 && gap <= err * evalh[4]) { conv = true; break; }
+        if (!(gap == gap)) break;
+      }
+    }
+    total += it;
+    first_stage = false;
+    (void)first_stage;
+    if (e <= eps) { rc = conv || err < 0.0 ? 0 : 1; break; }
+    e = fmax(eps, 0.5 * e);
+  }
+  // primal / dual at the final eps (z from the last Y-half of the final iterate)
+  const double kap = std::isfinite(lam) ? eps / (1.0 + eps / lam) : eps;
+  (void)kap;
+  k_sk_eval<R><<<1, 512, 0, st>>>(mu, nu, alpha, beta, w.w2, w.z2, eps, lam, n, d_eval);
+  cudaMemcpyAsync(evalh, d_eval, 6 * sizeof(double), cudaMemcpyDeviceToHost, st);
+  *cerr = cudaStreamSynchronize(st);
+  cudaFreeAsync(w.in2, st);
+  if (*cerr != cudaSuccess) return -1;
+  const double D = eps * evalh[4] * evalh[5] - eps * evalh[1] - evalh[2] - evalh[3];
+  const double pd = std::isfinite(lam) ? lam * evalh[0] : evalh[0];
+  out[0] = (double)total;
+  out[1] = evalh[0];
+  out[2] = D + pd;
+  out[3] = D;
+  return rc;
+}
+
+int full_sinkhorn_dev(const double* mu, const double* nu, const double* logmu, const double* lognu, int N,
+                      double eps_start, double eps, double lam, int variant, int precision, int maxit,
+                      double err, int check_every, double* alpha, double* beta, double* out, double* d_eval,
+                      cudaStream_t st, cudaError_t* cerr) {
+  if (precision)
+    return full_sinkhorn_impl<double>(mu, nu, logmu, lognu, N, eps_start, eps, lam, variant, maxit, err,
+                                      check_every, alpha, beta, out, d_eval, st, cerr);
+  return full_sinkhorn_impl<float>(mu, nu, logmu, lognu, N, eps_start, eps, lam, variant, maxit, err,
+                                   check_every, alpha, beta, out, d_eval, st, cerr);
+}

@@ -1,0 +1,535 @@
+// Sweep kernels other than the cell solve:
+//  k_decide  -- GetWeights (greedy / safe / swift) for one sub-batch from FP64 score deltas (a6)
+//  k_apply   -- pi' = sum_J (1-theta) pi_J + theta pi~_J on the basic-cell boxes, truncation,
+//               tight boxes, P_Y / P_X / C_i / H_i updates (a7)
+//  compaction of the box arena, initial plans, score and certificate reductions.
+#include "dd_common.cuh"
+
+// ============================================================== decision (a6)
+// Tracked score (the sum of per-basic-cell transport cost and entropy plus the
+// two exact marginal penalties) and its value after mixing with theta = 1 and
+// theta = 1/|b|; decision on the device, deterministic fixed-order reductions.
+__global__ void __launch_bounds__(512)
+k_decide(DevState S, const CellDesc* __restrict__ cells, int begin, int nbatch, int slot) {
+  __shared__ double red[32 * 5];
+  __shared__ bool is_last;
+  const int n = S.N * S.N;
+  const double lam = S.lam, eps = S.eps, th_s = 1.0 / nbatch;
+  double v[5] = {0, 0, 0, 0, 0};
+  for (int y = blockIdx.x * blockDim.x + threadIdx.x; y < n; y += gridDim.x * blockDim.x) {
+    v[0] += dd_kl_term(S.PX[y], S.mu[y]);
+    double p = S.PY[y], m = S.nu[y];
+    double k0 = dd_kl_term(p, m);
+    v[1] += k0;
+    double d = S.dPY[y];
+    if (d != 0.0) {
+      v[2] += dd_kl_term(fmax(0.0, p + d), m) - k0;
+      v[3] += dd_kl_term(fmax(0.0, p + th_s * d), m) - k0;
+    }
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.nbasic; i += gridDim.x * blockDim.x)
+    v[4] += S.Cc[i] + eps * S.Hh[i];
+  block_sum<5>(v, red);
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 5; ++k) S.red[blockIdx.x * 5 + k] = v[k];
+    __threadfence();
+    unsigned int t = atomicAdd(S.red_count, 1u);
+    is_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last || threadIdx.x != 0) return;
+  __threadfence();
+  double tot[5] = {0, 0, 0, 0, 0};
+  for (int b = 0; b < (int)gridDim.x; ++b)
+    for (int k = 0; k < 5; ++k) tot[k] += ((volatile double*)S.red)[b * 5 + k];
+  double dL = 0.0, dKX1 = 0.0, dKXs = 0.0;
+  for (int j = 0; j < nbatch; ++j) {
+    const CellOut o = S.cout[j];
+    if (o.status == CELL_EMPTY || o.status == CELL_TOOBIG) continue;
+    const CellDesc cd = cells[begin + j];
+    for (int q = 0; q < 4; ++q) {
+      int bi = cd.mem[q];
+      if (bi < 0) continue;
+      dL += (o.Ct[q] - S.Cc[bi]) + eps * (o.Ht[q] - S.Hh[bi]);
+    }
+    dKX1 += o.dKX[0];
+    dKXs += o.dKX[1];
+  }
+  const double E0 = tot[4] + lam * tot[0] + lam * tot[1];
+  const double Eg = E0 + dL + lam * dKX1 + lam * tot[2];
+  const double Es = E0 + th_s * dL + lam * dKXs + lam * tot[3];
+  double theta;
+  if (S.strategy == 3) theta = 1.0;                 // greedy
+  else if (S.strategy == 2) theta = th_s;           // safe
+  else theta = (Eg <= Es + 1e-12 * fabs(E0) || (S.tau > 0.0 && Eg <= (1.0 + S.tau) * E0)) ? 1.0 : th_s;
+  *S.theta = theta;
+  double* lg = S.declog + 4 * slot;
+  lg[0] = E0; lg[1] = Eg; lg[2] = Es; lg[3] = theta;
+  atomicAdd(S.counters + (theta == 1.0 ? 3 : 4), 1ull);
+  *S.red_count = 0u;
+}
+
+// ================================================================= apply (a7)
+__global__ void __launch_bounds__(256)
+k_apply(DevState S, const CellDesc* __restrict__ cells, int begin) {
+  __shared__ BoxRec ob[4];
+  __shared__ int bb[4][4];       // per quadrant: min kk, max kk, min ll, max ll of kept entries
+  __shared__ long long noff[4];
+  __shared__ int nbox[4][4];
+  const CellOut o = S.cout[blockIdx.x];
+  if (o.status == CELL_EMPTY || o.status == CELL_TOOBIG) return;
+  const CellDesc cd = cells[begin + blockIdx.x];
+  const double th = *S.theta, thr = S.thr;
+  const int N = S.N, H = o.H, W = o.W, ny = H * W;
+  double* arena = S.arena[*S.cur];
+  const double* nut = S.nut + (long long)blockIdx.x * 4 * S.cap_ny;
+  const int tid = threadIdx.x;
+  if (tid < 4) {
+    BoxRec b = {0, 0, 0, 0, 0};
+    if (cd.mem[tid] >= 0) b = S.box[cd.mem[tid]];
+    ob[tid] = b;
+    bb[tid][0] = 1 << 30; bb[tid][1] = -1; bb[tid][2] = 1 << 30; bb[tid][3] = -1;
+  }
+  __syncthreads();
+  int lb[4][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) { lb[q][0] = 1 << 30; lb[q][1] = -1; lb[q][2] = 1 << 30; lb[q][3] = -1; }
+  for (int u = tid; u < ny; u += blockDim.x) {
+    int kk = u / W, ll = u - kk * W;
+    int y1 = o.k0 + kk, y2 = o.l0 + ll;
+    double dl = 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (cd.mem[q] < 0) continue;
+      const BoxRec& b = ob[q];
+      int a = y1 - b.k0, c = y2 - b.l0;
+      double old = (a >= 0 && c >= 0 && a < b.H && c < b.W) ? arena[b.off + (long long)a * b.W + c] : 0.0;
+      double v = (1.0 - th) * old + th * nut[q * S.cap_ny + u];
+      if (v < thr) v = 0.0;
+      dl += v - old;
+      if (v > 0.0) {
+        lb[q][0] = min(lb[q][0], kk); lb[q][1] = max(lb[q][1], kk);
+        lb[q][2] = min(lb[q][2], ll); lb[q][3] = max(lb[q][3], ll);
+      }
+    }
+    int y = y1 * N + y2;
+    if (dl != 0.0) atomicAdd(S.PY + y, dl);
+    S.dPY[y] = 0.0;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    int m0 = warp_min(lb[q][0]), m1 = warp_max(lb[q][1]), m2 = warp_min(lb[q][2]), m3 = warp_max(lb[q][3]);
+    if ((tid & 31) == 0) {
+      atomicMin(&bb[q][0], m0); atomicMax(&bb[q][1], m1);
+      atomicMin(&bb[q][2], m2); atomicMax(&bb[q][3], m3);
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int q = 0; q < 4; ++q) {
+      int bi = cd.mem[q];
+      if (bi < 0) continue;
+      BoxRec nb = {o.k0, o.l0, 0, 0, 0};
+      if (bb[q][1] >= 0) {
+        nb.k0 = o.k0 + bb[q][0]; nb.l0 = o.l0 + bb[q][2];
+        nb.H = bb[q][1] - bb[q][0] + 1; nb.W = bb[q][3] - bb[q][2] + 1;
+      }
+      long long sz = (long long)nb.H * nb.W;
+      unsigned long long off = atomicAdd(S.head, (unsigned long long)sz);
+      if ((long long)off + sz > S.cap) {
+        atomicOr(S.status, ST_ARENA);
+        nb.H = nb.W = 0;
+        off = 0;
+      }
+      nb.off = (long long)off;
+      noff[q] = nb.off;
+      nbox[q][0] = nb.k0; nbox[q][1] = nb.l0; nbox[q][2] = nb.H; nbox[q][3] = nb.W;
+      S.box[bi] = nb;
+      S.Cc[bi] = (1.0 - th) * S.Cc[bi] + th * o.Ct[q];
+      S.Hh[bi] = (1.0 - th) * S.Hh[bi] + th * o.Ht[q];
+    }
+  }
+  __syncthreads();
+  for (int q = 0; q < 4; ++q) {
+    if (cd.mem[q] < 0) continue;
+    const int nk0 = nbox[q][0], nl0 = nbox[q][1], nH = nbox[q][2], nW = nbox[q][3];
+    const BoxRec& b = ob[q];
+    for (int u = tid; u < nH * nW; u += blockDim.x) {
+      int a = u / nW, c = u - a * nW;
+      int y1 = nk0 + a, y2 = nl0 + c;
+      int oa = y1 - b.k0, oc = y2 - b.l0;
+      double old = (oa >= 0 && oc >= 0 && oa < b.H && oc < b.W) ? arena[b.off + (long long)oa * b.W + oc] : 0.0;
+      double v = (1.0 - th) * old + th * nut[q * S.cap_ny + (y1 - o.k0) * W + (y2 - o.l0)];
+      if (v < thr) v = 0.0;
+      arena[noff[q] + u] = v;
+    }
+  }
+  for (int t = tid; t < cd.nx1 * cd.nx2; t += blockDim.x) {
+    int r = t / cd.nx2, c = t - r * cd.nx2;
+    int x = (cd.i0 + r) * N + cd.j0 + c;
+    S.PX[x] = (1.0 - th) * S.PX[x] + th * S.PXnew[x];
+  }
+}
+
+// ============================================================ arena compaction
+// Exclusive scan of the box sizes (one block), new offsets into `newoff`.
+__global__ void __launch_bounds__(1024) k_scan_boxes(DevState S, long long* newoff) {
+  __shared__ long long part[1024];
+  const int nb = S.nbasic, tid = threadIdx.x, per = (nb + blockDim.x - 1) / blockDim.x;
+  const int b0 = min(nb, tid * per), b1 = min(nb, b0 + per);
+  long long acc = 0;
+  for (int i = b0; i < b1; ++i) acc += (long long)S.box[i].H * S.box[i].W;
+  part[tid] = acc;
+  __syncthreads();
+  if (tid == 0) {
+    long long run = 0;
+    for (int t = 0; t < (int)blockDim.x; ++t) { long long v = part[t]; part[t] = run; run += v; }
+    newoff[nb] = run;
+  }
+  __syncthreads();
+  long long run = part[tid];
+  for (int i = b0; i < b1; ++i) { newoff[i] = run; run += (long long)S.box[i].H * S.box[i].W; }
+}
+
+__global__ void __launch_bounds__(256) k_copy_boxes(DevState S, const long long* newoff) {
+  const int i = blockIdx.x;
+  const int cur = *S.cur;
+  const double* src = S.arena[cur];
+  double* dst = S.arena[1 - cur];
+  BoxRec b = S.box[i];
+  long long sz = (long long)b.H * b.W, no = newoff[i];
+  for (long long u = threadIdx.x; u < sz; u += blockDim.x) dst[no + u] = src[b.off + u];
+  __syncthreads();
+  if (threadIdx.x == 0) S.box[i].off = no;
+}
+
+__global__ void k_flip_arena(DevState S, const long long* newoff) {
+  *S.cur = 1 - *S.cur;
+  *S.head = (unsigned long long)newoff[S.nbasic];
+}
+
+// ============================================================ inputs and init
+__global__ void k_prepare_inputs(const double* mu, const double* nu, double* logmu, double* lognu,
+                                 int n, int* status) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double a = mu[i], b = nu[i];
+    if (!(a > 0.0) || !(b > 0.0) || isinf(a) || isinf(b)) atomicOr(status, ST_BADINPUT);
+    logmu[i] = log(a);
+    lognu[i] = log(b);
+  }
+}
+
+// Per basic cell: |mu_i|, the first two moments of mu_i (for <c, mu_i x nu>)
+// and |mu_i| |nu|.  One block per basic cell.
+__global__ void __launch_bounds__(256)
+k_basic_masses(DevState S, const double* nu_mom, double* mumass) {
+  __shared__ double red[32 * 4];
+  const int i = blockIdx.x, s = S.s, I = i / S.nb, J = i % S.nb;
+  double v[4] = {0, 0, 0, 0};
+  for (int t = threadIdx.x; t < s * s; t += blockDim.x) {
+    int r = I * s + t / s, c = J * s + t % s;
+    double m = S.mu[r * S.N + c], x1 = r * S.h, x2 = c * S.h;
+    v[0] += m; v[1] += m * x1; v[2] += m * x2; v[3] += m * (x1 * x1 + x2 * x2);
+  }
+  block_sum<4>(v, red);
+  if (threadIdx.x == 0) {
+    // nu_mom = (|nu|, sum y1 nu, sum y2 nu, sum |y|^2 nu)
+    mumass[i] = v[0];
+    S.muinu[i] = v[0] * nu_mom[0];
+    // <c, mu_i x nu> = |nu| sum|x|^2 mu - 2 sum x mu . sum y nu + |mu_i| sum |y|^2 nu
+    S.Cc[i] = nu_mom[0] * v[3] - 2.0 * (v[1] * nu_mom[1] + v[2] * nu_mom[2]) + v[0] * nu_mom[3];
+    S.Hh[i] = 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(512) k_moments(const double* nu, int N, double h, double* out) {
+  __shared__ double red[32 * 4];
+  double v[4] = {0, 0, 0, 0};
+  for (int y = threadIdx.x; y < N * N; y += blockDim.x) {
+    double m = nu[y], y1 = (y / N) * h, y2 = (y % N) * h;
+    v[0] += m; v[1] += m * y1; v[2] += m * y2; v[3] += m * (y1 * y1 + y2 * y2);
+  }
+  block_sum<4>(v, red);
+  if (threadIdx.x == 0) for (int k = 0; k < 4; ++k) out[k] = v[k];
+}
+
+// Product plan pi0 = mu x nu: nu_i = |mu_i| nu on the full grid, truncated.
+// Pass 1 (mode 0): tight box of the kept entries.  Pass 2 (mode 1): values, P_Y.
+__global__ void __launch_bounds__(256)
+k_init_product(DevState S, const double* mumass, int mode) {
+  __shared__ int bb[4];
+  const int i = blockIdx.x, N = S.N, n = N * N;
+  const double mi = mumass[i];
+  double* arena = S.arena[*S.cur];
+  if (mode == 0) {
+    if (threadIdx.x == 0) { bb[0] = 1 << 30; bb[1] = -1; bb[2] = 1 << 30; bb[3] = -1; }
+    __syncthreads();
+    int lb[4] = {1 << 30, -1, 1 << 30, -1};
+    for (int y = threadIdx.x; y < n; y += blockDim.x) {
+      if (mi * S.nu[y] >= S.thr) {
+        int k = y / N, l = y % N;
+        lb[0] = min(lb[0], k); lb[1] = max(lb[1], k); lb[2] = min(lb[2], l); lb[3] = max(lb[3], l);
+      }
+    }
+    lb[0] = warp_min(lb[0]); lb[1] = warp_max(lb[1]); lb[2] = warp_min(lb[2]); lb[3] = warp_max(lb[3]);
+    if ((threadIdx.x & 31) == 0) {
+      atomicMin(&bb[0], lb[0]); atomicMax(&bb[1], lb[1]); atomicMin(&bb[2], lb[2]); atomicMax(&bb[3], lb[3]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      BoxRec b = {0, 0, 0, 0, 0};
+      if (bb[1] >= 0) { b.k0 = bb[0]; b.l0 = bb[2]; b.H = bb[1] - bb[0] + 1; b.W = bb[3] - bb[2] + 1; }
+      S.box[i] = b;
+    }
+  } else {
+    BoxRec b = S.box[i];
+    for (int u = threadIdx.x; u < b.H * b.W; u += blockDim.x) {
+      int y = (b.k0 + u / b.W) * N + b.l0 + u % b.W;
+      double v = mi * S.nu[y];
+      if (v < S.thr) v = 0.0;
+      arena[b.off + u] = v;
+      if (v != 0.0) atomicAdd(S.PY + y, v);
+    }
+  }
+}
+
+__global__ void k_set_offsets(DevState S, const long long* newoff) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.nbasic; i += gridDim.x * blockDim.x)
+    S.box[i].off = newoff[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) *S.head = (unsigned long long)newoff[S.nbasic];
+}
+
+__global__ void k_px_product(DevState S, const double* nu_mom) {
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < S.N * S.N; x += gridDim.x * blockDim.x) {
+    S.PX[x] = S.mu[x] * nu_mom[0];
+    S.alpha[x] = 0.0;
+  }
+}
+
+// Plan from duals pi = exp((alpha0 + beta0 - c)/eps0) mu x nu, per basic cell.
+// mode 0: tight box of {y : nu_i(y) >= thr} from the full-grid log marginal,
+//         computed with two 1-D log-sum-exp passes over X_i (FP64);
+// mode 1: values on the box (dense over X_i), C_i, H_i, P_Y.
+__global__ void __launch_bounds__(256)
+k_init_duals(DevState S, const double* __restrict__ alpha0, const double* __restrict__ beta0,
+             double eps0, int mode) {
+  extern __shared__ double tsm[];   // s * N doubles (mode 0)
+  __shared__ int bb[4];
+  __shared__ double red[32 * 2];
+  const int i = blockIdx.x, s = S.s, N = S.N, I = i / S.nb, J = i % S.nb;
+  const int r0 = I * s, c0 = J * s;
+  const double q = S.h * S.h / eps0;
+  double* arena = S.arena[*S.cur];
+  if (mode == 0) {
+    // T(r, l) = log sum_{c in cols(X_i)} exp(alpha0/eps0 + log mu - q (c - l)^2), r in rows(X_i)
+    for (int t = threadIdx.x; t < s * N; t += blockDim.x) {
+      int r = t / N, l = t % N;
+      double mx = -INFINITY;
+      for (int c = 0; c < s; ++c) {
+        int x = (r0 + r) * N + c0 + c;
+        double d = c0 + c - l;
+        mx = fmax(mx, alpha0[x] / eps0 + S.logmu[x] - q * d * d);
+      }
+      double acc = 0.0;
+      for (int c = 0; c < s; ++c) {
+        int x = (r0 + r) * N + c0 + c;
+        double d = c0 + c - l;
+        acc += exp(alpha0[x] / eps0 + S.logmu[x] - q * d * d - mx);
+      }
+      tsm[t] = mx + log(acc);
+    }
+    if (threadIdx.x == 0) { bb[0] = 1 << 30; bb[1] = -1; bb[2] = 1 << 30; bb[3] = -1; }
+    __syncthreads();
+    int lb[4] = {1 << 30, -1, 1 << 30, -1};
+    const double lthr = log(S.thr);
+    for (int y = threadIdx.x; y < N * N; y += blockDim.x) {
+      int k = y / N, l = y % N;
+      double mx = -INFINITY;
+      for (int r = 0; r < s; ++r) { double d = r0 + r - k; mx = fmax(mx, tsm[r * N + l] - q * d * d); }
+      double acc = 0.0;
+      for (int r = 0; r < s; ++r) { double d = r0 + r - k; acc += exp(tsm[r * N + l] - q * d * d - mx); }
+      double lv = S.lognu[y] + beta0[y] / eps0 + mx + log(acc);
+      if (lv >= lthr) {
+        lb[0] = min(lb[0], k); lb[1] = max(lb[1], k); lb[2] = min(lb[2], l); lb[3] = max(lb[3], l);
+      }
+    }
+    lb[0] = warp_min(lb[0]); lb[1] = warp_max(lb[1]); lb[2] = warp_min(lb[2]); lb[3] = warp_max(lb[3]);
+    if ((threadIdx.x & 31) == 0) {
+      atomicMin(&bb[0], lb[0]); atomicMax(&bb[1], lb[1]); atomicMin(&bb[2], lb[2]); atomicMax(&bb[3], lb[3]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      BoxRec b = {0, 0, 0, 0, 0};
+      if (bb[1] >= 0) { b.k0 = bb[0]; b.l0 = bb[2]; b.H = bb[1] - bb[0] + 1; b.W = bb[3] - bb[2] + 1; }
+      S.box[i] = b;
+    }
+  } else {
+    BoxRec b = S.box[i];
+    double v[2] = {0.0, 0.0};
+    for (int u = threadIdx.x; u < b.H * b.W; u += blockDim.x) {
+      int k = b.k0 + u / b.W, l = b.l0 + u % b.W, y = k * N + l;
+      double by = beta0[y], nuy = S.nu[y];
+      double acc = 0.0, cacc = 0.0, hacc = 0.0;
+      for (int t = 0; t < s * s; ++t) {
+        int r = r0 + t / s, c = c0 + t % s, x = r * N + c;
+        double cc = S.h * S.h * (double)((r - k) * (r - k) + (c - l) * (c - l));
+        double lr = (alpha0[x] + by - cc) / eps0;
+        double p = exp(lr) * S.mu[x] * nuy;
+        acc += p; cacc += cc * p; hacc += p * lr - p;
+      }
+      double val = acc < S.thr ? 0.0 : acc;
+      arena[b.off + u] = val;
+      if (val != 0.0) atomicAdd(S.PY + y, val);
+      v[0] += cacc; v[1] += hacc;
+    }
+    block_sum<2>(v, red);
+    if (threadIdx.x == 0) {
+      S.Cc[i] = v[0];
+      S.Hh[i] = v[1] + S.muinu[i];
+    }
+  }
+}
+
+// ================================================================ reductions
+// out: [sum_i (C_i + eps H_i), lam KL(P_X|mu), lam KL(P_Y|nu), |P_Y|, box entries]
+__global__ void __launch_bounds__(512) k_score(DevState S, double* out) {
+  __shared__ double red[32 * 5];
+  const int n = S.N * S.N;
+  double v[5] = {0, 0, 0, 0, 0};
+  for (int y = threadIdx.x; y < n; y += blockDim.x) {
+    v[1] += dd_kl_term(S.PX[y], S.mu[y]);
+    v[2] += dd_kl_term(S.PY[y], S.nu[y]);
+    v[3] += S.PY[y];
+  }
+  for (int i = threadIdx.x; i < S.nbasic; i += blockDim.x) {
+    v[0] += S.Cc[i] + S.eps * S.Hh[i];
+    v[4] += (double)S.box[i].H * S.box[i].W;
+  }
+  block_sum<5>(v, red);
+  if (threadIdx.x == 0) {
+    out[0] = v[0]; out[1] = S.lam * v[1]; out[2] = S.lam * v[2]; out[3] = v[3]; out[4] = v[4];
+  }
+}
+
+// Dual value and marginal errors of the certificate.
+// z: log int exp((alpha - c)/eps) dmu per y (natural units); beta* = -kappa z.
+// out: [sum_y nu e^{beta*/eps + z}, sum_x (e^{-alpha/lam}-1) mu, sum_y (e^{-beta*/lam}-1) nu,
+//       |mu|, |nu|, L1 X error, L1 Y error]
+__global__ void __launch_bounds__(512)
+k_cert(DevState S, const double* z, double* beta_out, double* out) {
+  __shared__ double red[32 * 7];
+  const int n = S.N * S.N;
+  const double eps = S.eps, lam = S.lam, kap = eps / (1.0 + eps / lam);
+  double v[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int y = threadIdx.x; y < n; y += blockDim.x) {
+    double b = -kap * z[y];
+    if (beta_out) beta_out[y] = b;
+    double ea = exp(-S.alpha[y] / lam), eb = exp(-b / lam);
+    v[0] += S.nu[y] * exp(b / eps + z[y]);
+    v[1] += (ea - 1.0) * S.mu[y];
+    v[2] += (eb - 1.0) * S.nu[y];
+    v[3] += S.mu[y];
+    v[4] += S.nu[y];
+    v[5] += fabs(S.PX[y] - ea * S.mu[y]);
+    v[6] += fabs(S.PY[y] - eb * S.nu[y]);
+  }
+  block_sum<7>(v, red);
+  if (threadIdx.x == 0) for (int k = 0; k < 7; ++k) out[k] = v[k];
+}
+
+// ======================================================= host launch wrappers
+cudaError_t launch_decide(const DevState& S, const CellDesc* cells, int begin, int nbatch, int slot,
+                          cudaStream_t st) {
+  int nblk = 2 * 152;
+  int n = S.N * S.N;
+  if (n < nblk * 512) nblk = (n + 511) / 512;
+  if (nblk < 1) nblk = 1;
+  k_decide<<<nblk, 512, 0, st>>>(S, cells, begin, nbatch, slot);
+  return cudaGetLastError();
+}
+cudaError_t launch_apply(const DevState& S, const CellDesc* cells, int begin, int nbatch, cudaStream_t st) {
+  k_apply<<<nbatch, 256, 0, st>>>(S, cells, begin);
+  return cudaGetLastError();
+}
+cudaError_t launch_compact(const DevState& S, long long* newoff, cudaStream_t st) {
+  k_scan_boxes<<<1, 1024, 0, st>>>(S, newoff);
+  k_copy_boxes<<<S.nbasic, 256, 0, st>>>(S, newoff);
+  k_flip_arena<<<1, 1, 0, st>>>(S, newoff);
+  return cudaGetLastError();
+}
+cudaError_t launch_prepare_inputs(const double* mu, const double* nu, double* logmu, double* lognu,
+                                  int n, int* status, cudaStream_t st) {
+  k_prepare_inputs<<<(n + 255) / 256, 256, 0, st>>>(mu, nu, logmu, lognu, n, status);
+  return cudaGetLastError();
+}
+__global__ void k_px_duals(DevState S, const double* alpha0, const double* w, double eps0) {
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < S.N * S.N; x += gridDim.x * blockDim.x) {
+    S.PX[x] = S.mu[x] * exp(alpha0[x] / eps0 + w[x]);
+    S.alpha[x] = alpha0[x];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_copy_boxes_to(DevState S, const long long* newoff, double* dst) {
+  const int i = blockIdx.x;
+  const double* src = S.arena[*S.cur];
+  BoxRec b = S.box[i];
+  long long sz = (long long)b.H * b.W, no = newoff[i];
+  for (long long u = threadIdx.x; u < sz; u += blockDim.x) dst[no + u] = src[b.off + u];
+}
+
+__global__ void k_reset_cur(DevState S, const long long* newoff) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.nbasic; i += gridDim.x * blockDim.x)
+    S.box[i].off = newoff[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *S.cur = 0;
+    *S.head = (unsigned long long)newoff[S.nbasic];
+  }
+}
+
+cudaError_t launch_init_product_boxes(const DevState& S, double* nu_mom, double* mumass, long long* newoff,
+                                      cudaStream_t st) {
+  k_moments<<<1, 512, 0, st>>>(S.nu, S.N, S.h, nu_mom);
+  k_basic_masses<<<S.nbasic, 256, 0, st>>>(S, nu_mom, mumass);
+  k_init_product<<<S.nbasic, 256, 0, st>>>(S, mumass, 0);
+  k_scan_boxes<<<1, 1024, 0, st>>>(S, newoff);
+  return cudaGetLastError();
+}
+cudaError_t launch_init_product_fill(const DevState& S, double* nu_mom, double* mumass, long long* newoff,
+                                     cudaStream_t st) {
+  k_set_offsets<<<(S.nbasic + 255) / 256, 256, 0, st>>>(S, newoff);
+  k_init_product<<<S.nbasic, 256, 0, st>>>(S, mumass, 1);
+  k_px_product<<<(S.N * S.N + 255) / 256, 256, 0, st>>>(S, nu_mom);
+  return cudaGetLastError();
+}
+cudaError_t launch_init_duals_boxes(const DevState& S, const double* alpha0, const double* beta0, double eps0,
+                                    double* nu_mom, double* mumass, long long* newoff, cudaStream_t st) {
+  k_moments<<<1, 512, 0, st>>>(S.nu, S.N, S.h, nu_mom);
+  k_basic_masses<<<S.nbasic, 256, 0, st>>>(S, nu_mom, mumass);
+  size_t sm = (size_t)S.s * S.N * sizeof(double);
+  cudaFuncSetAttribute(k_init_duals, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_init_duals<<<S.nbasic, 256, sm, st>>>(S, alpha0, beta0, eps0, 0);
+  k_scan_boxes<<<1, 1024, 0, st>>>(S, newoff);
+  return cudaGetLastError();
+}
+cudaError_t launch_init_duals_fill(const DevState& S, const double* alpha0, const double* beta0, double eps0,
+                                   const double* w, long long* newoff, cudaStream_t st) {
+  k_set_offsets<<<(S.nbasic + 255) / 256, 256, 0, st>>>(S, newoff);
+  k_init_duals<<<S.nbasic, 256, 0, st>>>(S, alpha0, beta0, eps0, 1);
+  k_px_duals<<<(S.N * S.N + 255) / 256, 256, 0, st>>>(S, alpha0, w, eps0);
+  return cudaGetLastError();
+}
+cudaError_t launch_regrow(const DevState& S, double* new0, double* new1, long long* newoff, cudaStream_t st) {
+  (void)new1;
+  k_scan_boxes<<<1, 1024, 0, st>>>(S, newoff);
+  k_copy_boxes_to<<<S.nbasic, 256, 0, st>>>(S, newoff, new0);
+  k_reset_cur<<<(S.nbasic + 255) / 256, 256, 0, st>>>(S, newoff);
+  return cudaGetLastError();
+}
+cudaError_t launch_score(const DevState& S, double* out, cudaStream_t st) {
+  k_score<<<1, 512, 0, st>>>(S, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_cert(const DevState& S, const double* z, double* beta_out, double* out, cudaStream_t st) {
+  k_cert<<<1, 512, 0, st>>>(S, z, beta_out, out);
+  return cudaGetLastError();
+}

@@ -1,0 +1,233 @@
+"""GPU parity of the DomDec sweep (C ABI) against the FP64 CPU oracle.
+
+FP64 cell arithmetic: the GPU must reproduce the oracle sweep by sub-batch --
+the same theta decisions, the same cell iteration counts, the same boxes, and
+scores / marginals / potentials to round-off (tolerances below).
+FP32 cell arithmetic: with a fixed number of cell iterations (err < 0) the
+same decisions and scores within FP32 error; run to convergence it must reach
+the oracle's global optimum within the stated tolerances (relative score
+<= 1e-6, plan-marginal L1 <= 1e-5 of the mass).
+"""
+import numpy as np
+import pytest
+
+from oracle import domdec as odd
+from oracle import uot
+from paper_2410_08859_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dd():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2410_08859_gb300 import domdec
+    return domdec
+
+
+def gpu_boxes(g, geo):
+    box, vals = g.basic_marginals()
+    out = []
+    pos = 0
+    for i in range(geo.nbasic):
+        k0, l0, H, W = box[i]
+        out.append((k0, l0, H, W, vals[pos:pos + H * W].reshape(H, W)))
+        pos += H * W
+    return out
+
+
+def compare_state(g, st, tol_score, tol_l1, tol_alpha, check_boxes=True, tol_box=None):
+    sc = g.score()
+    ref = odd.score_terms(st)
+    assert abs(sc[0] - ref[0]) <= tol_score * abs(ref[0]), (sc[0], ref[0])
+    PX, PY = g.marginals()
+    mass = st.mu.sum()
+    assert np.abs(PX - st.PX).sum() <= tol_l1 * mass
+    assert np.abs(PY - st.PY).sum() <= tol_l1 * mass
+    a = g.duals()
+    assert np.abs(a - st.alpha).max() <= tol_alpha * (1 + np.abs(st.alpha).max())
+    if check_boxes:
+        for i, (k0, l0, H, W, v) in enumerate(gpu_boxes(g, st.geo)):
+            lo, hi = st.lo[i], st.hi[i]
+            assert (k0, l0, H, W) == (lo[0], lo[1], hi[0] - lo[0], hi[1] - lo[1]), i
+            if tol_box is not None and v.size:
+                assert np.abs(v - st.vals[i]).max() <= tol_box * max(st.vals[i].max(), 1e-300)
+
+
+def run_pair(dd, N, s, mu, nu, eps, lam, sweeps, precision, strategy="staggered", err=2e-5, maxit=2000,
+             tau=0.0, thr=1e-15, tols=(1e-10, 1e-10, 1e-8), tol_box=1e-8, init_duals=None):
+    geo = odd.Geometry(N, s)
+    mu, nu = mu.ravel(), nu.ravel()
+    kw = dict(precision=precision, strategy=strategy, err=err, maxit=maxit, tau=tau, trunc_thr=thr)
+    if init_duals is None:
+        st = odd.init_product(geo, mu, nu, eps, lam, thr)
+        g = dd.DomDec(mu, nu, eps, lam, s, **kw)
+    else:
+        a0, b0, e0 = init_duals
+        st = odd.init_from_duals(geo, mu, nu, a0, b0, e0, eps, lam, thr)
+        g = dd.DomDec(mu, nu, eps, lam, s, alpha0=a0, beta0=b0, eps_init=e0, **kw)
+    compare_state(g, st, *tols, tol_box=tol_box)
+    nrec = 0
+    for k in range(sweeps):
+        which = "AB"[k % 2]
+        if strategy == "sequential":
+            raise ValueError
+        log = odd.sweep(st, which, strategy, tau=tau, err=err, maxit=maxit)
+        g.iterate(1)
+        rc = g.sync()
+        assert rc in (0, 1)
+        dec = g.decisions()
+        assert len(dec) == nrec + len(log)
+        for rec, d in zip(log, dec[nrec:]):
+            assert d[3] == rec["theta"], (k, d, rec)
+        nrec += len(log)
+        if precision == "fp64" or err < 0:
+            st_iters = sum(sum(r["iters"]) for r in log)
+            assert g.stats()["cell_iters"] - getattr(g, "_it", 0) == st_iters
+            g._it = g.stats()["cell_iters"]
+        compare_state(g, st, *tols, tol_box=tol_box)
+    return g, st
+
+
+def test_fp64_sweeps_match_oracle_mix32(dd):
+    """Small Gaussian-mixture workload (32 x 32, s = 4, eps = (1/32)^2, lam = 1,
+    FP64, pi0 = mu x nu): three sweeps, sub-batch by sub-batch."""
+    mu, nu = inputs.mixture_small(N=32, seed=1000)
+    g, st = run_pair(dd, 32, 4, mu, nu, (1 / 32) ** 2, 1.0, 3, "fp64")
+    g.close()
+
+
+def test_fp64_ragged_partition_and_odd_cell_size(dd):
+    """N = 24, s = 3: B cells clipped at the border (1x1, 1x2, 2x1 basic cells),
+    odd cell sides, boxes that touch the grid edge."""
+    mu, nu = inputs.mixture_small(N=24, seed=1002)
+    g, st = run_pair(dd, 24, 3, mu, nu, (1 / 24) ** 2, 0.5, 2, "fp64")
+    g.close()
+
+
+@pytest.mark.parametrize("strategy", ["swift", "safe", "greedy"])
+def test_fp64_other_strategies(dd, strategy):
+    mu, nu = inputs.mixture_small(N=16, seed=1003)
+    g, st = run_pair(dd, 16, 2, mu, nu, (1 / 16) ** 2, 2.0, 2, "fp64", strategy=strategy)
+    g.close()
+
+
+def test_fp64_truncation_and_leniency(dd):
+    mu, nu = inputs.mixture_small(N=16, seed=1004)
+    g, st = run_pair(dd, 16, 2, mu, nu, (1 / 16) ** 2, 1.0, 3, "fp64", thr=1e-9, tau=0.005)
+    g.close()
+
+
+def test_fp64_warm_start_from_duals(dd):
+    """pi0 from global Sinkhorn duals at eps0 = 2 eps (Section 5.3 warm start);
+    the duals come from the oracle."""
+    N, s = 32, 4
+    mu, nu = inputs.mixture_small(N=N, seed=1005)
+    mu, nu = mu.ravel(), nu.ravel()
+    geo = odd.Geometry(N, s)
+    eps = (1 / N) ** 2
+    a0, b0, _, _ = uot.full_sinkhorn(mu, nu, odd.full_cost(geo), 2 * eps, 1.0, err=1e-6)
+    g, st = run_pair(dd, N, s, mu, nu, eps, 1.0, 2, "fp64", init_duals=(a0, b0, 2 * eps),
+                     tols=(1e-9, 1e-9, 1e-8))
+    g.close()
+
+
+def test_fp32_fixed_iterations_match_oracle(dd):
+    """FP32 cell arithmetic with exactly 12 cell iterations per solve: same
+    decisions; scores and marginals within FP32 error of the FP64 oracle."""
+    mu, nu = inputs.mixture_small(N=32, seed=1000)
+    g, st = run_pair(dd, 32, 4, mu, nu, (1 / 32) ** 2, 1.0, 2, "fp32", err=-1.0, maxit=12,
+                     tols=(1e-6, 1e-5, 1e-4), tol_box=None)
+    g.close()
+
+
+def test_fp32_converges_to_oracle_optimum(dd):
+    """DomDec in FP32 run to convergence reaches the unique UOT optimum computed
+    by the oracle's global Sinkhorn: relative score <= 1e-6, marginal L1 <= 1e-5."""
+    N, s = 32, 4
+    mu, nu = inputs.mixture_small(N=N, seed=1006)
+    mu, nu = mu.ravel(), nu.ravel()
+    geo = odd.Geometry(N, s)
+    eps, lam = (1 / N) ** 2, 1.0
+    C = odd.full_cost(geo)
+    a, b, it, gap = uot.full_sinkhorn(mu, nu, C, eps, lam, err=1e-12, maxit=20000)
+    pi = uot.plan(a, b, C, mu, nu, eps)
+    Eopt = uot.primal_score(pi, C, mu, nu, eps, lam)
+    g = dd.DomDec(mu, nu, eps, lam, s, precision="fp32", err=1e-10, maxit=400, tau=0.0)
+    g.iterate(30)
+    g.sync()
+    E = g.score()[0]
+    PX, PY = g.marginals()
+    assert abs(E - Eopt) <= 1e-6 * Eopt
+    assert np.abs(PX - pi.sum(1)).sum() <= 1e-5 * mu.sum()
+    assert np.abs(PY - pi.sum(0)).sum() <= 1e-5 * mu.sum()
+    cert = g.pd_gap()
+    assert 0 <= cert[2] < 1e-5
+    g.close()
+
+
+def test_certificate_matches_oracle(dd):
+    mu, nu = inputs.mixture_small(N=16, seed=1007)
+    g, st = run_pair(dd, 16, 2, mu, nu, (1 / 16) ** 2, 0.7, 2, "fp64")
+    P, D, rel, beta = odd.pd_certificate(st)
+    out, gb = g.pd_gap(with_beta=True)
+    assert abs(out[0] - P) <= 1e-10 * abs(P)
+    assert abs(out[1] - D) <= 1e-10 * abs(D)
+    assert np.abs(gb - beta).max() <= 1e-9 * (1 + np.abs(beta).max())
+    ex, ey = odd.marginal_errors(st, beta)
+    assert abs(out[3] - ex) <= 1e-9 and abs(out[4] - ey) <= 1e-9
+    g.close()
+
+
+@pytest.mark.parametrize("variant,precision,tol", [(1, 1, 1e-10), (0, 1, 1e-10), (1, 0, 2e-3), (0, 0, 2e-3)])
+def test_full_sinkhorn_matches_oracle(dd, variant, precision, tol):
+    """Global Sinkhorn (Eq. sinkhorn-iters-ot): separable and dense evaluation,
+    FP64 and FP32, against the oracle with the same iteration count."""
+    N = 16
+    mu, nu = inputs.mixture_small(N=N, seed=1008)
+    mu, nu = mu.ravel(), nu.ravel()
+    geo = odd.Geometry(N, 2)
+    eps, lam = (2 / N) ** 2, 1.5
+    a_ref, b_ref, it_ref, gap_ref = uot.full_sinkhorn(mu, nu, odd.full_cost(geo), eps, lam, err=-1, maxit=40)
+    alpha, beta = np.empty(N * N), np.empty(N * N)
+    it, gap, P, D, rc = dd.domdec_full_sinkhorn(mu, nu, N, eps, lam, variant=variant, precision=precision,
+                                                maxit=40, err=-1.0, check_every=40, alpha=alpha, beta=beta)
+    assert it == 40
+    scale = 1 + np.abs(a_ref).max()
+    assert np.abs(alpha - a_ref).max() <= tol * scale
+    assert np.abs(beta - b_ref).max() <= tol * scale
+    assert abs(gap - gap_ref) <= max(tol, 1e-12) * max(gap_ref, 1e-12) * (1 if precision else 1e3)
+    assert P >= D
+
+
+def test_error_states_are_reported_and_sticky(dd):
+    """A cell Y-box larger than the kernel capacity is reported by the kernel
+    (no fault), then the handle refuses further work."""
+    mu, nu = inputs.mixture_small(N=32, seed=1009)
+    g = dd.DomDec(mu, nu, (1 / 32) ** 2, 1.0, 4, precision="fp32", max_ny=256)
+    g.iterate(1)
+    with pytest.raises(dd.DomDecError) as e:
+        g.sync()
+    assert e.value.code == dd.DOMDEC_ETOOBIG
+    with pytest.raises(dd.DomDecError) as e:
+        g.iterate(1)
+    assert e.value.code == dd.DOMDEC_ESTATE
+    g.close()
+    bad = mu.copy()
+    bad[3] = -1.0
+    with pytest.raises(dd.DomDecError) as e:
+        dd.DomDec(bad, nu, (1 / 32) ** 2, 1.0, 4)
+    assert e.value.code == dd.DOMDEC_EINVAL
+
+
+def test_maxit_warning(dd):
+    mu, nu = inputs.mixture_small(N=16, seed=1010)
+    g = dd.DomDec(mu, nu, (1 / 16) ** 2, 1.0, 2, precision="fp32", err=1e-12, maxit=2)
+    g.iterate(1)
+    assert g.sync() == dd.DOMDEC_WNOTCONV
+    assert g.stats()["maxit_cells"] > 0
+    g.close()
