@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Benchmark of the DomDec hot path on one GB300 (or N independent replicas).
+
+Workload (``blobs256``): 256 x 256 grids, mu and nu seeded mixtures of 5..20
+Gaussian blobs with mass ratio in [0.7, 1.5], squared-Euclidean cost, lam = 1,
+eps-scaling from 1 to (1/256)^2 (global Sinkhorn warm start down to
+2 (1/256)^2, then DomDec at (1/256)^2), basic cells 8 x 8, FP32 cell Sinkhorn,
+FP64 score and step size, staggered strategy (swift on each sub-batch, no leniency), cell tolerance 2e-5.
+
+One step = one DomDec sweep over one partition (all staggered sub-batches:
+nu_{-J} gather, cell Sinkhorn, GetWeights, mixing and box refresh, arena
+compaction).  Metric: cell-iterations per second (one X-half + one Y-half on one
+composite cell).  Inputs are smaller than L2, so L2 is flushed (256 MB write)
+between timed steps, outside the timed events.
+
+Also reported: the roofline of the cell kernel (exp terms of its log-sum-exp
+passes against the MUFU ex2 rate), the time to a relative primal-dual gap of
+1e-5 against global Sinkhorn on the same GPU, an end-to-end number through the
+C ABI with host buffers, and the FP64 CPU oracle on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to stated primal-dual gap and cell-iters/s vs full Sinkhorn on one GB300"
+UNIT = "cell-iters/s"
+N_SM = 152
+MUFU_PER_SM_CLK = 16      # ex2/lg2 results per SM per clock (4 per SM sub-partition)
+GAP_TARGET = 1e-5
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def workload_inputs(rank=0):
+    from paper_2410_08859_gb300 import inputs
+    mu, nu, spec = inputs.workload("blobs256", instance=rank)
+    return mu.ravel().copy(), nu.ravel().copy(), spec
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    def __init__(self, out_path=None):
+        self.proc = None
+        self.path = out_path
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            dev = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0"
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={dev}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        rows = [r.split(",") for r in out.strip().splitlines() if r.strip()]
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def warm_start(dd, mu_d, nu_d, N, eps, lam, torch):
+    """Global Sinkhorn (separable, FP64) from eps = 1 down to 2 eps (Section 5.3
+    warm start at a quarter of the DomDec tolerance)."""
+    a = torch.empty(N * N, dtype=torch.float64, device="cuda")
+    b = torch.empty_like(a)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    it, gap, P, D, rc = dd.domdec_full_sinkhorn(mu_d, nu_d, N, 2 * eps, lam, eps_start=1.0,
+                                                variant=dd.SINKHORN_SEPARABLE, precision=dd.MIXED,
+                                                maxit=4000, err=2e-5 / 4, check_every=10, alpha=a, beta=b)
+    torch.cuda.synchronize()
+    return a, b, time.perf_counter() - t0, it
+
+
+def sinkhorn_to_gap(dd, mu_d, nu_d, N, eps, lam, variant, precision, torch, max_rounds=6, maxit=3000):
+    """Global Sinkhorn with eps-scaling from 1 to eps, tightening the PD tolerance
+    until the relative gap (E - D)/|D| <= GAP_TARGET.  Returns (seconds, gap, iterations)."""
+    b = torch.zeros(N * N, dtype=torch.float64, device="cuda")
+    a = torch.empty_like(b)
+    err = 2e-5
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tot = 0
+    it, gap, P, D, rc = dd.domdec_full_sinkhorn(mu_d, nu_d, N, eps, lam, eps_start=1.0, variant=variant,
+                                                precision=precision, maxit=maxit, err=err, check_every=10,
+                                                beta_in=b, alpha=a, beta=b)
+    tot += it
+    rel = (P - D) / abs(D)
+    rounds = 0
+    while not rel <= GAP_TARGET and rounds < max_rounds:
+        err /= 4
+        it, gap, P, D, rc = dd.domdec_full_sinkhorn(mu_d, nu_d, N, eps, lam, variant=variant,
+                                                    precision=precision, maxit=maxit, err=err,
+                                                    check_every=10, beta_in=b.clone(), alpha=a, beta=b)
+        tot += it
+        rel = (P - D) / abs(D)
+        rounds += 1
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0, rel, tot
+
+
+def domdec_to_gap(dd, mu_d, nu_d, N, s, eps, lam, a0, b0, t_warm, torch, max_sweeps=40):
+    """DomDec from the warm start until the certificate's relative gap reaches
+    GAP_TARGET; cell tolerance 1e-7 (the paper's 2e-5 stalls near 1.5e-4 on this
+    workload because inexact cell solves make greedy steps lose to the safe step)."""
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = dd.DomDec(mu_d, nu_d, eps, lam, s, alpha0=a0, beta0=b0, eps_init=2 * eps, precision="fp32",
+                  tau=0.0, err=1e-7, maxit=5000)
+    sweeps, rel = 0, float("inf")
+    while sweeps < max_sweeps:
+        g.iterate(2)
+        sweeps += 2
+        cert = g.pd_gap()
+        rel = cert[2]
+        if rel <= GAP_TARGET:
+            break
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    st = g.stats()
+    g.close()
+    return t + t_warm, t, rel, sweeps, st["cell_iters"]
+
+
+def oracle_sample(max_seconds=20.0, sweeps=None, maxit=None):
+    """The FP64 oracle on a bounded sample of the workload: the same blob
+    distribution and cell geometry (s = 8, composite cells of 16 x 16 pixels,
+    eps = h^2) on a 32 x 32 grid from the product plan; whole sweeps are timed
+    until max_seconds.  Returns (cell-iters/s, description, cell-iters, seconds)."""
+    from oracle import domdec as odd
+    from paper_2410_08859_gb300 import inputs
+    N, s = 32, 8
+    mu, nu = inputs.mixture_blobs(N=N, seed=2000)
+    mu, nu = mu.ravel(), nu.ravel()
+    geo = odd.Geometry(N, s)
+    st = odd.init_product(geo, mu, nu, (1.0 / N) ** 2, 1.0)
+    t0 = time.perf_counter()
+    its, k = 0, 0
+    while True:
+        lg = odd.sweep(st, "AB"[k % 2], "staggered", tau=0.005, err=2e-5, maxit=maxit or 2000)
+        its += sum(sum(r["iters"]) for r in lg)
+        k += 1
+        el = time.perf_counter() - t0
+        if (sweeps is not None and k >= sweeps) or (sweeps is None and el >= max_seconds):
+            break
+    desc = (f"oracle (NumPy FP64, 1 thread) DomDec sweeps on blobs 32x32, s=8 "
+            f"(composite cells 16x16 = the workload's cell size), eps=h^2, lam=1, pi0=mu x nu; "
+            f"{k} sweeps, {its} cell-iterations in {el:.1f} s")
+    return its / el, desc, its, el
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    vals = []
+    for w in range(args.warmup):
+        oracle_sample(sweeps=1, maxit=200)
+    t_all, its_all = 0.0, 0
+    for k in range(args.steps):
+        v, desc, its, el = oracle_sample(sweeps=1, maxit=200)
+        t_all += el
+        its_all += its
+        vals.append(v)
+    value = its_all / t_all
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * t_all / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "blobs256 (oracle sample: 32x32 grid, same cell geometry)",
+                       "lam": 1.0, "s": 8},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "one oracle sweep per step (cell maxit 200) on blobs 32x32, s=8"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=4)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--lam", type=float, default=1.0)
+    ap.add_argument("--no-extras", action="store_true", help="skip time-to-gap, e2e and CPU baseline")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2410_08859_gb300 import domdec as dd
+    dd.lib()
+
+    mu, nu, spec = workload_inputs(rank)
+    N, s, eps, lam = spec["N"], spec["s"], spec["eps"], args.lam
+    mu_d = torch.from_numpy(mu).cuda()
+    nu_d = torch.from_numpy(nu).cuda()
+    a0, b0, t_warm, it_warm = warm_start(dd, mu_d, nu_d, N, eps, lam, torch)
+
+    g = dd.DomDec(mu_d, nu_d, eps, lam, s, alpha0=a0, beta0=b0, eps_init=2 * eps, precision="fp32",
+                  tau=0.0, err=2e-5, profile=1)
+    g.iterate(args.warmup)
+    g.sync()
+    g.kernel_times(reset=True)
+    st0 = g.stats()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler() if rank == 0 else None
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        g.iterate(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    g.sync()
+    t_ms = sum(a.elapsed_time(b) for a, b in ev)
+    st1 = g.stats()
+    kms, kn = g.kernel_times(reset=True)
+    iters = st1["cell_iters"] - st0["cell_iters"]
+    terms = st1["lse_terms"] - st0["lse_terms"]
+    launches = int(kn.sum())
+    cert = g.pd_gap()
+    g.close()
+
+    tot = torch.tensor([float(iters), t_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        it_t = torch.tensor([float(iters)], dtype=torch.float64, device="cuda")
+        t_t = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(it_t, op=dist.ReduceOp.SUM)
+        dist.all_reduce(t_t, op=dist.ReduceOp.MAX)
+        tot = torch.stack([it_t[0], t_t[0]])
+    iters_all, t_max = float(tot[0]), float(tot[1])
+    value = iters_all / (t_max / 1000.0)
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    pk, pk_kind = peaks()
+    sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    peak_mufu = N_SM * MUFU_PER_SM_CLK * sm_mhz * 1e6 / 1e12   # T ex2/s
+    k1_s = kms[0] / 1000.0
+    achieved = (terms / k1_s) / 1e12 if k1_s > 0 else 0.0
+    roofline = {"bound": "alu", "kernel": "k_cell_solve<float>", "achieved": achieved, "peak": peak_mufu,
+                "unit": "Tex2/s", "frac": achieved / peak_mufu, "traffic": None,
+                "peak_source": f"{N_SM} SMs x {MUFU_PER_SM_CLK} MUFU/clk x {sm_mhz:.0f} MHz ({pk_kind} max clock)",
+                "kernel_share": float(kms[0] / max(kms.sum(), 1e-12)),
+                "kernel_ms": {"cell_solve": kms[0], "decide": kms[1], "apply": kms[2], "compact": kms[3]},
+                "launches": {"cell_solve": int(kn[0]), "decide": int(kn[1]), "apply": int(kn[2]),
+                             "compact": int(kn[3])}}
+
+    extras = {}
+    cpu = None
+    e2e = None
+    if not args.no_extras:
+        # time to the stated gap: DomDec (warm start + sweeps) vs global Sinkhorn on the same GPU
+        tt, t_dd, rel_dd, sw, its_dd = domdec_to_gap(dd, mu_d, nu_d, N, s, eps, lam, a0, b0, t_warm, torch)
+        t_sep, rel_sep, it_sep = sinkhorn_to_gap(dd, mu_d, nu_d, N, eps, lam, dd.SINKHORN_SEPARABLE, dd.FP64,
+                                                 torch)
+        t_dense, rel_dense, it_dense = sinkhorn_to_gap(dd, mu_d, nu_d, N, eps, lam, dd.SINKHORN_DENSE, dd.FP32,
+                                                       torch, max_rounds=1, maxit=400)
+        extras["time_to_gap"] = {
+            "target_rel_gap": GAP_TARGET,
+            "domdec_s": tt, "domdec_warm_start_s": t_warm, "domdec_sweeps_s": t_dd, "domdec_gap": rel_dd,
+            "domdec_sweeps": sw, "domdec_cell_iters": its_dd, "warm_start_sinkhorn_iters": it_warm,
+            "sinkhorn_separable_fp64_s": t_sep, "sinkhorn_separable_fp64_gap": rel_sep,
+            "sinkhorn_separable_fp64_iters": it_sep,
+            "sinkhorn_dense_fp32_s": t_dense, "sinkhorn_dense_fp32_gap": rel_dense,
+            "sinkhorn_dense_fp32_iters": it_dense}
+        # end to end through the C ABI with host buffers: init (H2D of mu, nu and the
+        # warm-start duals), one A and one B sweep, score and marginals back to the host
+        mu_h = torch.from_numpy(mu).pin_memory()
+        nu_h = torch.from_numpy(nu).pin_memory()
+        a_h = a0.cpu().pin_memory()
+        b_h = b0.cpu().pin_memory()
+        PX = torch.empty(N * N, dtype=torch.float64).pin_memory()
+        PY = torch.empty_like(PX)
+        n_e2e = 3
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its_e = 0
+        for _ in range(n_e2e):
+            ge = dd.DomDec(mu_h, nu_h, eps, lam, s, alpha0=a_h, beta0=b_h, eps_init=2 * eps, precision="fp32",
+                           tau=0.0)
+            ge.iterate(2)
+            ge.score()
+            dd.domdec_plan_marginals(ge.h, PX, PY)
+            its_e += ge.stats()["cell_iters"]
+            ge.close()
+        te = time.perf_counter() - t0
+        e2e = {"value": its_e / te, "unit": UNIT, "h2d_bytes_per_step": 4 * N * N * 8,
+               "d2h_bytes_per_step": 2 * N * N * 8 + 6 * 8,
+               "step": "domdec_init from host mu, nu, alpha0, beta0 + 2 sweeps + score + P_X, P_Y to host"}
+        v, desc, its, el = oracle_sample(max_seconds=15.0)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "blobs256", "N": N, "basic_cell": s, "eps": eps, "lam": lam,
+                       "eps_scaling": "1 -> 2 eps by global Sinkhorn (warm start), DomDec at eps",
+                       "strategy": "staggered", "tau": 0.0, "err": 2e-5, "precision": "fp32 cell / fp64 score",
+                       "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": launches, "cell_iters_timed": int(iters_all),
+            "final_rel_gap_after_timed_sweeps": float(cert[2])}
+    line.update(extras)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -53,6 +53,7 @@ extern "C" {
 
 #define DOMDEC_FP32 0        /* cell Sinkhorn arithmetic in float (state, score, decision stay double) */
 #define DOMDEC_FP64 1        /* cell Sinkhorn arithmetic in double */
+#define DOMDEC_MIXED 2       /* domdec_full_sinkhorn only: float for coarse eps stages, double for fine */
 
 typedef struct domdec_s* domdec_t;
 
@@ -72,6 +73,9 @@ typedef struct {
   int    max_ny;       /* capacity of a cell Y-box in the kernel (0: default 8192 for FP32, 4096 for FP64) */
   double arena_factor; /* box arena capacity in units of N*N doubles (0: default 48) */
   double eps_init;     /* eps of the warm-start duals passed to domdec_init (ignored without duals) */
+  int    profile;      /* 1: time every kernel of a sweep with CUDA events on the handle's stream */
+  int    spill_slots;  /* cells whose Y-box exceeds max_ny run from global memory slots: 0 = default
+                          (up to 4 GiB), > 0 = that many, < 0 = none (such cells fail with DOMDEC_ETOOBIG) */
 } domdec_params;
 
 typedef struct {
@@ -82,6 +86,7 @@ typedef struct {
   long long greedy_steps;    /* sub-batches that accepted theta = 1 */
   long long safe_steps;      /* sub-batches that fell back to theta = 1/|b| */
   long long box_entries;     /* stored entries of all nu_i (memory diagnostic, Section 5.3 "Sparsity") */
+  long long lse_terms;       /* exp terms of the cell log-sum-exp passes (algorithmic work of the cell kernel) */
   int       max_cell_iters;  /* largest iteration count of one cell solve */
   int       max_ny;          /* largest cell Y-box seen */
 } domdec_stats;
@@ -154,6 +159,20 @@ long long domdec_basic_marginals(domdec_t h, int* box, double* values, long long
  * the 4096 most recent.  Synchronises. */
 int domdec_decision_log(domdec_t h, double* out, int max_records);
 
+/* With params.profile = 1: accumulated device time (ms, CUDA events on the
+ * handle's stream) and launch counts of the sweep kernels since the last reset,
+ * per class: [0] cell solve (a1-a5), [1] step-size decision (a6),
+ * [2] mix / truncate / box refresh (a7), [3] arena compaction.
+ * reset != 0 clears the accumulators after reading.  Synchronises. */
+int domdec_kernel_times(domdec_t h, double ms[4], long long launches[4], int reset);
+
+/* Per-cell records of the most recent sub-batch (diagnostics): record j is
+ * out[8j..8j+7] = (k0, l0, H, W of the cell's Y-box B_J, cell Sinkhorn
+ * iterations, status (0 ok, 1 maxit, 2 empty, 3 too big, 4 non-finite), last
+ * PD/lam, spill slot or -1).  Returns the number of records (<= max_records).
+ * Synchronises. */
+int domdec_cell_log(domdec_t h, double* out, int max_records);
+
 /* Counters since domdec_init.  Synchronises. */
 int domdec_get_stats(domdec_t h, domdec_stats* s);
 
@@ -169,7 +188,8 @@ const char* domdec_error_string(int code);
  *             DOMDEC_SINKHORN_SEPARABLE : the same update evaluated as two 1-D
  *                                         log-sum-exp passes (|x-y|^2 separates
  *                                         over the axes), O(N^3) per half-step
- *   precision DOMDEC_FP32 | DOMDEC_FP64
+ *   precision DOMDEC_FP32 | DOMDEC_FP64 | DOMDEC_MIXED (float stages while
+ *             eps >= 64 h^2, double below)
  *   eps_start >= eps: geometric eps-scaling eps_start, eps_start/2, ... eps;
  *   at each stage iterate until PD/lam <= err*|mu| (Eq. PD-gap-KL, tested every
  *   check_every iterations) or maxit iterations.

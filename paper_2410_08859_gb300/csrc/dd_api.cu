@@ -65,9 +65,16 @@ struct domdec_s {
   long long sweeps = 0;
   long long slot = 0;
   int sticky = 0;
+  int last_batch = 0;
   // graphs: one sweep per partition
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   bool graph_ok = true;
+  // profiling: pending event pairs per kernel class
+  struct EvPair { cudaEvent_t a, b; int cls; };
+  std::vector<EvPair> pend;
+  std::vector<cudaEvent_t> pool;
+  double kt[4] = {0, 0, 0, 0};
+  long long kn[4] = {0, 0, 0, 0};
 };
 
 namespace {
@@ -129,10 +136,12 @@ int check_params(const domdec_params* p, int N) {
 }
 
 int read_status(domdec_s* h) {
-  cudaError_t e = cudaMemcpyAsync(h->h_pinned, h->S.status, sizeof(int), cudaMemcpyDeviceToHost, h->st);
+  // slot 63 of the pinned buffer is reserved for the status word
+  int* hs = reinterpret_cast<int*>(h->h_pinned + 63);
+  cudaError_t e = cudaMemcpyAsync(hs, h->S.status, sizeof(int), cudaMemcpyDeviceToHost, h->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
   if (e != cudaSuccess) return fail(h, DOMDEC_ECUDA);
-  int st = *reinterpret_cast<int*>(h->h_pinned);
+  int st = *hs;
   if (st & ST_BADINPUT) return fail(h, DOMDEC_EINVAL);
   if (st & ST_TOOBIG) return fail(h, DOMDEC_ETOOBIG);
   if (st & ST_ARENA) return fail(h, DOMDEC_EARENA);
@@ -165,6 +174,46 @@ int ensure_arena(domdec_s* h) {
   return DOMDEC_OK;
 }
 
+cudaEvent_t take_event(domdec_s* h) {
+  if (!h->pool.empty()) {
+    cudaEvent_t e = h->pool.back();
+    h->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Record a start event (profiling only); returns it, or nullptr.
+cudaEvent_t prof_begin(domdec_s* h) {
+  if (!h->p.profile) return nullptr;
+  cudaEvent_t a = take_event(h);
+  cudaEventRecord(a, h->st);
+  return a;
+}
+
+void prof_end(domdec_s* h, cudaEvent_t a, int cls) {
+  if (!a) return;
+  cudaEvent_t b = take_event(h);
+  cudaEventRecord(b, h->st);
+  h->pend.push_back({a, b, cls});
+}
+
+// Fold finished event pairs into the accumulators (after a synchronisation).
+void prof_collect(domdec_s* h) {
+  for (auto& ev : h->pend) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ev.a, ev.b) == cudaSuccess) {
+      h->kt[ev.cls] += ms;
+      h->kn[ev.cls] += 1;
+    }
+    h->pool.push_back(ev.a);
+    h->pool.push_back(ev.b);
+  }
+  h->pend.clear();
+}
+
 // Enqueue one sweep of partition `part`.
 int enqueue_sweep(domdec_s* h, int part, long long slot0) {
   const int prec = h->p.precision;
@@ -179,11 +228,20 @@ int enqueue_sweep(domdec_s* h, int part, long long slot0) {
     const int begin = bt.first, nbt = bt.second - bt.first;
     if (nbt <= 0) continue;
     const int slot = (int)((slot0 + k++) % LOGCAP);
+    cudaEvent_t ev = prof_begin(h);
     if (launch_cell_solve(h->S, h->d_cells[part], begin, nbt, prec, h->st) != cudaSuccess) return DOMDEC_ECUDA;
+    prof_end(h, ev, 0);
+    ev = prof_begin(h);
     if (launch_decide(h->S, h->d_cells[part], begin, nbt, slot, h->st) != cudaSuccess) return DOMDEC_ECUDA;
+    prof_end(h, ev, 1);
+    ev = prof_begin(h);
     if (launch_apply(h->S, h->d_cells[part], begin, nbt, h->st) != cudaSuccess) return DOMDEC_ECUDA;
+    prof_end(h, ev, 2);
+    h->last_batch = nbt;
   }
+  cudaEvent_t ev = prof_begin(h);
   if (launch_compact(h->S, h->d_newoff, h->st) != cudaSuccess) return DOMDEC_ECUDA;
+  prof_end(h, ev, 3);
   return DOMDEC_OK;
 }
 
@@ -235,6 +293,8 @@ const char* domdec_error_string(int code) {
 void domdec_free(domdec_t h) {
   if (!h) return;
   cudaStreamSynchronize(h->st);
+  prof_collect(h);
+  for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
   for (int k = 0; k < 2; ++k)
     if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
   for (void* q : h->allocs)
@@ -318,6 +378,23 @@ int domdec_init(domdec_t* out, const double* mu, const double* nu, int N, const 
   DD_ALLOC(S.theta, 1); DD_ALLOC(S.declog, 4 * LOGCAP); DD_ALLOC(S.counters, NCOUNT);
   DD_ALLOC(S.status, 1); DD_ALLOC(S.red, 2 * 152 * 5 + 8); DD_ALLOC(S.red_count, 1);
   DD_ALLOC(h->d_newoff, h->nbasic + 1); DD_ALLOC(h->d_scratch, 64); DD_ALLOC(h->d_numom, 8);
+  {
+    // spill slots for cell boxes beyond the shared-memory capacity: Y-side arrays
+    // (4 s N + 5 N^2 values) followed by 4 N^2 doubles of new marginals
+    const size_t rs = pin->precision ? sizeof(double) : sizeof(float);
+    size_t ybytes = rs * (4 * (size_t)h->s * N + 5 * (size_t)n);
+    ybytes = (ybytes + 255) / 256 * 256;
+    const size_t stride = ybytes + 4 * (size_t)n * sizeof(double);
+    const size_t budget = (size_t)4 << 30;  // at most 4 GiB of slots
+    int slots = (int)std::min<size_t>((size_t)std::max(1, mb), std::max<size_t>(1, budget / stride));
+    if (pin->spill_slots > 0) slots = pin->spill_slots;
+    if (pin->spill_slots < 0) slots = 0;
+    S.spill_stride = (long long)stride;
+    S.spill_nut_off = (long long)ybytes;
+    S.spill_slots = slots;
+    DD_ALLOC(S.spill, stride * std::max(slots, 1));
+    DD_ALLOC(S.spill_count, 1);
+  }
   S.mu = dmu; S.nu = dnu; S.logmu = dlogmu; S.lognu = dlognu; S.muinu = dmuinu;
   if (cudaMallocHost(&h->h_pinned, 64 * sizeof(double)) != cudaSuccess) { domdec_free(h); return DOMDEC_ENOMEM; }
   cudaStream_t st = h->st;
@@ -328,6 +405,7 @@ int domdec_init(domdec_t* out, const double* mu, const double* nu, int N, const 
   cudaMemsetAsync(S.head, 0, sizeof(unsigned long long), st);
   cudaMemsetAsync(S.counters, 0, NCOUNT * sizeof(unsigned long long), st);
   cudaMemsetAsync(S.red_count, 0, sizeof(unsigned int), st);
+  cudaMemsetAsync(S.spill_count, 0, sizeof(unsigned int), st);
   cudaMemsetAsync(S.dPY, 0, n * sizeof(double), st);
   cudaMemsetAsync(S.PY, 0, n * sizeof(double), st);
   cudaMemsetAsync(S.theta, 0, sizeof(double), st);
@@ -511,6 +589,19 @@ long long domdec_basic_marginals(domdec_t h, int* box, double* values, long long
   return total;
 }
 
+int domdec_kernel_times(domdec_t h, double ms[4], long long launches[4], int reset) {
+  if (!h || !ms || !launches) return DOMDEC_EINVAL;
+  if (h->sticky) return DOMDEC_ESTATE;
+  if (cudaStreamSynchronize(h->st) != cudaSuccess) return fail(h, DOMDEC_ECUDA);
+  prof_collect(h);
+  for (int k = 0; k < 4; ++k) {
+    ms[k] = h->kt[k];
+    launches[k] = h->kn[k];
+    if (reset) { h->kt[k] = 0.0; h->kn[k] = 0; }
+  }
+  return read_status(h);
+}
+
 int domdec_decision_log(domdec_t h, double* out, int max_records) {
   if (!h || !out || max_records < 0) return DOMDEC_EINVAL;
   if (h->sticky) return DOMDEC_ESTATE;
@@ -523,6 +614,22 @@ int domdec_decision_log(domdec_t h, double* out, int max_records) {
   for (int k = 0; k < cnt; ++k) {
     const long long rec = h->slot - cnt + k;
     for (int j = 0; j < 4; ++j) out[4 * k + j] = all[4 * (rec % LOGCAP) + j];
+  }
+  return cnt;
+}
+
+int domdec_cell_log(domdec_t h, double* out, int max_records) {
+  if (!h || !out || max_records < 0) return DOMDEC_EINVAL;
+  if (h->sticky) return DOMDEC_ESTATE;
+  const int cnt = std::min(h->last_batch, max_records);
+  std::vector<CellOut> rec(std::max(cnt, 1));
+  if (cudaStreamSynchronize(h->st) != cudaSuccess ||
+      (cnt && cudaMemcpy(rec.data(), h->S.cout, cnt * sizeof(CellOut), cudaMemcpyDeviceToHost) != cudaSuccess))
+    return fail(h, DOMDEC_ECUDA);
+  for (int j = 0; j < cnt; ++j) {
+    const CellOut& o = rec[j];
+    double* r = out + 8 * j;
+    r[0] = o.k0; r[1] = o.l0; r[2] = o.H; r[3] = o.W; r[4] = o.iters; r[5] = o.status; r[6] = o.gap; r[7] = o.slot;
   }
   return cnt;
 }
@@ -542,6 +649,7 @@ int domdec_get_stats(domdec_t h, domdec_stats* s) {
   s->maxit_cells = (long long)c[2];
   s->greedy_steps = (long long)c[3];
   s->safe_steps = (long long)c[4];
+  s->lse_terms = (long long)c[7];
   s->max_cell_iters = (int)c[5];
   s->max_ny = (int)c[6];
   s->box_entries = (long long)h->h_pinned[4];
@@ -552,7 +660,7 @@ int domdec_full_sinkhorn(const double* mu, const double* nu, int N, double eps_s
                          int variant, int precision, int maxit, double err, int check_every,
                          const double* beta_in, double* alpha, double* beta, double out[4], void* stream) {
   if (!mu || !nu || !out || N <= 0) return DOMDEC_EINVAL;
-  if (!(eps > 0.0) || !(lambda > 0.0) || (variant != 0 && variant != 1) || (precision != 0 && precision != 1) ||
+  if (!(eps > 0.0) || !(lambda > 0.0) || (variant != 0 && variant != 1) || precision < 0 || precision > 2 ||
       maxit < 1)
     return DOMDEC_EINVAL;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

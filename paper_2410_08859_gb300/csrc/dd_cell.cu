@@ -104,7 +104,7 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbat
 
   // ---------------------------------------------------------------- B_J
   if (tid == 0) {
-    int k0 = 1 << 30, l0 = 1 << 30, k1 = -1, l1 = -1;
+    int k0 = 1 << 30, l0 = 1 << 30, k1 = -1, l1 = -1, slot = -1;
     for (int q = 0; q < 4; ++q) {
       BoxRec b = {0, 0, 0, 0, 0};
       if (cd.mem[q] >= 0) b = S.box[cd.mem[q]];
@@ -121,9 +121,14 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbat
       k0 = max(0, k0 - S.margin); l0 = max(0, l0 - S.margin);
       k1 = min(N, k1 + S.margin); l1 = min(N, l1 + S.margin);
       int H = k1 - k0, W = l1 - l0;
-      if (H * W > S.cap_ny || H > S.cap_side || W > S.cap_side) st = CELL_TOOBIG;
+      // boxes beyond the shared-memory capacity run from a global spill slot
+      if (H * W > S.cap_ny || H > S.cap_side || W > S.cap_side) {
+        int sl = S.spill_slots > 0 ? (int)atomicAdd(S.spill_count, 1u) : S.spill_slots;
+        if (sl >= S.spill_slots) st = CELL_TOOBIG;
+        else slot = sl;
+      }
     }
-    sgeo[0] = k0; sgeo[1] = l0; sgeo[2] = k1 - k0; sgeo[3] = l1 - l0; sgeo[4] = st;
+    sgeo[0] = k0; sgeo[1] = l0; sgeo[2] = k1 - k0; sgeo[3] = l1 - l0; sgeo[4] = st; sgeo[7] = slot;
   }
   __syncthreads();
   const int k0 = sgeo[0], l0 = sgeo[1], H = sgeo[2], W = sgeo[3];
@@ -131,7 +136,7 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbat
     if (tid == 0) {
       CellOut o;
       o.k0 = k0; o.l0 = l0; o.H = H; o.W = W; o.iters = 0; o.status = sgeo[4];
-      o.D1 = o.D2 = 0; o.gap = 0.0; o.dKX[0] = o.dKX[1] = 0.0;
+      o.D1 = o.D2 = 0; o.gap = 0.0; o.dKX[0] = o.dKX[1] = 0.0; o.slot = -1; o.pad = 0;
       for (int q = 0; q < 4; ++q) {
         int bi = cd.mem[q];
         o.Ct[q] = bi >= 0 ? S.Cc[bi] : 0.0;
@@ -146,13 +151,20 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbat
   const int ny = H * W;
 
   // ------------------------------------------------------- shared layout
-  const int cap_nx = 4 * s * s, tsz = 2 * s * S.cap_side, cap_ny = S.cap_ny;
+  // X-side arrays always live in shared memory; the Y-side arrays too unless
+  // the box exceeds the shared capacity, then in this block's spill area
+  // (global memory, L2-resident) sized for an N x N box.
+  const int cap_nx = 4 * s * s;
+  const int slot = sgeo[7];
+  const bool spilled = slot >= 0;
+  const int tsz = spilled ? 2 * s * N : 2 * s * S.cap_side;
+  const int cap_ny = spilled ? N * N : S.cap_ny;
   R* xa = reinterpret_cast<R*>(smem_raw + 32 * 16 * sizeof(double));
   R* av = xa + cap_nx;
   R* g0 = av + cap_nx;
   R* Wv = g0 + cap_nx;
   R* lm = Wv + cap_nx;
-  R* T = lm + cap_nx;
+  R* T = spilled ? reinterpret_cast<R*>(S.spill + (long long)slot * S.spill_stride) : lm + cap_nx;
   R* U = T + tsz;
   R* bl = U + tsz;
   R* lrho = bl + cap_ny;
@@ -161,8 +173,30 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbat
   R* lnu = bv + cap_ny;
 
   // ------------------------------------------------------- frame constants
+  // Y frame origin: the pixel nearest to the barycentre of the cell's current
+  // Y-marginal nu_J, so that 2 q D.xi carries the cell's mean displacement.
+  {
+    double m3[3] = {0.0, 0.0, 0.0};
+    for (int u = tid; u < ny; u += nthr) {
+      int kk = u / W, ll = u - kk * W;
+      double v = 0.0;
+#pragma unroll
+      for (int q4 = 0; q4 < 4; ++q4) v += box_value(sbox[q4], arena, k0 + kk, l0 + ll);
+      m3[0] += v; m3[1] += v * kk; m3[2] += v * ll;
+    }
+    block_sum<3>(m3, red);
+    if (tid == 0) {
+      int c1 = H / 2, c2 = W / 2;
+      if (m3[0] > 0.0) {
+        c1 = min(H - 1, max(0, (int)lrint(m3[1] / m3[0])));
+        c2 = min(W - 1, max(0, (int)lrint(m3[2] / m3[0])));
+      }
+      sgeo[5] = c1; sgeo[6] = c2;
+    }
+    __syncthreads();
+  }
   const int xc1 = cd.i0 + nx1 / 2, xc2 = cd.j0 + nx2 / 2;
-  const int yc1 = k0 + H / 2, yc2 = l0 + W / 2;
+  const int yc1 = k0 + sgeo[5], yc2 = l0 + sgeo[6];
   const int D1 = xc1 - yc1, D2 = xc2 - yc2;
   const int offr = (k0 - cd.i0) + D1, offc = (l0 - cd.j0) + D2;
   const double eps = S.eps, lam = S.lam;
@@ -300,7 +334,13 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbat
 #pragma unroll
   for (int k = 0; k < 12; ++k) hs[k] = 0.0;
   const int nhr = nx1 > s ? 2 : 1, nhc = nx2 > s ? 2 : 1;
-  double* nut = S.nut + (long long)blockIdx.x * 4 * cap_ny;
+  int nst;
+  double* nut;
+  {
+    CellOut tmp;
+    tmp.slot = slot;
+    nut = cell_nut(S, tmp, blockIdx.x, &nst);
+  }
   R* Te = T;                 // epilogue scratch spans T, U, bl, lrho, Zv
   R* Ma = T + nx1 * W;
   R* Md = Ma + nx1 * W;
@@ -348,7 +388,7 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbat
         R isw = R(1) / sw;
         const int qd = 2 * hr + hc;
         double nt = nuy * exp((double)bv[u] + (double)P2 * DD_LN2);
-        nut[qd * cap_ny + u] = nt;
+        nut[qd * nst + u] = nt;
         hs[qd] += nt * ((double)(sa * isw) + (double)bv[u]);
         hs[4 + qd] += h2 * nt * (double)(sd * isw);
         hs[8 + qd] += nt;
@@ -366,7 +406,7 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbat
       if (cd.mem[q4] < 0) continue;
       int hr = q4 >> 1, hc = q4 & 1;
       if (hr >= nhr || hc >= nhc) continue;
-      dlt += nut[q4 * cap_ny + u] - box_value(sbox[q4], arena, y1, y2);
+      dlt += nut[q4 * nst + u] - box_value(sbox[q4], arena, y1, y2);
     }
     if (dlt != 0.0) atomicAdd(S.dPY + y1 * N + y2, dlt);
   }
@@ -377,6 +417,7 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbat
     o.iters = it;
     o.status = nonfinite ? CELL_NONFINITE : ((S.err >= 0.0 && gap > tol) ? CELL_MAXIT : CELL_OK);
     o.D1 = D1; o.D2 = D2;
+    o.slot = slot; o.pad = 0;
     o.gap = gap;
     o.dKX[0] = dk[0]; o.dKX[1] = dk[1];
     for (int q4 = 0; q4 < 4; ++q4) {
@@ -391,6 +432,8 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbat
     if (o.status == CELL_MAXIT) atomicAdd(S.counters + 2, 1ull);
     atomicMax(S.counters + 5, (unsigned long long)it);
     atomicMax(S.counters + 6, (unsigned long long)ny);
+    atomicAdd(S.counters + 7, (unsigned long long)it *
+                                  (unsigned long long)(nx1 * W * nx2 + H * W * nx1 + H * nx2 * W + nx * H));
     if (nonfinite) atomicOr(S.status, ST_NONFINITE);
   }
 }

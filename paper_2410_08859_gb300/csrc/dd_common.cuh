@@ -26,10 +26,14 @@ struct CellDesc {
 struct CellOut {
   int k0, l0, H, W;      // the cell's Y box B_J
   int iters, status, D1, D2;
+  int slot, pad;         // spill slot of an oversized box (-1: none)
   double Ct[4], Ht[4], mass[4];  // per quadrant: <c, pi~_i>, KL(pi~_i | mu_i x nu), |nu~_i|
   double dKX[2];         // sum_{x in X_J} [mu phi(P'/mu) - mu phi(P/mu)] for theta = 1 and theta_safe
   double gap;            // last PD/lam of the cell
 };
+
+// New marginals of cell position j of the current launch (quadrant stride in *stride).
+__device__ __forceinline__ double* cell_nut(const struct DevState& S, const CellOut& o, int j, int* stride);
 
 // Basic-cell box: Y rows [k0, k0+H), columns [l0, l0+W), values at arena[off..].
 struct BoxRec {
@@ -43,6 +47,11 @@ struct DevState {
   double h, eps, lam, thr, err, tau;
   int maxit, newton_maxit, strategy, margin;
   int cap_ny, cap_side;
+  unsigned char* spill;         // spill slots: Y-side arrays and new marginals of cells too large
+  long long spill_stride;       //   for shared memory (bytes per slot)
+  long long spill_nut_off;      //   byte offset of the new marginals (4 N^2 doubles) inside a slot
+  int spill_slots;              //   number of slots
+  unsigned int* spill_count;    //   slots taken in the current launch (reset by k_decide)
   const double *mu, *nu, *logmu, *lognu;
   double* muinu;                // muinu[i] = |mu_i| |nu|
   double *alpha, *PX, *PY, *PXnew, *dPY;
@@ -56,7 +65,8 @@ struct DevState {
   double* nut;                  // per cell position: 4 * cap_ny new marginals
   double* theta;                // device scalar: last theta
   double* declog;               // per sub-batch: E0, E(1), E(safe), theta
-  unsigned long long* counters; // 0 cell_iters, 1 cell_solves, 2 maxit cells, 3 greedy, 4 safe, 5 max iters, 6 max ny
+  unsigned long long* counters; // 0 cell_iters, 1 cell_solves, 2 maxit cells, 3 greedy, 4 safe, 5 max iters,
+                                // 6 max ny, 7 lse terms
   int* status;
   double* red;                  // reduction scratch
   unsigned int* red_count;
@@ -140,4 +150,13 @@ __device__ __forceinline__ void block_sum(double (&v)[K], double* scratch) {
     v[k] = a;
   }
   __syncthreads();
+}
+
+__device__ __forceinline__ double* cell_nut(const DevState& S, const CellOut& o, int j, int* stride) {
+  if (o.slot >= 0) {
+    *stride = S.N * S.N;
+    return reinterpret_cast<double*>(S.spill + (long long)o.slot * S.spill_stride + S.spill_nut_off);
+  }
+  *stride = S.cap_ny;
+  return S.nut + (long long)j * 4 * S.cap_ny;
 }

@@ -12,6 +12,10 @@
 
 namespace {
 
+// Terms more than `cut` (log2 units) below the maximum are skipped: at most N
+// of them change the sum by N 2^-cut relative (< 1e-15 in double, < 1e-7 in float).
+template <typename R> __device__ __forceinline__ R cut_log2() { return sizeof(R) == 4 ? R(32) : R(64); }
+
 // out[k*N + j] = log2 sum_l 2^{in[k*N + l] - q2 (j - l)^2}   (one block row k, threads over j)
 template <typename R>
 __global__ void __launch_bounds__(256) k_sep_rows(const R* __restrict__ in, R* __restrict__ out, int N, R q2) {
@@ -20,12 +24,17 @@ __global__ void __launch_bounds__(256) k_sep_rows(const R* __restrict__ in, R* _
   const int k = blockIdx.x;
   for (int l = threadIdx.x; l < N; l += blockDim.x) row[l] = in[(long long)k * N + l];
   __syncthreads();
+  const R cut = cut_log2<R>();
   for (int j = threadIdx.x; j < N; j += blockDim.x) {
     R mx = -dd_inf<R>();
     for (int l = 0; l < N; ++l) { R d = R(j - l); mx = max(mx, row[l] - q2 * d * d); }
     R acc = R(0);
     if (mx > -dd_inf<R>())
-      for (int l = 0; l < N; ++l) { R d = R(j - l); acc += dd_ex2(row[l] - q2 * d * d - mx); }
+      for (int l = 0; l < N; ++l) {
+        R d = R(j - l);
+        R v = row[l] - q2 * d * d - mx;
+        if (v > -cut) acc += dd_ex2(v);
+      }
     out[(long long)k * N + j] = mx + dd_lg2(acc);
   }
 }
@@ -36,11 +45,16 @@ __global__ void __launch_bounds__(256) k_sep_cols(const R* __restrict__ in, R* _
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = blockIdx.y;
   if (j >= N) return;
+  const R cut = cut_log2<R>();
   R mx = -dd_inf<R>();
   for (int k = 0; k < N; ++k) { R d = R(i - k); mx = max(mx, in[(long long)k * N + j] - q2 * d * d); }
   R acc = R(0);
   if (mx > -dd_inf<R>())
-    for (int k = 0; k < N; ++k) { R d = R(i - k); acc += dd_ex2(in[(long long)k * N + j] - q2 * d * d - mx); }
+    for (int k = 0; k < N; ++k) {
+      R d = R(i - k);
+      R v = in[(long long)k * N + j] - q2 * d * d - mx;
+      if (v > -cut) acc += dd_ex2(v);
+    }
   out[(long long)i * N + j] = mx + dd_lg2(acc);
 }
 
@@ -242,6 +256,28 @@ int full_sinkhorn_dev(const double* mu, const double* nu, const double* logmu, c
                       double eps_start, double eps, double lam, int variant, int precision, int maxit,
                       double err, int check_every, double* alpha, double* beta, double* out, double* d_eval,
                       cudaStream_t st, cudaError_t* cerr) {
+  if (precision == 2) {
+    // float stages while eps >= 64 h^2 (|pot|/eps small enough for float), then double
+    const double h = 1.0 / N, e_sw = 64.0 * h * h;
+    double o1[4] = {0, 0, 0, 0};
+    long long its = 0;
+    if (eps_start > e_sw && eps < e_sw) {
+      double e_end = e_sw;
+      // last float stage is the first eps of the halving sequence below e_sw's bound
+      double e = eps_start;
+      while (e * 0.5 >= e_sw) e *= 0.5;
+      e_end = e;
+      int r = full_sinkhorn_impl<float>(mu, nu, logmu, lognu, N, eps_start, e_end, lam, variant, maxit, err,
+                                        check_every, alpha, beta, o1, d_eval, st, cerr);
+      if (r < 0) return r;
+      its += (long long)o1[0];
+      int r2 = full_sinkhorn_impl<double>(mu, nu, logmu, lognu, N, 0.5 * e_end, eps, lam, variant, maxit, err,
+                                          check_every, alpha, beta, out, d_eval, st, cerr);
+      out[0] += (double)its;
+      return r2;
+    }
+    precision = eps < e_sw ? 1 : 0;
+  }
   if (precision)
     return full_sinkhorn_impl<double>(mu, nu, logmu, lognu, N, eps_start, eps, lam, variant, maxit, err,
                                       check_every, alpha, beta, out, d_eval, st, cerr);

@@ -67,6 +67,7 @@ k_decide(DevState S, const CellDesc* __restrict__ cells, int begin, int nbatch, 
   lg[0] = E0; lg[1] = Eg; lg[2] = Es; lg[3] = theta;
   atomicAdd(S.counters + (theta == 1.0 ? 3 : 4), 1ull);
   *S.red_count = 0u;
+  if (S.spill_count) *S.spill_count = 0u;
 }
 
 // ================================================================= apply (a7)
@@ -82,7 +83,8 @@ k_apply(DevState S, const CellDesc* __restrict__ cells, int begin) {
   const double th = *S.theta, thr = S.thr;
   const int N = S.N, H = o.H, W = o.W, ny = H * W;
   double* arena = S.arena[*S.cur];
-  const double* nut = S.nut + (long long)blockIdx.x * 4 * S.cap_ny;
+  int nst;
+  const double* nut = cell_nut(S, o, blockIdx.x, &nst);
   const int tid = threadIdx.x;
   if (tid < 4) {
     BoxRec b = {0, 0, 0, 0, 0};
@@ -104,7 +106,7 @@ k_apply(DevState S, const CellDesc* __restrict__ cells, int begin) {
       const BoxRec& b = ob[q];
       int a = y1 - b.k0, c = y2 - b.l0;
       double old = (a >= 0 && c >= 0 && a < b.H && c < b.W) ? arena[b.off + (long long)a * b.W + c] : 0.0;
-      double v = (1.0 - th) * old + th * nut[q * S.cap_ny + u];
+      double v = (1.0 - th) * old + th * nut[q * nst + u];
       if (v < thr) v = 0.0;
       dl += v - old;
       if (v > 0.0) {
@@ -159,7 +161,7 @@ k_apply(DevState S, const CellDesc* __restrict__ cells, int begin) {
       int y1 = nk0 + a, y2 = nl0 + c;
       int oa = y1 - b.k0, oc = y2 - b.l0;
       double old = (oa >= 0 && oc >= 0 && oa < b.H && oc < b.W) ? arena[b.off + (long long)oa * b.W + oc] : 0.0;
-      double v = (1.0 - th) * old + th * nut[q * S.cap_ny + (y1 - o.k0) * W + (y2 - o.l0)];
+      double v = (1.0 - th) * old + th * nut[q * nst + (y1 - o.k0) * W + (y2 - o.l0)];
       if (v < thr) v = 0.0;
       arena[noff[q] + u] = v;
     }

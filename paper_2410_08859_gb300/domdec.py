@@ -19,7 +19,7 @@ DOMDEC_EINVAL, DOMDEC_ENOMEM, DOMDEC_ECUDA = -1, -2, -3
 DOMDEC_ETOOBIG, DOMDEC_EARENA, DOMDEC_ESTATE, DOMDEC_ENOLIB = -4, -5, -6, -7
 STAGGERED, SWIFT, SAFE, GREEDY = 0, 1, 2, 3
 STRATEGIES = {"staggered": STAGGERED, "swift": SWIFT, "safe": SAFE, "greedy": GREEDY}
-FP32, FP64 = 0, 1
+FP32, FP64, MIXED = 0, 1, 2
 SINKHORN_DENSE, SINKHORN_SEPARABLE = 0, 1
 
 
@@ -36,14 +36,16 @@ class domdec_params(ctypes.Structure):
                 ("strategy", ctypes.c_int), ("maxit", ctypes.c_int),
                 ("newton_maxit", ctypes.c_int), ("precision", ctypes.c_int),
                 ("box_margin", ctypes.c_int), ("max_ny", ctypes.c_int),
-                ("arena_factor", ctypes.c_double), ("eps_init", ctypes.c_double)]
+                ("arena_factor", ctypes.c_double), ("eps_init", ctypes.c_double),
+                ("profile", ctypes.c_int), ("spill_slots", ctypes.c_int)]
 
 
 class domdec_stats(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_longlong), ("cell_solves", ctypes.c_longlong),
                 ("cell_iters", ctypes.c_longlong), ("maxit_cells", ctypes.c_longlong),
                 ("greedy_steps", ctypes.c_longlong), ("safe_steps", ctypes.c_longlong),
-                ("box_entries", ctypes.c_longlong), ("max_cell_iters", ctypes.c_int),
+                ("box_entries", ctypes.c_longlong), ("lse_terms", ctypes.c_longlong),
+                ("max_cell_iters", ctypes.c_int),
                 ("max_ny", ctypes.c_int)]
 
     def as_dict(self):
@@ -69,6 +71,8 @@ _SIGS = {
     "domdec_basic_marginals": (ctypes.c_longlong, [_P, ctypes.POINTER(ctypes.c_int), _P, ctypes.c_longlong]),
     "domdec_get_stats": (_I, [_P, ctypes.POINTER(domdec_stats)]),
     "domdec_decision_log": (_I, [_P, _DP, _I]),
+    "domdec_kernel_times": (_I, [_P, _DP, ctypes.POINTER(ctypes.c_longlong), _I]),
+    "domdec_cell_log": (_I, [_P, _DP, _I]),
     "domdec_free": (None, [_P]),
     "domdec_error_string": (ctypes.c_char_p, [_I]),
     "domdec_full_sinkhorn": (_I, [_P, _P, _I, _D, _D, _D, _I, _I, _I, _D, _I, _P, _P, _P, _DP, _P]),
@@ -211,6 +215,21 @@ def domdec_decision_log(h, max_records=4096):
     return np.array(out[:4 * cnt]).reshape(cnt, 4)
 
 
+def domdec_kernel_times(h, reset=True):
+    """(ms[4], launches[4]) per kernel class: cell solve, decision, apply, compaction."""
+    ms = (ctypes.c_double * 4)()
+    n = (ctypes.c_longlong * 4)()
+    _check(lib().domdec_kernel_times(h, ms, n, int(reset)), "domdec_kernel_times")
+    return np.array(ms[:]), np.array(n[:])
+
+
+def domdec_cell_log(h, max_records=4096):
+    """(n, 8) array per cell of the last sub-batch: k0, l0, H, W, iters, status, gap, spill slot."""
+    out = (ctypes.c_double * (8 * max_records))()
+    cnt = _check(lib().domdec_cell_log(h, out, int(max_records)), "domdec_cell_log")
+    return np.array(out[:8 * cnt]).reshape(cnt, 8)
+
+
 def domdec_get_stats(h):
     s = domdec_stats()
     _check(lib().domdec_get_stats(h, ctypes.byref(s)), "domdec_get_stats")
@@ -288,6 +307,12 @@ class DomDec:
 
     def stats(self):
         return domdec_get_stats(self.h)
+
+    def kernel_times(self, reset=True):
+        return domdec_kernel_times(self.h, reset)
+
+    def cell_log(self, max_records=4096):
+        return domdec_cell_log(self.h, max_records)
 
     def decisions(self, max_records=4096):
         return domdec_decision_log(self.h, max_records)
