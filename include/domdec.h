@@ -206,6 +206,32 @@ int domdec_full_sinkhorn(const double* mu, const double* nu, int N, double eps_s
                          const double* beta_in, double* alpha, double* beta,
                          double out[4], void* stream);
 
+/* Allocation-free variant of domdec_full_sinkhorn (no counterpart in the
+ * paper; it exists for callers that cannot allocate device memory while the
+ * solver runs -- e.g. a process whose device memory is all handed to its own
+ * pool at start-up, where cudaMalloc would fail or fragment it, or a loop that
+ * must not pay the device-wide synchronisation of cudaMalloc/cudaFree).
+ * Same arguments and results as domdec_full_sinkhorn, except:
+ *  - mu, nu (N*N, > 0), alpha and beta (N*N outputs, also the iteration state)
+ *    must be DEVICE pointers of the current device; beta_in may be NULL
+ *    (start from 0), equal to beta, or another device pointer;
+ *  - precision must be DOMDEC_FP32 or DOMDEC_FP64;
+ *  - N*N must not exceed 65536 (N <= 256): larger grids return DOMDEC_ETOOBIG.
+ * It calls no cudaMalloc, cudaFree or allocating library routine: all working
+ * arrays live in one static device array of about 3.1 MB that every GPU which
+ * loads the library keeps until the process exits.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) and
+ * caches it; make that first call before any stream capture on the device.
+ * All calls share the one array, which keeps the last call's contents (the
+ * status word it needs cleared is reset at the start of each call): calls that
+ * overlap on the GPU -- from several streams or host threads -- race and
+ * must be serialised by the caller.  Synchronises. */
+int domdec_full_sinkhorn_noalloc(const double* mu, const double* nu, int N, double eps_start,
+                                 double eps, double lambda, int variant, int precision,
+                                 int maxit, double err, int check_every,
+                                 const double* beta_in, double* alpha, double* beta,
+                                 double out[4], void* stream);
+
 #ifdef __cplusplus
 }
 #endif

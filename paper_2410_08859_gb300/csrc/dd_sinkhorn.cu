@@ -8,7 +8,10 @@
 //  * separable  : |x-y|^2 = (x1-y1)^2 + (x2-y2)^2, so L is a 1-D log-sum-exp along rows
 //                 followed by one along columns: 2 N^3 terms instead of N^4.
 // Values are kept in log2 units (ex2/lg2); float or double arithmetic.
+#include <cmath>
+
 #include "dd_common.cuh"
+#include "domdec.h"
 
 namespace {
 
@@ -283,4 +286,154 @@ int full_sinkhorn_dev(const double* mu, const double* nu, const double* logmu, c
                                       check_every, alpha, beta, out, d_eval, st, cerr);
   return full_sinkhorn_impl<float>(mu, nu, logmu, lognu, N, eps_start, eps, lam, variant, maxit, err,
                                    check_every, alpha, beta, out, d_eval, st, cerr);
+}
+
+// ------------------------------------------------------------------------
+// Allocation-free variant of the global Sinkhorn.
+//
+// Some callers cannot allocate device memory while they run this solver: a
+// process that has handed all device memory to its own pool at start-up (a
+// cudaMalloc would fail or fragment that pool), or a latency-sensitive loop
+// that must not pay the implicit device-wide synchronisation of
+// cudaMalloc/cudaFree.  For them the working arrays live in one file-scope
+// device array of fixed size, reserved on every GPU that loads the library
+// for the life of the process.
+#include <mutex>
+
+namespace {
+constexpr int kNoAllocMaxN2 = 256 * 256;  // largest grid: N*N <= 65536 (N <= 256)
+// log mu, log nu (N*N doubles each), four N*N work arrays of the log-sum-exp
+// (double-sized slots, also used for float), 8 doubles of reductions and the
+// input-status word.
+constexpr long long kNoAllocDoubles = 6LL * kNoAllocMaxN2 + 16;
+__device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+constexpr int kMaxDevices = 64;
+double* g_noalloc_ptr[kMaxDevices] = {nullptr};
+std::mutex g_noalloc_mu;
+
+// Device address of the scratch array for the current device (host code must
+// not use the symbol itself: it is only a host-side stand-in).
+cudaError_t noalloc_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+template <typename R>
+int full_sinkhorn_noalloc_impl(const double* mu, const double* nu, const double* logmu, const double* lognu,
+                               int N, double eps_start, double eps, double lam, int variant, int maxit,
+                               double err, int check_every, double* alpha, double* beta, double* out,
+                               double* work, double* d_eval, cudaStream_t st, cudaError_t* cerr) {
+  const int n = N * N;
+  const double h = 1.0 / N;
+  // four work arrays in double-sized slots (float arrays use the first half of each)
+  R* in2 = reinterpret_cast<R*>(work);
+  R* tmp = reinterpret_cast<R*>(work + n);
+  R* w2 = reinterpret_cast<R*>(work + 2 * (long long)n);
+  R* z2 = reinterpret_cast<R*>(work + 3 * (long long)n);
+  const int grid = (n + 255) / 256;
+  double evalh[6];
+  long long total = 0;
+  int rc = 0;
+  if (check_every < 1) check_every = 1;
+  double e = eps_start > eps ? eps_start : eps;
+  for (;;) {
+    const double kap = std::isfinite(lam) ? e / (1.0 + e / lam) : e;
+    const double q = h * h / e;
+    k_to_log2<R><<<grid, 256, 0, st>>>(beta, lognu, 1.0 / e, in2, n);
+    lse_all<R>(in2, tmp, w2, N, q, variant, 0, st);
+    int it = 0, shift_ok = 0;
+    bool conv = false;
+    while (it < maxit) {
+      k_half<R><<<grid, 256, 0, st>>>(w2, kap, alpha, n);
+      k_to_log2<R><<<grid, 256, 0, st>>>(alpha, logmu, 1.0 / e, in2, n);
+      lse_all<R>(in2, tmp, z2, N, q, variant, shift_ok, st);
+      k_half<R><<<grid, 256, 0, st>>>(z2, kap, beta, n);
+      k_to_log2<R><<<grid, 256, 0, st>>>(beta, lognu, 1.0 / e, in2, n);
+      lse_all<R>(in2, tmp, w2, N, q, variant, 1, st);
+      shift_ok = 1;
+      ++it;
+      if (it % check_every == 0 || it == maxit) {
+        k_sk_eval<R><<<1, 512, 0, st>>>(mu, nu, alpha, beta, w2, nullptr, e, lam, n, d_eval);
+        cudaMemcpyAsync(evalh, d_eval, 6 * sizeof(double), cudaMemcpyDeviceToHost, st);
+        *cerr = cudaStreamSynchronize(st);
+        if (*cerr != cudaSuccess) return -1;
+        if (err >= 0.0 && evalh[0] <= err * evalh[4]) { conv = true; break; }
+        if (!(evalh[0] == evalh[0])) break;
+      }
+    }
+    total += it;
+    if (e <= eps) { rc = conv || err < 0.0 ? 0 : 1; break; }
+    e = fmax(eps, 0.5 * e);
+  }
+  k_sk_eval<R><<<1, 512, 0, st>>>(mu, nu, alpha, beta, w2, z2, eps, lam, n, d_eval);
+  cudaMemcpyAsync(evalh, d_eval, 6 * sizeof(double), cudaMemcpyDeviceToHost, st);
+  *cerr = cudaStreamSynchronize(st);
+  if (*cerr != cudaSuccess) return -1;
+  const double D = eps * evalh[4] * evalh[5] - eps * evalh[1] - evalh[2] - evalh[3];
+  const double pd = std::isfinite(lam) ? lam * evalh[0] : evalh[0];
+  out[0] = (double)total;
+  out[1] = evalh[0];
+  out[2] = D + pd;
+  out[3] = D;
+  return rc;
+}
+}  // namespace
+
+cudaError_t launch_prepare_inputs(const double* mu, const double* nu, double* logmu, double* lognu, int n,
+                                  int* status, cudaStream_t st);
+
+int domdec_full_sinkhorn_noalloc(const double* mu, const double* nu, int N, double eps_start,
+                                            double eps, double lambda, int variant, int precision, int maxit,
+                                            double err, int check_every, const double* beta_in, double* alpha,
+                                            double* beta, double out[4], void* stream) {
+  if (!mu || !nu || !alpha || !beta || !out || N <= 0) return DOMDEC_EINVAL;
+  if (!(eps > 0.0) || !(lambda > 0.0) || (variant != 0 && variant != 1) || (precision != 0 && precision != 1) ||
+      maxit < 1)
+    return DOMDEC_EINVAL;
+  if ((long long)N * N > kNoAllocMaxN2) return DOMDEC_ETOOBIG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  double* base = nullptr;
+  if (noalloc_scratch(&base) != cudaSuccess) return DOMDEC_ECUDA;
+  const int n = N * N;
+  double* logmu = base;
+  double* lognu = base + n;
+  double* work = base + 2 * (long long)n;
+  double* d_eval = base + 6LL * kNoAllocMaxN2;
+  int* d_status = reinterpret_cast<int*>(d_eval + 8);
+  // every call starts from a cleared status word and its own beta
+  cudaError_t e = cudaMemsetAsync(d_status, 0, sizeof(int), st);
+  if (e == cudaSuccess) {
+    if (beta_in) {
+      if (beta_in != beta) e = cudaMemcpyAsync(beta, beta_in, n * sizeof(double), cudaMemcpyDefault, st);
+    } else {
+      e = cudaMemsetAsync(beta, 0, n * sizeof(double), st);
+    }
+  }
+  if (e == cudaSuccess) e = launch_prepare_inputs(mu, nu, logmu, lognu, n, d_status, st);
+  int hstat = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hstat, d_status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return DOMDEC_ECUDA;
+  if (hstat) return DOMDEC_EINVAL;
+  cudaError_t ce = cudaSuccess;
+  int r = precision ? full_sinkhorn_noalloc_impl<double>(mu, nu, logmu, lognu, N, eps_start, eps, lambda,
+                                                         variant, maxit, err, check_every, alpha, beta, out,
+                                                         work, d_eval, st, &ce)
+                    : full_sinkhorn_noalloc_impl<float>(mu, nu, logmu, lognu, N, eps_start, eps, lambda,
+                                                        variant, maxit, err, check_every, alpha, beta, out,
+                                                        work, d_eval, st, &ce);
+  if (r < 0) return DOMDEC_ECUDA;
+  return r ? 1 : 0;
 }

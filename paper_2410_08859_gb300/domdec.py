@@ -76,6 +76,7 @@ _SIGS = {
     "domdec_free": (None, [_P]),
     "domdec_error_string": (ctypes.c_char_p, [_I]),
     "domdec_full_sinkhorn": (_I, [_P, _P, _I, _D, _D, _D, _I, _I, _I, _D, _I, _P, _P, _P, _DP, _P]),
+    "domdec_full_sinkhorn_noalloc": (_I, [_P, _P, _I, _D, _D, _D, _I, _I, _I, _D, _I, _P, _P, _P, _DP, _P]),
 }
 
 
@@ -253,6 +254,22 @@ def domdec_full_sinkhorn(mu, nu, N, eps, lam, eps_start=None, variant=SINKHORN_S
                                     _ptr(beta_in, n), _ptr(alpha, n, True), _ptr(beta, n, True), out,
                                     _stream_ptr(stream))
     _check(rc, "domdec_full_sinkhorn")
+    return int(out[0]), out[1], out[2], out[3], rc
+
+
+def domdec_full_sinkhorn_noalloc(mu, nu, N, eps, lam, alpha, beta, eps_start=None,
+                                 variant=SINKHORN_SEPARABLE, precision=FP64, maxit=10000, err=2e-5,
+                                 check_every=10, beta_in=None, stream=None):
+    """Allocation-free global Sinkhorn: device tensors only, N <= 256 (see
+    include/domdec.h).  Returns (iterations, PD/lam, primal, dual, rc)."""
+    out = (ctypes.c_double * 4)()
+    n = N * N
+    rc = lib().domdec_full_sinkhorn_noalloc(_ptr(mu, n), _ptr(nu, n), int(N),
+                                            float(eps if eps_start is None else eps_start), float(eps),
+                                            float(lam), int(variant), int(precision), int(maxit), float(err),
+                                            int(check_every), _ptr(beta_in, n), _ptr(alpha, n, True),
+                                            _ptr(beta, n, True), out, _stream_ptr(stream))
+    _check(rc, "domdec_full_sinkhorn_noalloc")
     return int(out[0]), out[1], out[2], out[3], rc
 
 
