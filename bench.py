@@ -97,16 +97,20 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def warm_start(dd, mu_d, nu_d, N, eps, lam, torch):
-    """Global Sinkhorn (separable, FP64) from eps = 1 down to 2 eps (Section 5.3
-    warm start at a quarter of the DomDec tolerance)."""
+def warm_start(dd, mu_d, nu_d, N, eps, lam, torch, quick=False):
+    """Global Sinkhorn (separable; float for coarse eps, double for fine) from
+    eps = 1 down to 2 eps, at a quarter of the DomDec tolerance (Section 5.3
+    warm start).  quick: float only, at most 200 iterations per stage (profiling
+    runs, where only the shape of the DomDec state matters)."""
     a = torch.empty(N * N, dtype=torch.float64, device="cuda")
     b = torch.empty_like(a)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     it, gap, P, D, rc = dd.domdec_full_sinkhorn(mu_d, nu_d, N, 2 * eps, lam, eps_start=1.0,
-                                                variant=dd.SINKHORN_SEPARABLE, precision=dd.MIXED,
-                                                maxit=4000, err=2e-5 / 4, check_every=10, alpha=a, beta=b)
+                                                variant=dd.SINKHORN_SEPARABLE,
+                                                precision=dd.FP32 if quick else dd.MIXED,
+                                                maxit=200 if quick else 4000, err=2e-5 / 4, check_every=10,
+                                                alpha=a, beta=b)
     torch.cuda.synchronize()
     return a, b, time.perf_counter() - t0, it
 
@@ -221,6 +225,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--lam", type=float, default=1.0)
     ap.add_argument("--no-extras", action="store_true", help="skip time-to-gap, e2e and CPU baseline")
+    ap.add_argument("--quick-warm", action="store_true",
+                    help="float-only, capped warm start (profiling runs; not a bench number)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -245,7 +251,7 @@ def main():
     N, s, eps, lam = spec["N"], spec["s"], spec["eps"], args.lam
     mu_d = torch.from_numpy(mu).cuda()
     nu_d = torch.from_numpy(nu).cuda()
-    a0, b0, t_warm, it_warm = warm_start(dd, mu_d, nu_d, N, eps, lam, torch)
+    a0, b0, t_warm, it_warm = warm_start(dd, mu_d, nu_d, N, eps, lam, torch, quick=args.quick_warm)
 
     g = dd.DomDec(mu_d, nu_d, eps, lam, s, alpha0=a0, beta0=b0, eps_init=2 * eps, precision="fp32",
                   tau=0.0, err=2e-5, profile=1)

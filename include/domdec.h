@@ -218,7 +218,7 @@ int domdec_full_sinkhorn(const double* mu, const double* nu, int N, double eps_s
  *  - precision must be DOMDEC_FP32 or DOMDEC_FP64;
  *  - N*N must not exceed 65536 (N <= 256): larger grids return DOMDEC_ETOOBIG.
  * It calls no cudaMalloc, cudaFree or allocating library routine: all working
- * arrays live in one static device array of about 3.1 MB that every GPU which
+ * arrays live in one static device array of about 3.7 MB that every GPU which
  * loads the library keeps until the process exits.  The first call on a
  * device looks up that array's device address (cudaGetSymbolAddress) and
  * caches it; make that first call before any stream capture on the device.

@@ -36,7 +36,7 @@ cudaError_t launch_score(const DevState& S, double* out, cudaStream_t st);
 cudaError_t launch_cert(const DevState& S, const double* z, double* beta_out, double* out, cudaStream_t st);
 cudaError_t launch_regrow(const DevState& S, double* new0, double* new1, long long* newoff, cudaStream_t st);
 cudaError_t global_lse64(const double* pot, const double* logm, double eps, double h, int N, double* out,
-                         double* buf_a, double* buf_b, cudaStream_t st);
+                         double* buf_a, double* buf_b, double* buf_c, cudaStream_t st);
 int full_sinkhorn_dev(const double* mu, const double* nu, const double* logmu, const double* lognu, int N,
                       double eps_start, double eps, double lam, int variant, int precision, int maxit,
                       double err, int check_every, double* alpha, double* beta, double* out, double* d_eval,
@@ -421,7 +421,7 @@ int domdec_init(domdec_t* out, const double* mu, const double* nu, int N, const 
   double* bd = nullptr;
   double* wtmp = nullptr;
   if (alpha0) {
-    DD_ALLOC(ad, n); DD_ALLOC(bd, n); DD_ALLOC(wtmp, 3 * (size_t)n);
+    DD_ALLOC(ad, n); DD_ALLOC(bd, n); DD_ALLOC(wtmp, 4 * (size_t)n);
     cudaMemcpyAsync(ad, alpha0, n * sizeof(double), cudaMemcpyDefault, st);
     cudaMemcpyAsync(bd, beta0, n * sizeof(double), cudaMemcpyDefault, st);
     e = launch_init_duals_boxes(S, ad, bd, pin->eps_init, h->d_numom, h->d_mumass, h->d_newoff, st);
@@ -441,7 +441,8 @@ int domdec_init(domdec_t* out, const double* mu, const double* nu, int N, const 
   DD_ALLOC(S.arena[1], S.cap);
   if (alpha0) {
     // w(x) = log sum_y exp(beta0/eps0 + log nu - c/eps0): P_X of the initial plan
-    global_lse64(bd, dlognu, pin->eps_init, 1.0 / N, N, wtmp, wtmp + n, wtmp + 2 * (size_t)n, st);
+    global_lse64(bd, dlognu, pin->eps_init, 1.0 / N, N, wtmp, wtmp + n, wtmp + 2 * (size_t)n,
+                 wtmp + 3 * (size_t)n, st);
     e = launch_init_duals_fill(S, ad, bd, pin->eps_init, wtmp, h->d_newoff, st);
   } else {
     e = launch_init_product_fill(S, h->d_numom, h->d_mumass, h->d_newoff, st);
@@ -537,9 +538,9 @@ int domdec_pd_gap(domdec_t h, double out[5], double* beta) {
   if (h->sticky) return DOMDEC_ESTATE;
   const int n = h->n;
   double* buf = nullptr;
-  if (cudaMallocAsync(&buf, 4 * (size_t)n * sizeof(double), h->st) != cudaSuccess) return fail(h, DOMDEC_ENOMEM);
-  double *z = buf, *ba = buf + n, *bb = buf + 2 * (size_t)n, *bt = buf + 3 * (size_t)n;
-  cudaError_t e = global_lse64(h->S.alpha, h->S.logmu, h->S.eps, h->S.h, h->N, z, ba, bb, h->st);
+  if (cudaMallocAsync(&buf, 5 * (size_t)n * sizeof(double), h->st) != cudaSuccess) return fail(h, DOMDEC_ENOMEM);
+  double *z = buf, *ba = buf + n, *bb = buf + 2 * (size_t)n, *bt = buf + 3 * (size_t)n, *bc = buf + 4 * (size_t)n;
+  cudaError_t e = global_lse64(h->S.alpha, h->S.logmu, h->S.eps, h->S.h, h->N, z, ba, bb, bc, h->st);
   if (e == cudaSuccess) e = launch_cert(h->S, z, bt, h->d_scratch + 16, h->st);
   if (e == cudaSuccess) e = launch_score(h->S, h->d_scratch, h->st);
   if (e == cudaSuccess && beta) e = cudaMemcpyAsync(beta, bt, n * sizeof(double), cudaMemcpyDefault, h->st);

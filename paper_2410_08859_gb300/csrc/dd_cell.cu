@@ -52,6 +52,68 @@ __device__ __forceinline__ R lse2_1d(F src, int M, R ctr, R q2, R shift, bool us
   return mx + dd_lg2(acc);
 }
 
+// Partial sum of 2^{src(m) - q2 (m - ctr)^2 - shift} over m = part, part + P, ...
+// (four independent accumulators to keep several ex2 in flight).
+template <typename R, typename F>
+__device__ __forceinline__ R psum2(F src, int M, R ctr, R q2, R shift, int part, int P) {
+  R a0 = R(0), a1 = R(0), a2 = R(0), a3 = R(0);
+  const R dP = R(P);
+  R d = R(part) - ctr;
+  int m = part;
+  for (; m + 3 * P < M; m += 4 * P) {
+    R v0 = src(m) - q2 * d * d - shift;
+    R d1 = d + dP, d2 = d1 + dP, d3 = d2 + dP;
+    R v1 = src(m + P) - q2 * d1 * d1 - shift;
+    R v2 = src(m + 2 * P) - q2 * d2 * d2 - shift;
+    R v3 = src(m + 3 * P) - q2 * d3 * d3 - shift;
+    a0 += dd_ex2(v0); a1 += dd_ex2(v1); a2 += dd_ex2(v2); a3 += dd_ex2(v3);
+    d = d3 + dP;
+  }
+  for (; m < M; m += P, d += dP) a0 += dd_ex2(src(m) - q2 * d * d - shift);
+  return (a0 + a1) + (a2 + a3);
+}
+
+template <typename R, typename F>
+__device__ __forceinline__ R pmax2(F src, int M, R ctr, R q2, int part, int P) {
+  R mx = -dd_inf<R>();
+  const R dP = R(P);
+  R d = R(part) - ctr;
+  for (int m = part; m < M; m += P, d += dP) mx = max(mx, src(m) - q2 * d * d);
+  return mx;
+}
+
+// log2 sum_m 2^{src(m) - q2 (m - ctr)^2} computed by the P lanes of an aligned
+// lane group (P a power of two dividing 32).  Must be called by all 32 lanes of
+// the warp.  With use_shift the sum is taken against `shift` (the previous
+// iteration's value) in one pass; if the group's sum leaves the safe range, or
+// without a shift, the warp falls back to the exact max-shifted two passes.
+template <typename R, typename F>
+__device__ __forceinline__ R lse2_group(F src, int M, R ctr, R q2, R shift, bool use_shift, int part, int P) {
+  R acc = R(0);
+  bool bad = true;
+  if (use_shift) {
+    acc = psum2<R>(src, M, ctr, q2, shift, part, P);
+    for (int o = 1; o < P; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    bad = !(acc > R(1e-25) && acc < R(1e25));
+  }
+  if (__any_sync(0xffffffffu, bad)) {
+    R mx = pmax2<R>(src, M, ctr, q2, part, P);
+    for (int o = 1; o < P; o <<= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const bool fin = mx > -dd_inf<R>();
+    R s2 = psum2<R>(src, M, ctr, q2, fin ? mx : R(0), part, P);
+    for (int o = 1; o < P; o <<= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    if (bad) return fin ? mx + dd_lg2(s2) : mx;
+  }
+  return shift + dd_lg2(acc);
+}
+
+// Lanes per target for a pass with `nt` targets of `M` sources on `nthr` threads.
+__device__ __forceinline__ int lanes_per_target(int nt, int M, int nthr) {
+  int P = 1;
+  while (P < 32 && nt * P * 2 <= nthr && P * 2 <= M) P *= 2;
+  return P;
+}
+
 // Root u of g(u) = (1+s) u + c0 + softplus(lr - u) = 0, i.e. of
 // log(rho + e^u) + s u + c0 = 0 with lr = log rho (Eq. proxdiv-problem with
 // u = beta/eps + z).  g is convex and increasing (g' = 1 + s - sigmoid(lr - u) >= s).
@@ -91,7 +153,7 @@ template <typename R>
 __global__ void __launch_bounds__(512, 1)
 k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbatch) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* red = reinterpret_cast<double*>(smem_raw);  // 32 * 16 doubles
+  double* red = reinterpret_cast<double*>(smem_raw);  // 32 * 16 doubles (block reductions)
   __shared__ BoxRec sbox[4];
   __shared__ int sgeo[8];
 
@@ -255,46 +317,71 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbat
   for (;;) {
     ++it;
     // Y-half, pass over columns of X: T(r, ll) = log2 sum_c 2^{xa(r,c) - q2 (c - ll - offc)^2}
-    for (int t = tid; t < nx1 * W; t += nthr) {
-      int r = t / W, ll = t - r * W;
-      const R* row = xa + r * nx2;
-      T[t] = lse2_1d<R>([&](int m) { return row[m]; }, nx2, R(ll + offc), q2, T[t], !first);
+    {
+      const int nt = nx1 * W, P = lanes_per_target(nt, nx2, nthr), ni = (nt * P + 31) & ~31;
+      for (int i = tid; i < ni; i += nthr) {
+        const int tg0 = i / P, part = i - tg0 * P, tg = min(tg0, nt - 1);
+        const int r = tg / W, ll = tg - r * W;
+        const R* row = xa + r * nx2;
+        R v = lse2_group<R>([&](int m) { return row[m]; }, nx2, R(ll + offc), q2, T[tg], !first, part, P);
+        __syncwarp();
+        if (part == 0 && tg0 < nt) T[tg] = v;
+      }
     }
     __syncthreads();
     // Y-half, pass over rows of X, then the Newton root per y (a3)
-    for (int u = tid; u < ny; u += nthr) {
-      int kk = u / W, ll = u - kk * W;
-      R Z2 = lse2_1d<R>([&](int m) { return T[m * W + ll]; }, nx1, R(kk + offr), q2, Zv[u], !first);
-      Zv[u] = Z2;
-      R Zn = Z2 * LN2;
-      R eta1 = R(k0 + kk - yc1), eta2 = R(l0 + ll - yc2);
-      R c0 = sB - cEta1 * eta1 - cEta2 * eta2 - sR * Zn;
-      R uu = newton_u<R>(lrho[u], c0, sR, S.newton_maxit);
-      R b = uu - Zn;
-      bv[u] = b;
-      bl[u] = (b + lnu[u]) * L2E;
+    {
+      const int ni = (ny + 31) & ~31;
+      for (int i = tid; i < ni; i += nthr) {
+        const int u = min(i, ny - 1);
+        const int kk = u / W, ll = u - kk * W;
+        R Z2 = lse2_group<R>([&](int m) { return T[m * W + ll]; }, nx1, R(kk + offr), q2, Zv[u], !first, 0, 1);
+        if (i < ny) {
+          Zv[u] = Z2;
+          R Zn = Z2 * LN2;
+          R eta1 = R(k0 + kk - yc1), eta2 = R(l0 + ll - yc2);
+          R c0 = sB - cEta1 * eta1 - cEta2 * eta2 - sR * Zn;
+          R uu = newton_u<R>(lrho[u], c0, sR, S.newton_maxit);
+          R b = uu - Zn;
+          bv[u] = b;
+          bl[u] = (b + lnu[u]) * L2E;
+        }
+      }
     }
     __syncthreads();
     // X-half, pass over columns of B_J: U(kk, c) = log2 sum_ll 2^{bl(kk,ll) - q2 (ll - (c - offc))^2}
-    for (int t = tid; t < H * nx2; t += nthr) {
-      int kk = t / nx2, c = t - kk * nx2;
-      const R* row = bl + kk * W;
-      U[t] = lse2_1d<R>([&](int m) { return row[m]; }, W, R(c - offc), q2, U[t], !first);
+    {
+      const int nt = H * nx2, P = lanes_per_target(nt, W, nthr), ni = (nt * P + 31) & ~31;
+      for (int i = tid; i < ni; i += nthr) {
+        const int tg0 = i / P, part = i - tg0 * P, tg = min(tg0, nt - 1);
+        const int kk = tg / nx2, c = tg - kk * nx2;
+        const R* row = bl + kk * W;
+        R v = lse2_group<R>([&](int m) { return row[m]; }, W, R(c - offc), q2, U[tg], !first, part, P);
+        __syncwarp();
+        if (part == 0 && tg0 < nt) U[tg] = v;
+      }
     }
     __syncthreads();
-    // X-half, pass over rows of B_J, and the PD gap (a4)
-    double gl[1] = {0.0};
-    for (int t = tid; t < nx; t += nthr) {
-      int r = t / nx2, c = t - r * nx2;
-      R W2 = lse2_1d<R>([&](int m) { return U[m * nx2 + c]; }, H, R(r - offr), q2, Wv[t], !first);
-      Wv[t] = W2;
-      R a = av[t];
-      R tt = a + W2 * LN2;         // log(P_X pi / mu)
-      R g = g0[t] - sR * a;        // -alpha/lam
-      gl[0] += (double)(dd_ex2((lm[t] + g) * L2E) * dd_psi<R>(tt - g));
+    // X-half, pass over rows of B_J, and the PD gap (a4), accumulated in R
+    R gl[1] = {R(0)};
+    {
+      const int P = lanes_per_target(nx, H, nthr), ni = (nx * P + 31) & ~31;
+      for (int i = tid; i < ni; i += nthr) {
+        const int tg0 = i / P, part = i - tg0 * P, t = min(tg0, nx - 1);
+        const int r = t / nx2, c = t - r * nx2;
+        R W2 = lse2_group<R>([&](int m) { return U[m * nx2 + c]; }, H, R(r - offr), q2, Wv[t], !first, part, P);
+        __syncwarp();
+        if (part == 0 && tg0 < nx) {
+          Wv[t] = W2;
+          R a = av[t];
+          R tt = a + W2 * LN2;         // log(P_X pi / mu)
+          R g = g0[t] - sR * a;        // -alpha/lam
+          gl[0] += dd_ex2((lm[t] + g) * L2E) * dd_psi<R>(tt - g);
+        }
+      }
     }
-    block_sum<1>(gl, red);
-    gap = gl[0];
+    block_sum<1>(gl, reinterpret_cast<R*>(red));
+    gap = (double)gl[0];
     first = false;
     if ((S.err >= 0.0 && gap <= tol) || it >= S.maxit || !(gap == gap)) break;
     // X-update (closed form, a2)

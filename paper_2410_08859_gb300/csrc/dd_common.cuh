@@ -32,9 +32,6 @@ struct CellOut {
   double gap;            // last PD/lam of the cell
 };
 
-// New marginals of cell position j of the current launch (quadrant stride in *stride).
-__device__ __forceinline__ double* cell_nut(const struct DevState& S, const CellOut& o, int j, int* stride);
-
 // Basic-cell box: Y rows [k0, k0+H), columns [l0, l0+W), values at arena[off..].
 struct BoxRec {
   int k0, l0, H, W;
@@ -131,27 +128,34 @@ template <typename T> __device__ __forceinline__ T warp_max(T v) {
   return v;
 }
 
-// Block-wide sum of K doubles per thread; result valid in every thread.
-// `scratch` must hold 32*K doubles; ends with a barrier.
-template <int K>
-__device__ __forceinline__ void block_sum(double (&v)[K], double* scratch) {
+// Block-wide sum of K values per thread; result valid in every thread.
+// Warp 0 adds the per-warp partials in a fixed order (deterministic).
+// `scratch` must hold 32*K values of type T; ends with a barrier.
+template <int K, typename T>
+__device__ __forceinline__ void block_sum(T (&v)[K], T* scratch) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
   for (int k = 0; k < K; ++k) v[k] = warp_sum(v[k]);
-  __syncthreads();
   if (lane == 0)
 #pragma unroll
     for (int k = 0; k < K; ++k) scratch[wid * K + k] = v[k];
   __syncthreads();
+  if (wid == 0) {
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    double a = 0.0;
-    for (int w = 0; w < nw; ++w) a += scratch[w * K + k];  // fixed order: deterministic
-    v[k] = a;
+    for (int k = 0; k < K; ++k) {
+      T a = lane < nw ? scratch[lane * K + k] : T(0);
+      // fixed-order pairwise combination across the lanes
+      a = warp_sum(a);
+      if (lane == 0) scratch[32 * K + k] = a;
+    }
   }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = scratch[32 * K + k];
   __syncthreads();
 }
 
+// New marginals of cell position j of the current launch (quadrant stride in *stride).
 __device__ __forceinline__ double* cell_nut(const DevState& S, const CellOut& o, int j, int* stride) {
   if (o.slot >= 0) {
     *stride = S.N * S.N;

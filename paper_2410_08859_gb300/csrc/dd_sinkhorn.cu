@@ -19,46 +19,82 @@ namespace {
 // of them change the sum by N 2^-cut relative (< 1e-15 in double, < 1e-7 in float).
 template <typename R> __device__ __forceinline__ R cut_log2() { return sizeof(R) == 4 ? R(32) : R(64); }
 
-// out[k*N + j] = log2 sum_l 2^{in[k*N + l] - q2 (j - l)^2}   (one block row k, threads over j)
+// Buffers of one separable log-sum-exp: `in`/`tmp`/`out` in R; for R = double
+// the kernels also keep float shadows of `in` and `tmp` (for R = float the
+// shadow pointers alias the arrays themselves).
 template <typename R>
-__global__ void __launch_bounds__(256) k_sep_rows(const R* __restrict__ in, R* __restrict__ out, int N, R q2) {
+struct SepBufs {
+  const R* in;
+  const float* inf;
+  R* tmp;
+  float* tmpf;
+  R* out;
+};
+
+// One 1-D log-sum-exp per target with P lanes: the maximum and the window
+// test run in float on the shadow values; only terms within `cut` of the
+// maximum are evaluated (in R) and summed.
+template <typename R, typename FS, typename FF>
+__device__ __forceinline__ R lse_window(FS src, FF srcf, int M, int ctr, double q2, int part, int P) {
+  const float q2f = (float)q2;
+  float mxf = -INFINITY;
+  for (int m = part; m < M; m += P) {
+    float d = (float)(ctr - m);
+    mxf = fmaxf(mxf, srcf(m) - q2f * d * d);
+  }
+  for (int o = 1; o < P; o <<= 1) mxf = fmaxf(mxf, __shfl_xor_sync(0xffffffffu, mxf, o));
+  if (!(mxf > -INFINITY)) return R(mxf);
+  const float cutf = (float)cut_log2<R>() + 1.0f;
+  const R mx = R(mxf), q2r = R(q2);
+  R acc = R(0);
+  for (int m = part; m < M; m += P) {
+    float d = (float)(ctr - m);
+    if (srcf(m) - q2f * d * d - mxf > -cutf) {
+      R dr = R(ctr - m);
+      acc += dd_ex2(src(m) - q2r * dr * dr - mx);
+    }
+  }
+  for (int o = 1; o < P; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  return mx + dd_lg2(acc);
+}
+
+constexpr int kSepLanes = 4;   // lanes per target in the separable passes
+
+// tmp[k*N + j] = log2 sum_l 2^{in[k*N + l] - q2 (j - l)^2}   (block = row k)
+template <typename R>
+__global__ void __launch_bounds__(1024) k_sep_rows(SepBufs<R> B, int N, double q2) {
   extern __shared__ __align__(16) unsigned char sm[];
   R* row = reinterpret_cast<R*>(sm);
+  float* rowf = reinterpret_cast<float*>(row + N);
   const int k = blockIdx.x;
-  for (int l = threadIdx.x; l < N; l += blockDim.x) row[l] = in[(long long)k * N + l];
+  for (int l = threadIdx.x; l < N; l += blockDim.x) {
+    row[l] = B.in[(long long)k * N + l];
+    rowf[l] = B.inf[(long long)k * N + l];
+  }
   __syncthreads();
-  const R cut = cut_log2<R>();
-  for (int j = threadIdx.x; j < N; j += blockDim.x) {
-    R mx = -dd_inf<R>();
-    for (int l = 0; l < N; ++l) { R d = R(j - l); mx = max(mx, row[l] - q2 * d * d); }
-    R acc = R(0);
-    if (mx > -dd_inf<R>())
-      for (int l = 0; l < N; ++l) {
-        R d = R(j - l);
-        R v = row[l] - q2 * d * d - mx;
-        if (v > -cut) acc += dd_ex2(v);
-      }
-    out[(long long)k * N + j] = mx + dd_lg2(acc);
+  const int P = kSepLanes, nt = (N * P + 31) & ~31;
+  for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+    const int j0 = i / P, part = i % P, j = min(j0, N - 1);
+    R v = lse_window<R>([&](int m) { return row[m]; }, [&](int m) { return rowf[m]; }, N, j, q2, part, P);
+    if (part == 0 && j0 < N) {
+      B.tmp[(long long)k * N + j] = v;
+      if (sizeof(R) == 8) B.tmpf[(long long)k * N + j] = (float)v;
+    }
   }
 }
 
-// out[i*N + j] = log2 sum_k 2^{in[k*N + j] - q2 (i - k)^2}   (threads over j, blocks over (i-tile))
+// out[i*N + j] = log2 sum_k 2^{tmp[k*N + j] - q2 (i - k)^2}   (block = (j tile, i))
 template <typename R>
-__global__ void __launch_bounds__(256) k_sep_cols(const R* __restrict__ in, R* __restrict__ out, int N, R q2) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_sep_cols(SepBufs<R> B, int N, double q2) {
+  const int P = kSepLanes;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j0 = t / P, part = t % P, j = min(j0, N - 1);
   const int i = blockIdx.y;
-  if (j >= N) return;
-  const R cut = cut_log2<R>();
-  R mx = -dd_inf<R>();
-  for (int k = 0; k < N; ++k) { R d = R(i - k); mx = max(mx, in[(long long)k * N + j] - q2 * d * d); }
-  R acc = R(0);
-  if (mx > -dd_inf<R>())
-    for (int k = 0; k < N; ++k) {
-      R d = R(i - k);
-      R v = in[(long long)k * N + j] - q2 * d * d - mx;
-      if (v > -cut) acc += dd_ex2(v);
-    }
-  out[(long long)i * N + j] = mx + dd_lg2(acc);
+  const R* col = B.tmp + j;
+  const float* colf = B.tmpf + j;
+  R v = lse_window<R>([&](int m) { return col[(long long)m * N]; }, [&](int m) { return colf[(long long)m * N]; },
+                      N, i, q2, part, P);
+  if (part == 0 && j0 < N) B.out[(long long)i * N + j] = v;
 }
 
 // Dense: out[x] = log2 sum_y 2^{in[y] - q2 |x - y|^2}, shifted by the previous
@@ -107,9 +143,12 @@ __global__ void __launch_bounds__(256) k_dense(const R* __restrict__ in, R* __re
 
 template <typename R>
 __global__ void k_to_log2(const double* __restrict__ pot, const double* __restrict__ logm, double inv_eps,
-                          R* __restrict__ out, int n) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    out[i] = R((pot ? pot[i] * inv_eps : 0.0) + logm[i]) * R(DD_LOG2E);
+                          R* __restrict__ out, int n, float* __restrict__ shadow = nullptr) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    R v = R((pot ? pot[i] * inv_eps : 0.0) + logm[i]) * R(DD_LOG2E);
+    out[i] = v;
+    if (shadow) shadow[i] = (float)v;
+  }
 }
 
 template <typename R>
@@ -131,7 +170,7 @@ __global__ void __launch_bounds__(512)
 k_sk_eval(const double* __restrict__ mu, const double* __restrict__ nu, const double* __restrict__ alpha,
           const double* __restrict__ beta, const R* __restrict__ w2, const R* __restrict__ z2, double eps,
           double lam, int n, double* out) {
-  __shared__ double red[32 * 6];
+  __shared__ double red[33 * 6];
   double v[6] = {0, 0, 0, 0, 0, 0};
   const bool fin = isfinite(lam);
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -155,15 +194,26 @@ k_sk_eval(const double* __restrict__ mu, const double* __restrict__ nu, const do
 template <typename R>
 struct Work {
   R *in2, *tmp, *w2, *z2;
+  float *in2f, *tmpf;  // float shadows (double precision only)
 };
 
+// in2f / tmpf: float shadows (required for R = double; ignored for float).
 template <typename R>
-cudaError_t lse_all(const R* in2, R* tmp, R* out2, int N, double q, int variant, int use_shift, cudaStream_t st) {
-  R q2 = R(q * DD_LOG2E);
+cudaError_t lse_all(const R* in2, R* tmp, R* out2, int N, double q, int variant, int use_shift, cudaStream_t st,
+                    const float* in2f = nullptr, float* tmpf = nullptr) {
   if (variant == 1) {
-    k_sep_rows<R><<<N, 256, N * sizeof(R), st>>>(in2, tmp, N, q2);
-    k_sep_cols<R><<<dim3((N + 255) / 256, N), 256, 0, st>>>(tmp, out2, N, q2);
+    SepBufs<R> B;
+    B.in = in2;
+    B.inf = sizeof(R) == 8 ? in2f : reinterpret_cast<const float*>(in2);
+    B.tmp = tmp;
+    B.tmpf = sizeof(R) == 8 ? tmpf : reinterpret_cast<float*>(tmp);
+    B.out = out2;
+    const double q2 = q * DD_LOG2E;
+    const int thr_rows = min(1024, ((N * kSepLanes + 31) / 32) * 32);
+    k_sep_rows<R><<<N, thr_rows, N * (sizeof(R) + sizeof(float)), st>>>(B, N, q2);
+    k_sep_cols<R><<<dim3((N * kSepLanes + 255) / 256, N), 256, 0, st>>>(B, N, q2);
   } else {
+    R q2 = R(q * DD_LOG2E);
     int n = N * N;
     k_dense<R><<<(n + 255) / 256, 256, 0, st>>>(in2, out2, N, q2, use_shift);
   }
@@ -174,11 +224,14 @@ cudaError_t lse_all(const R* in2, R* tmp, R* out2, int N, double q, int variant,
 
 // Separable FP64 log-sum-exp over the whole grid (natural units):
 // out[x] = log sum_y exp(pot[y]/eps + logm[y] - h^2 |x-y|^2/eps).  pot may be NULL.
+// buf_a, buf_b, buf_c: N*N doubles of scratch each.
 cudaError_t global_lse64(const double* pot, const double* logm, double eps, double h, int N, double* out,
-                         double* buf_a, double* buf_b, cudaStream_t st) {
+                         double* buf_a, double* buf_b, double* buf_c, cudaStream_t st) {
   int n = N * N;
-  k_to_log2<double><<<(n + 255) / 256, 256, 0, st>>>(pot, logm, 1.0 / eps, buf_a, n);
-  lse_all<double>(buf_a, buf_b, buf_a, N, h * h / eps, 1, 0, st);
+  float* sh_in = reinterpret_cast<float*>(buf_c);
+  float* sh_tmp = sh_in + n;
+  k_to_log2<double><<<(n + 255) / 256, 256, 0, st>>>(pot, logm, 1.0 / eps, buf_a, n, sh_in);
+  lse_all<double>(buf_a, buf_b, buf_a, N, h * h / eps, 1, 0, st, sh_in, sh_tmp);
   k_to_nat<double><<<(n + 255) / 256, 256, 0, st>>>(buf_a, out, n);
   return cudaGetLastError();
 }
@@ -193,9 +246,11 @@ static int full_sinkhorn_impl(const double* mu, const double* nu, const double* 
   const int n = N * N;
   const double h = 1.0 / N;
   Work<R> w;
-  *cerr = cudaMallocAsync(&w.in2, sizeof(R) * 4 * (size_t)n, st);
+  *cerr = cudaMallocAsync(&w.in2, sizeof(R) * 4 * (size_t)n + sizeof(float) * 2 * (size_t)n, st);
   if (*cerr != cudaSuccess) return -1;
   w.tmp = w.in2 + n; w.w2 = w.tmp + n; w.z2 = w.w2 + n;
+  w.in2f = reinterpret_cast<float*>(w.z2 + n);
+  w.tmpf = w.in2f + n;
   const int grid = (n + 255) / 256;
   double evalh[6];
   long long total = 0;
@@ -208,18 +263,18 @@ static int full_sinkhorn_impl(const double* mu, const double* nu, const double* 
     const double kap = std::isfinite(lam) ? e / (1.0 + e / lam) : e;
     const double q = h * h / e;
     // w = LSE_y[beta/e + log nu]
-    k_to_log2<R><<<grid, 256, 0, st>>>(beta, lognu, 1.0 / e, w.in2, n);
-    lse_all<R>(w.in2, w.tmp, w.w2, N, q, variant, 0, st);
+    k_to_log2<R><<<grid, 256, 0, st>>>(beta, lognu, 1.0 / e, w.in2, n, w.in2f);
+    lse_all<R>(w.in2, w.tmp, w.w2, N, q, variant, 0, st, w.in2f, w.tmpf);
     int it = 0;
     bool conv = false;
     int shift_ok = 0;
     while (it < maxit) {
       k_half<R><<<grid, 256, 0, st>>>(w.w2, kap, alpha, n);
-      k_to_log2<R><<<grid, 256, 0, st>>>(alpha, logmu, 1.0 / e, w.in2, n);
-      lse_all<R>(w.in2, w.tmp, w.z2, N, q, variant, shift_ok, st);
+      k_to_log2<R><<<grid, 256, 0, st>>>(alpha, logmu, 1.0 / e, w.in2, n, w.in2f);
+      lse_all<R>(w.in2, w.tmp, w.z2, N, q, variant, shift_ok, st, w.in2f, w.tmpf);
       k_half<R><<<grid, 256, 0, st>>>(w.z2, kap, beta, n);
-      k_to_log2<R><<<grid, 256, 0, st>>>(beta, lognu, 1.0 / e, w.in2, n);
-      lse_all<R>(w.in2, w.tmp, w.w2, N, q, variant, 1, st);
+      k_to_log2<R><<<grid, 256, 0, st>>>(beta, lognu, 1.0 / e, w.in2, n, w.in2f);
+      lse_all<R>(w.in2, w.tmp, w.w2, N, q, variant, 1, st, w.in2f, w.tmpf);
       shift_ok = 1;
       ++it;
       if (it % check_every == 0 || it == maxit) {
@@ -303,9 +358,9 @@ int full_sinkhorn_dev(const double* mu, const double* nu, const double* logmu, c
 namespace {
 constexpr int kNoAllocMaxN2 = 256 * 256;  // largest grid: N*N <= 65536 (N <= 256)
 // log mu, log nu (N*N doubles each), four N*N work arrays of the log-sum-exp
-// (double-sized slots, also used for float), 8 doubles of reductions and the
-// input-status word.
-constexpr long long kNoAllocDoubles = 6LL * kNoAllocMaxN2 + 16;
+// (double-sized slots, also used for float), one N*N double slot holding two
+// float shadow arrays, 8 doubles of reductions and the input-status word.
+constexpr long long kNoAllocDoubles = 7LL * kNoAllocMaxN2 + 16;
 __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
 
 constexpr int kMaxDevices = 64;
@@ -342,6 +397,8 @@ int full_sinkhorn_noalloc_impl(const double* mu, const double* nu, const double*
   R* tmp = reinterpret_cast<R*>(work + n);
   R* w2 = reinterpret_cast<R*>(work + 2 * (long long)n);
   R* z2 = reinterpret_cast<R*>(work + 3 * (long long)n);
+  float* in2f = reinterpret_cast<float*>(work + 4 * (long long)n);
+  float* tmpf = in2f + n;
   const int grid = (n + 255) / 256;
   double evalh[6];
   long long total = 0;
@@ -351,17 +408,17 @@ int full_sinkhorn_noalloc_impl(const double* mu, const double* nu, const double*
   for (;;) {
     const double kap = std::isfinite(lam) ? e / (1.0 + e / lam) : e;
     const double q = h * h / e;
-    k_to_log2<R><<<grid, 256, 0, st>>>(beta, lognu, 1.0 / e, in2, n);
-    lse_all<R>(in2, tmp, w2, N, q, variant, 0, st);
+    k_to_log2<R><<<grid, 256, 0, st>>>(beta, lognu, 1.0 / e, in2, n, in2f);
+    lse_all<R>(in2, tmp, w2, N, q, variant, 0, st, in2f, tmpf);
     int it = 0, shift_ok = 0;
     bool conv = false;
     while (it < maxit) {
       k_half<R><<<grid, 256, 0, st>>>(w2, kap, alpha, n);
-      k_to_log2<R><<<grid, 256, 0, st>>>(alpha, logmu, 1.0 / e, in2, n);
-      lse_all<R>(in2, tmp, z2, N, q, variant, shift_ok, st);
+      k_to_log2<R><<<grid, 256, 0, st>>>(alpha, logmu, 1.0 / e, in2, n, in2f);
+      lse_all<R>(in2, tmp, z2, N, q, variant, shift_ok, st, in2f, tmpf);
       k_half<R><<<grid, 256, 0, st>>>(z2, kap, beta, n);
-      k_to_log2<R><<<grid, 256, 0, st>>>(beta, lognu, 1.0 / e, in2, n);
-      lse_all<R>(in2, tmp, w2, N, q, variant, 1, st);
+      k_to_log2<R><<<grid, 256, 0, st>>>(beta, lognu, 1.0 / e, in2, n, in2f);
+      lse_all<R>(in2, tmp, w2, N, q, variant, 1, st, in2f, tmpf);
       shift_ok = 1;
       ++it;
       if (it % check_every == 0 || it == maxit) {
@@ -410,7 +467,7 @@ int domdec_full_sinkhorn_noalloc(const double* mu, const double* nu, int N, doub
   double* logmu = base;
   double* lognu = base + n;
   double* work = base + 2 * (long long)n;
-  double* d_eval = base + 6LL * kNoAllocMaxN2;
+  double* d_eval = base + 7LL * kNoAllocMaxN2;
   int* d_status = reinterpret_cast<int*>(d_eval + 8);
   // every call starts from a cleared status word and its own beta
   cudaError_t e = cudaMemsetAsync(d_status, 0, sizeof(int), st);

@@ -11,7 +11,7 @@
 // theta = 1/|b|; decision on the device, deterministic fixed-order reductions.
 __global__ void __launch_bounds__(512)
 k_decide(DevState S, const CellDesc* __restrict__ cells, int begin, int nbatch, int slot) {
-  __shared__ double red[32 * 5];
+  __shared__ double red[33 * 5];
   __shared__ bool is_last;
   const int n = S.N * S.N;
   const double lam = S.lam, eps = S.eps, th_s = 1.0 / nbatch;
@@ -37,24 +37,28 @@ k_decide(DevState S, const CellDesc* __restrict__ cells, int begin, int nbatch, 
     is_last = (t == gridDim.x - 1);
   }
   __syncthreads();
-  if (!is_last || threadIdx.x != 0) return;
+  if (!is_last) return;
   __threadfence();
-  double tot[5] = {0, 0, 0, 0, 0};
-  for (int b = 0; b < (int)gridDim.x; ++b)
+  // last block: fixed-order reduction of the block partials and the per-cell terms
+  double tot[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
     for (int k = 0; k < 5; ++k) tot[k] += ((volatile double*)S.red)[b * 5 + k];
-  double dL = 0.0, dKX1 = 0.0, dKXs = 0.0;
-  for (int j = 0; j < nbatch; ++j) {
-    const CellOut o = S.cout[j];
+  for (int j = threadIdx.x; j < nbatch; j += blockDim.x) {
+    const CellOut& o = S.cout[j];
     if (o.status == CELL_EMPTY || o.status == CELL_TOOBIG) continue;
     const CellDesc cd = cells[begin + j];
     for (int q = 0; q < 4; ++q) {
       int bi = cd.mem[q];
       if (bi < 0) continue;
-      dL += (o.Ct[q] - S.Cc[bi]) + eps * (o.Ht[q] - S.Hh[bi]);
+      tot[5] += (o.Ct[q] - S.Cc[bi]) + eps * (o.Ht[q] - S.Hh[bi]);
     }
-    dKX1 += o.dKX[0];
-    dKXs += o.dKX[1];
+    tot[6] += o.dKX[0];
+    tot[7] += o.dKX[1];
   }
+  __shared__ double red8[33 * 8];
+  block_sum<8>(tot, red8);
+  if (threadIdx.x != 0) return;
+  const double dL = tot[5], dKX1 = tot[6], dKXs = tot[7];
   const double E0 = tot[4] + lam * tot[0] + lam * tot[1];
   const double Eg = E0 + dL + lam * dKX1 + lam * tot[2];
   const double Es = E0 + th_s * dL + lam * dKXs + lam * tot[3];
@@ -225,7 +229,7 @@ __global__ void k_prepare_inputs(const double* mu, const double* nu, double* log
 // and |mu_i| |nu|.  One block per basic cell.
 __global__ void __launch_bounds__(256)
 k_basic_masses(DevState S, const double* nu_mom, double* mumass) {
-  __shared__ double red[32 * 4];
+  __shared__ double red[33 * 4];
   const int i = blockIdx.x, s = S.s, I = i / S.nb, J = i % S.nb;
   double v[4] = {0, 0, 0, 0};
   for (int t = threadIdx.x; t < s * s; t += blockDim.x) {
@@ -245,7 +249,7 @@ k_basic_masses(DevState S, const double* nu_mom, double* mumass) {
 }
 
 __global__ void __launch_bounds__(512) k_moments(const double* nu, int N, double h, double* out) {
-  __shared__ double red[32 * 4];
+  __shared__ double red[33 * 4];
   double v[4] = {0, 0, 0, 0};
   for (int y = threadIdx.x; y < N * N; y += blockDim.x) {
     double m = nu[y], y1 = (y / N) * h, y2 = (y % N) * h;
@@ -317,7 +321,7 @@ k_init_duals(DevState S, const double* __restrict__ alpha0, const double* __rest
              double eps0, int mode) {
   extern __shared__ double tsm[];   // s * N doubles (mode 0)
   __shared__ int bb[4];
-  __shared__ double red[32 * 2];
+  __shared__ double red[33 * 2];
   const int i = blockIdx.x, s = S.s, N = S.N, I = i / S.nb, J = i % S.nb;
   const int r0 = I * s, c0 = J * s;
   const double q = S.h * S.h / eps0;
@@ -395,7 +399,7 @@ k_init_duals(DevState S, const double* __restrict__ alpha0, const double* __rest
 // ================================================================ reductions
 // out: [sum_i (C_i + eps H_i), lam KL(P_X|mu), lam KL(P_Y|nu), |P_Y|, box entries]
 __global__ void __launch_bounds__(512) k_score(DevState S, double* out) {
-  __shared__ double red[32 * 5];
+  __shared__ double red[33 * 5];
   const int n = S.N * S.N;
   double v[5] = {0, 0, 0, 0, 0};
   for (int y = threadIdx.x; y < n; y += blockDim.x) {
@@ -419,7 +423,7 @@ __global__ void __launch_bounds__(512) k_score(DevState S, double* out) {
 //       |mu|, |nu|, L1 X error, L1 Y error]
 __global__ void __launch_bounds__(512)
 k_cert(DevState S, const double* z, double* beta_out, double* out) {
-  __shared__ double red[32 * 7];
+  __shared__ double red[33 * 7];
   const int n = S.N * S.N;
   const double eps = S.eps, lam = S.lam, kap = eps / (1.0 + eps / lam);
   double v[7] = {0, 0, 0, 0, 0, 0, 0};

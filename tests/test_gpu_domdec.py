@@ -157,7 +157,7 @@ def test_fp32_converges_to_oracle_optimum(dd):
     a, b, it, gap = uot.full_sinkhorn(mu, nu, C, eps, lam, err=1e-12, maxit=20000)
     pi = uot.plan(a, b, C, mu, nu, eps)
     Eopt = uot.primal_score(pi, C, mu, nu, eps, lam)
-    g = dd.DomDec(mu, nu, eps, lam, s, precision="fp32", err=1e-11, maxit=1000, tau=0.0)
+    g = dd.DomDec(mu, nu, eps, lam, s, precision="fp32", err=1e-12, maxit=2000, tau=0.0)
     g.iterate(30)
     g.sync()
     E = g.score()[0]
@@ -233,7 +233,7 @@ def test_fp64_spilled_boxes_match_oracle(dd):
     mu, nu = mu.ravel(), nu.ravel()
     eps = (1 / 32) ** 2
     st = odd.init_product(geo, mu, nu, eps, 1.0)
-    g = dd.DomDec(mu, nu, eps, 1.0, 4, precision="fp64", max_ny=256, spill_slots=2)
+    g = dd.DomDec(mu, nu, eps, 1.0, 4, precision="fp64", max_ny=256, spill_slots=4)
     for k in range(2):
         odd.sweep(st, "AB"[k], "staggered")
         g.iterate(1)
