@@ -141,6 +141,38 @@ __device__ __forceinline__ R newton_u(R lr, R c0, R s, int maxit) {
   return u;
 }
 
+// Two independent roots of newton_u advanced in lock-step (their dependency
+// chains interleave; each stops on its own tolerance).
+template <typename R>
+__device__ __forceinline__ void newton_u2(const R (&lr)[2], const R (&c0)[2], R s, int maxit, R (&u)[2]) {
+  const R L2E = R(DD_LOG2E), LN2 = R(DD_LN2);
+  const R one_s = R(1) + s;
+  const R tol = sizeof(R) == 4 ? R(2e-6) : R(1e-14);
+  bool act[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    u[k] = -c0[k] / one_s;
+    act[k] = lr[k] > -dd_inf<R>();
+    if (act[k] && s > R(0)) u[k] = min(u[k], -(lr[k] + c0[k]) / s);
+  }
+  for (int it = 0; it < maxit && (act[0] || act[1]); ++it) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      R t = lr[k] - u[k];
+      R e = dd_ex2(-fabs(t) * L2E);
+      R ie = dd_rcp(R(1) + e);
+      R sp = max(t, R(0)) + dd_lg2(R(1) + e) * LN2;
+      R sig = t >= R(0) ? ie : e * ie;
+      R g = one_s * u[k] + c0[k] + sp;
+      R du = g * dd_rcp(one_s - sig);
+      if (act[k]) {
+        u[k] -= du;
+        if (fabs(du) <= tol * max(R(1), fabs(u[k]))) act[k] = false;
+      }
+    }
+  }
+}
+
 __device__ __forceinline__ double box_value(const BoxRec& b, const double* arena, int y1, int y2) {
   int a = y1 - b.k0, c = y2 - b.l0;
   if (a < 0 || c < 0 || a >= b.H || c >= b.W) return 0.0;
@@ -235,16 +267,22 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbat
   R* lnu = bv + cap_ny;
 
   // ------------------------------------------------------- frame constants
-  // Y frame origin: the pixel nearest to the barycentre of the cell's current
-  // Y-marginal nu_J, so that 2 q D.xi carries the cell's mean displacement.
+  // Y side (a1): rho = max(0, P_Y - nu_J)/nu and log nu on B_J; the same pass
+  // accumulates the barycentre of nu_J, whose nearest pixel is the Y frame
+  // origin (so that 2 q D.xi carries the cell's mean displacement).
   {
     double m3[3] = {0.0, 0.0, 0.0};
     for (int u = tid; u < ny; u += nthr) {
       int kk = u / W, ll = u - kk * W;
-      double v = 0.0;
+      int y1 = k0 + kk, y2 = l0 + ll, y = y1 * N + y2;
+      double nuJ = 0.0;
 #pragma unroll
-      for (int q4 = 0; q4 < 4; ++q4) v += box_value(sbox[q4], arena, k0 + kk, l0 + ll);
-      m3[0] += v; m3[1] += v * kk; m3[2] += v * ll;
+      for (int q4 = 0; q4 < 4; ++q4) nuJ += box_value(sbox[q4], arena, y1, y2);
+      double nuy = S.nu[y];
+      R rho = R(fmax(0.0, S.PY[y] - nuJ)) / R(nuy);
+      lrho[u] = rho > R(0) ? dd_lg2(rho) * R(DD_LN2) : -dd_inf<R>();
+      lnu[u] = R(S.lognu[y]);
+      m3[0] += nuJ; m3[1] += nuJ * kk; m3[2] += nuJ * ll;
     }
     block_sum<3>(m3, red);
     if (tid == 0) {
@@ -295,17 +333,6 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbat
     g0[t] = R(-sl * (A + lin));
     xa[t] = (a + l) * R(DD_LOG2E);
   }
-  // ------------------------------------------------------- load Y side (a1)
-  for (int u = tid; u < ny; u += nthr) {
-    int kk = u / W, ll = u - kk * W;
-    int y1 = k0 + kk, y2 = l0 + ll, y = y1 * N + y2;
-    double nuJ = 0.0;
-#pragma unroll
-    for (int q4 = 0; q4 < 4; ++q4) nuJ += box_value(sbox[q4], arena, y1, y2);
-    double rho = fmax(0.0, S.PY[y] - nuJ) / S.nu[y];
-    lrho[u] = rho > 0.0 ? R(log(rho)) : -dd_inf<R>();
-    lnu[u] = R(S.lognu[y]);
-  }
   __syncthreads();
 
   // ------------------------------------------------------- Sinkhorn loop
@@ -329,23 +356,37 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbat
       }
     }
     __syncthreads();
-    // Y-half, pass over rows of X, then the Newton root per y (a3)
+    // Y-half, pass over rows of X: Z(kk, ll) = log2 sum_r 2^{T(r, ll) - q2 (r - kk - offr)^2}
     {
-      const int ni = (ny + 31) & ~31;
+      const int P = lanes_per_target(ny, nx1, nthr), ni = (ny * P + 31) & ~31;
       for (int i = tid; i < ni; i += nthr) {
-        const int u = min(i, ny - 1);
+        const int u0 = i / P, part = i - u0 * P, u = min(u0, ny - 1);
         const int kk = u / W, ll = u - kk * W;
-        R Z2 = lse2_group<R>([&](int m) { return T[m * W + ll]; }, nx1, R(kk + offr), q2, Zv[u], !first, 0, 1);
-        if (i < ny) {
-          Zv[u] = Z2;
-          R Zn = Z2 * LN2;
-          R eta1 = R(k0 + kk - yc1), eta2 = R(l0 + ll - yc2);
-          R c0 = sB - cEta1 * eta1 - cEta2 * eta2 - sR * Zn;
-          R uu = newton_u<R>(lrho[u], c0, sR, S.newton_maxit);
-          R b = uu - Zn;
-          bv[u] = b;
-          bl[u] = (b + lnu[u]) * L2E;
-        }
+        R Z2 = lse2_group<R>([&](int m) { return T[m * W + ll]; }, nx1, R(kk + offr), q2, Zv[u], !first, part, P);
+        __syncwarp();
+        if (part == 0 && u0 < ny) Zv[u] = Z2;
+      }
+    }
+    __syncthreads();
+    // Newton root per y (a3), two roots per thread in lock-step
+    for (int u = tid; u < ny; u += 2 * nthr) {
+      const int uu[2] = {u, min(u + nthr, ny - 1)};
+      R lr[2], c0[2], root[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int kk = uu[k] / W, ll = uu[k] - kk * W;
+        R Zn = Zv[uu[k]] * LN2;
+        R eta1 = R(k0 + kk - yc1), eta2 = R(l0 + ll - yc2);
+        c0[k] = sB - cEta1 * eta1 - cEta2 * eta2 - sR * Zn;
+        lr[k] = lrho[uu[k]];
+      }
+      newton_u2<R>(lr, c0, sR, S.newton_maxit, root);
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        if (k == 1 && u + nthr >= ny) break;
+        R b = root[k] - Zv[uu[k]] * LN2;
+        bv[uu[k]] = b;
+        bl[uu[k]] = (b + lnu[uu[k]]) * L2E;
       }
     }
     __syncthreads();
@@ -406,7 +447,7 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbat
       int xi1 = cd.i0 + r - xc1, xi2 = cd.j0 + c - xc2;
       double a = (double)av[t];
       S.alpha[x] = eps * (A + a + 2.0 * q * (double)(D1 * xi1 + D2 * xi2));
-      double p1 = exp((double)lm[t] + a + (double)Wv[t] * DD_LN2);
+      double p1 = (double)dd_ex2((lm[t] + av[t]) * L2E + Wv[t]);
       S.PXnew[x] = p1;
       double p0 = S.PX[x], m = S.mu[x];
       double ps = (1.0 - th_s) * p0 + th_s * p1;
@@ -417,9 +458,9 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbat
   }
   block_sum<2>(dk, red);
 
-  double hs[12];
+  R hs[12];
 #pragma unroll
-  for (int k = 0; k < 12; ++k) hs[k] = 0.0;
+  for (int k = 0; k < 12; ++k) hs[k] = R(0);
   const int nhr = nx1 > s ? 2 : 1, nhc = nx2 > s ? 2 : 1;
   int nst;
   double* nut;
@@ -474,10 +515,10 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbat
         }
         R isw = R(1) / sw;
         const int qd = 2 * hr + hc;
-        double nt = nuy * exp((double)bv[u] + (double)P2 * DD_LN2);
-        nut[qd * nst + u] = nt;
-        hs[qd] += nt * ((double)(sa * isw) + (double)bv[u]);
-        hs[4 + qd] += h2 * nt * (double)(sd * isw);
+        R nt = R(nuy) * dd_ex2(bv[u] * L2E + P2);
+        nut[qd * nst + u] = (double)nt;
+        hs[qd] += nt * (sa * isw + bv[u]);
+        hs[4 + qd] += nt * (sd * isw);
         hs[8 + qd] += nt;
       }
     }
@@ -497,7 +538,10 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbat
     }
     if (dlt != 0.0) atomicAdd(S.dPY + y1 * N + y2, dlt);
   }
-  block_sum<12>(hs, red);
+  double hsd[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) hsd[k] = (double)hs[k];
+  block_sum<12>(hsd, red);
   if (tid == 0) {
     CellOut o;
     o.k0 = k0; o.l0 = l0; o.H = H; o.W = W;
@@ -509,9 +553,9 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbat
     o.dKX[0] = dk[0]; o.dKX[1] = dk[1];
     for (int q4 = 0; q4 < 4; ++q4) {
       int bi = cd.mem[q4];
-      o.Ct[q4] = hs[4 + q4];
-      o.mass[q4] = hs[8 + q4];
-      o.Ht[q4] = bi >= 0 ? hs[q4] - hs[8 + q4] + S.muinu[bi] : 0.0;
+      o.Ct[q4] = h2 * hsd[4 + q4];
+      o.mass[q4] = hsd[8 + q4];
+      o.Ht[q4] = bi >= 0 ? hsd[q4] - hsd[8 + q4] + S.muinu[bi] : 0.0;
     }
     *out = o;
     atomicAdd(S.counters + 0, (unsigned long long)it);
