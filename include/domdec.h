@@ -76,6 +76,8 @@ typedef struct {
   int    profile;      /* 1: time every kernel of a sweep with CUDA events on the handle's stream */
   int    spill_slots;  /* cells whose Y-box exceeds max_ny run from global memory slots: 0 = default
                           (up to 4 GiB), > 0 = that many, < 0 = none (such cells fail with DOMDEC_ETOOBIG) */
+  int    cell_ctas;    /* CTAs per cell: 0 = a 2-CTA cluster when all cells of a sub-batch fit as resident
+                          clusters (else 1), 1 = always one CTA per cell */
 } domdec_params;
 
 typedef struct {

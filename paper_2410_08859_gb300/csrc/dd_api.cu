@@ -17,7 +17,8 @@
 // ---- kernels' launch wrappers (dd_cell.cu, dd_sweep.cu, dd_sinkhorn.cu)
 size_t cell_smem_bytes(int s, int cap_side, int cap_ny, int precision);
 cudaError_t launch_cell_solve(const DevState& S, const CellDesc* cells, int begin, int nbatch, int precision,
-                              cudaStream_t st);
+                              int csize, cudaStream_t st);
+int cell_max_pair_clusters(int s, int cap_side, int cap_ny, int precision);
 cudaError_t launch_decide(const DevState& S, const CellDesc* cells, int begin, int nbatch, int slot,
                           cudaStream_t st);
 cudaError_t launch_apply(const DevState& S, const CellDesc* cells, int begin, int nbatch, cudaStream_t st);
@@ -66,6 +67,7 @@ struct domdec_s {
   long long slot = 0;
   int sticky = 0;
   int last_batch = 0;
+  int max_pairs = 0;  // co-resident 2-CTA clusters of the cell kernel
   // graphs: one sweep per partition
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   bool graph_ok = true;
@@ -229,7 +231,9 @@ int enqueue_sweep(domdec_s* h, int part, long long slot0) {
     if (nbt <= 0) continue;
     const int slot = (int)((slot0 + k++) % LOGCAP);
     cudaEvent_t ev = prof_begin(h);
-    if (launch_cell_solve(h->S, h->d_cells[part], begin, nbt, prec, h->st) != cudaSuccess) return DOMDEC_ECUDA;
+    const int csize = (h->p.cell_ctas != 1 && nbt <= h->max_pairs) ? 2 : 1;
+    if (launch_cell_solve(h->S, h->d_cells[part], begin, nbt, prec, csize, h->st) != cudaSuccess)
+      return DOMDEC_ECUDA;
     prof_end(h, ev, 0);
     ev = prof_begin(h);
     if (launch_decide(h->S, h->d_cells[part], begin, nbt, slot, h->st) != cudaSuccess) return DOMDEC_ECUDA;
@@ -339,6 +343,7 @@ int domdec_init(domdec_t* out, const double* mu, const double* nu, int N, const 
   }
   S.cap_ny = cap_ny;
   S.cap_side = cap_side;
+  h->max_pairs = pin->cell_ctas == 1 ? 0 : cell_max_pair_clusters(h->s, cap_side, cap_ny, pin->precision);
   if (cell_smem_bytes(h->s, cap_side, cap_ny, pin->precision) > (size_t)smem_optin) {
     delete h;
     return DOMDEC_EINVAL;

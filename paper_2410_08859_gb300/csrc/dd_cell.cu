@@ -19,6 +19,8 @@
 //    a(xi) + b(eta) - q |xi - eta|^2 exactly; a and b stay moderate while alpha/eps is ~1e4-1e5.
 //  * exp/log are ex2.approx/lg2.approx in log2 units; each 1-D log-sum-exp is shifted by the
 //    previous iteration's value (one pass), with an exact max-shifted fallback.
+#include <cooperative_groups.h>
+
 #include "dd_common.cuh"
 
 namespace {
@@ -142,9 +144,13 @@ __device__ __forceinline__ R newton_u(R lr, R c0, R s, int maxit) {
 }
 
 // Two independent roots of newton_u advanced in lock-step (their dependency
-// chains interleave; each stops on its own tolerance).
+// chains interleave; each stops on its own tolerance).  `uw` holds a previous
+// root per target (or NaN): one Newton step from it lands right of the root
+// (g is convex and increasing), and the start is the smaller of that point and
+// the bound min(u0, u1), so the iteration still descends monotonically.
 template <typename R>
-__device__ __forceinline__ void newton_u2(const R (&lr)[2], const R (&c0)[2], R s, int maxit, R (&u)[2]) {
+__device__ __forceinline__ void newton_u2(const R (&lr)[2], const R (&c0)[2], const R (&uw)[2], R s, int maxit,
+                                          R (&u)[2]) {
   const R L2E = R(DD_LOG2E), LN2 = R(DD_LN2);
   const R one_s = R(1) + s;
   const R tol = sizeof(R) == 4 ? R(2e-6) : R(1e-14);
@@ -154,6 +160,19 @@ __device__ __forceinline__ void newton_u2(const R (&lr)[2], const R (&c0)[2], R 
     u[k] = -c0[k] / one_s;
     act[k] = lr[k] > -dd_inf<R>();
     if (act[k] && s > R(0)) u[k] = min(u[k], -(lr[k] + c0[k]) / s);
+  }
+  // probe step from the previous roots
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    R w = uw[k];
+    R t = lr[k] - w;
+    R e = dd_ex2(-fabs(t) * L2E);
+    R ie = dd_rcp(R(1) + e);
+    R sp = max(t, R(0)) + dd_lg2(R(1) + e) * LN2;
+    R sig = t >= R(0) ? ie : e * ie;
+    R g = one_s * w + c0[k] + sp;
+    R wn = w - g * dd_rcp(one_s - sig);
+    if (act[k] && wn == wn && wn < u[k]) u[k] = wn;
   }
   for (int it = 0; it < maxit && (act[0] || act[1]); ++it) {
 #pragma unroll
@@ -181,20 +200,38 @@ __device__ __forceinline__ double box_value(const BoxRec& b, const double* arena
 
 }  // namespace
 
+// One composite cell per CTA (csize = 1) or per pair of CTAs in a thread-block
+// cluster (csize = 2).  With a pair, both CTAs load the whole cell state, every
+// pass splits its targets between them and writes each result into both
+// CTAs' shared memory (distributed shared memory); pass boundaries are cluster
+// barriers.
 template <typename R>
 __global__ void __launch_bounds__(512, 1)
-k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbatch) {
+k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbatch, int csize) {
+  namespace cg = cooperative_groups;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* red = reinterpret_cast<double*>(smem_raw);  // 32 * 16 doubles (block reductions)
   __shared__ BoxRec sbox[4];
   __shared__ int sgeo[8];
+  __shared__ double xchg[16];                         // cross-CTA partial sums
 
-  const CellDesc cd = cells[begin + blockIdx.x];
-  CellOut* out = S.cout + blockIdx.x;
+  const int crank = csize > 1 ? (int)cg::this_cluster().block_rank() : 0;
+  const int cidx = blockIdx.x / csize;
+  const CellDesc cd = cells[begin + cidx];
+  CellOut* out = S.cout + cidx;
   const double* __restrict__ arena = S.arena[*S.cur];
   const int tid = threadIdx.x, nthr = blockDim.x;
+  const int gtid = crank * nthr + tid, gthr = csize * nthr;  // thread index / count across the pair
   const int N = S.N, s = S.s;
   const int nx1 = cd.nx1, nx2 = cd.nx2, nx = nx1 * nx2;
+  auto csync = [&]() {
+    if (csize > 1) cg::this_cluster().sync();
+    else __syncthreads();
+  };
+  // address of the same shared-memory object in the partner CTA (nullptr without a pair)
+  auto peer = [&](auto* p) -> decltype(p) {
+    return csize > 1 ? cg::this_cluster().map_shared_rank(p, crank ^ 1) : nullptr;
+  };
 
   // ---------------------------------------------------------------- B_J
   if (tid == 0) {
@@ -216,18 +253,26 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbat
       k1 = min(N, k1 + S.margin); l1 = min(N, l1 + S.margin);
       int H = k1 - k0, W = l1 - l0;
       // boxes beyond the shared-memory capacity run from a global spill slot
-      if (H * W > S.cap_ny || H > S.cap_side || W > S.cap_side) {
+      // (taken once per cell, by the first CTA of a pair)
+      if ((H * W > S.cap_ny || H > S.cap_side || W > S.cap_side) && crank == 0) {
         int sl = S.spill_slots > 0 ? (int)atomicAdd(S.spill_count, 1u) : S.spill_slots;
         if (sl >= S.spill_slots) st = CELL_TOOBIG;
         else slot = sl;
       }
     }
-    sgeo[0] = k0; sgeo[1] = l0; sgeo[2] = k1 - k0; sgeo[3] = l1 - l0; sgeo[4] = st; sgeo[7] = slot;
+    sgeo[0] = k0; sgeo[1] = l0; sgeo[2] = k1 - k0; sgeo[3] = l1 - l0;
+    if (crank == 0) {
+      sgeo[4] = st; sgeo[7] = slot;
+      if (csize > 1) {
+        int* ps = peer(sgeo);
+        ps[4] = st; ps[7] = slot;
+      }
+    }
   }
-  __syncthreads();
+  csync();
   const int k0 = sgeo[0], l0 = sgeo[1], H = sgeo[2], W = sgeo[3];
   if (sgeo[4] != CELL_OK) {
-    if (tid == 0) {
+    if (tid == 0 && crank == 0) {
       CellOut o;
       o.k0 = k0; o.l0 = l0; o.H = H; o.W = W; o.iters = 0; o.status = sgeo[4];
       o.D1 = o.D2 = 0; o.gap = 0.0; o.dKX[0] = o.dKX[1] = 0.0; o.slot = -1; o.pad = 0;
@@ -246,7 +291,7 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbat
 
   // ------------------------------------------------------- shared layout
   // X-side arrays always live in shared memory; the Y-side arrays too unless
-  // the box exceeds the shared capacity, then in this block's spill area
+  // the box exceeds the shared capacity, then in the cell's spill slot
   // (global memory, L2-resident) sized for an N x N box.
   const int cap_nx = 4 * s * s;
   const int slot = sgeo[7];
@@ -258,18 +303,36 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbat
   R* g0 = av + cap_nx;
   R* Wv = g0 + cap_nx;
   R* lm = Wv + cap_nx;
-  R* T = spilled ? reinterpret_cast<R*>(S.spill + (long long)slot * S.spill_stride) : lm + cap_nx;
+  R* xa_nx = lm + cap_nx;    // next iterate of xa / a (double buffer of the X-update)
+  R* av_nx = xa_nx + cap_nx;
+  R* T = spilled ? reinterpret_cast<R*>(S.spill + (long long)slot * S.spill_stride) : av_nx + cap_nx;
   R* U = T + tsz;
   R* bl = U + tsz;
   R* lrho = bl + cap_ny;
   R* Zv = lrho + cap_ny;
   R* bv = Zv + cap_ny;
   R* lnu = bv + cap_ny;
+  // partner copies (Y-side arrays in a spill slot are shared, nothing to copy)
+  R* const xa_p = peer(xa);
+  R* const av_p = peer(av);
+  R* const xanx_p = peer(xa_nx);
+  R* const avnx_p = peer(av_nx);
+  R* const Wv_p = peer(Wv);
+  R* const T_p = spilled ? nullptr : peer(T);
+  R* const U_p = spilled ? nullptr : peer(U);
+  R* const bl_p = spilled ? nullptr : peer(bl);
+  R* const Zv_p = spilled ? nullptr : peer(Zv);
+  R* const bv_p = spilled ? nullptr : peer(bv);
+  auto put = [](R* a, R* ap, int i, R v) {
+    a[i] = v;
+    if (ap) ap[i] = v;
+  };
 
-  // ------------------------------------------------------- frame constants
-  // Y side (a1): rho = max(0, P_Y - nu_J)/nu and log nu on B_J; the same pass
-  // accumulates the barycentre of nu_J, whose nearest pixel is the Y frame
-  // origin (so that 2 q D.xi carries the cell's mean displacement).
+  // ------------------------------------------------------- load Y side (a1)
+  // rho = max(0, P_Y - nu_J)/nu and log nu on B_J; the same pass accumulates
+  // the barycentre of nu_J, whose nearest pixel is the Y frame origin (so
+  // that 2 q D.xi carries the cell's mean displacement).  Both CTAs of a
+  // pair load everything.
   {
     double m3[3] = {0.0, 0.0, 0.0};
     for (int u = tid; u < ny; u += nthr) {
@@ -280,8 +343,10 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbat
       for (int q4 = 0; q4 < 4; ++q4) nuJ += box_value(sbox[q4], arena, y1, y2);
       double nuy = S.nu[y];
       R rho = R(fmax(0.0, S.PY[y] - nuJ)) / R(nuy);
-      lrho[u] = rho > R(0) ? dd_lg2(rho) * R(DD_LN2) : -dd_inf<R>();
-      lnu[u] = R(S.lognu[y]);
+      if (!spilled || crank == 0) {
+        lrho[u] = rho > R(0) ? dd_lg2(rho) * R(DD_LN2) : -dd_inf<R>();
+        lnu[u] = R(S.lognu[y]);
+      }
       m3[0] += nuJ; m3[1] += nuJ * kk; m3[2] += nuJ * ll;
     }
     block_sum<3>(m3, red);
@@ -333,121 +398,166 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbat
     g0[t] = R(-sl * (A + lin));
     xa[t] = (a + l) * R(DD_LOG2E);
   }
-  __syncthreads();
+  csync();
 
   // ------------------------------------------------------- Sinkhorn loop
+  // Barriers per iteration: after each of the five passes.  The X-update is
+  // computed speculatively inside the last pass into the second buffer, and
+  // the gap is reduced from per-warp partials after that pass's barrier.
   const double tol = S.err * muJ;
   const R LN2 = R(DD_LN2), L2E = R(DD_LOG2E);
+  R* gpart = reinterpret_cast<R*>(red) + 32 * 12;   // per-warp gap partials of both CTAs
+  R* const gpart_p = peer(gpart);
+  const int lane = tid & 31, wid = tid >> 5, nwarp = nthr >> 5;
   int it = 0;
   double gap = 0.0;
   bool first = true;
+  const bool fused_y = ny * 2 > gthr;   // large boxes: one lane per y, LSE and Newton fused
+  R *xa_c = xa, *xa_cp = xa_p, *av_c = av, *av_cp = av_p;          // current iterate
+  R *xa_n = xa_nx, *xa_np = xanx_p, *av_n = av_nx, *av_np = avnx_p;  // next iterate
   for (;;) {
     ++it;
     // Y-half, pass over columns of X: T(r, ll) = log2 sum_c 2^{xa(r,c) - q2 (c - ll - offc)^2}
     {
-      const int nt = nx1 * W, P = lanes_per_target(nt, nx2, nthr), ni = (nt * P + 31) & ~31;
-      for (int i = tid; i < ni; i += nthr) {
+      const int nt = nx1 * W, P = lanes_per_target(nt, nx2, gthr), ni = (nt * P + 31) & ~31;
+      for (int i = gtid; i < ni; i += gthr) {
         const int tg0 = i / P, part = i - tg0 * P, tg = min(tg0, nt - 1);
         const int r = tg / W, ll = tg - r * W;
-        const R* row = xa + r * nx2;
+        const R* row = xa_c + r * nx2;
         R v = lse2_group<R>([&](int m) { return row[m]; }, nx2, R(ll + offc), q2, T[tg], !first, part, P);
         __syncwarp();
-        if (part == 0 && tg0 < nt) T[tg] = v;
+        if (part == 0 && tg0 < nt) put(T, T_p, tg, v);
       }
     }
-    __syncthreads();
-    // Y-half, pass over rows of X: Z(kk, ll) = log2 sum_r 2^{T(r, ll) - q2 (r - kk - offr)^2}
-    {
-      const int P = lanes_per_target(ny, nx1, nthr), ni = (ny * P + 31) & ~31;
-      for (int i = tid; i < ni; i += nthr) {
+    csync();
+    // Y-half, pass over rows of X: Z(kk, ll), then the Newton root per y (a3)
+    if (fused_y) {
+      // every lane runs the same number of rounds (lse2_group is warp-collective)
+      const int rounds = (ny + 2 * gthr - 1) / (2 * gthr);
+      for (int rd = 0; rd < rounds; ++rd) {
+        const int u = gtid + rd * 2 * gthr;
+        const int uu[2] = {min(u, ny - 1), min(u + gthr, ny - 1)};
+        const bool ok[2] = {u < ny, u + gthr < ny};
+        R lr[2], c0[2], uw[2], root[2], Zn[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int kk = uu[k] / W, ll = uu[k] - kk * W;
+          R Z2 = lse2_group<R>([&](int m) { return T[m * W + ll]; }, nx1, R(kk + offr), q2, Zv[uu[k]], !first, 0, 1);
+          Zn[k] = Z2 * LN2;
+          R eta1 = R(k0 + kk - yc1), eta2 = R(l0 + ll - yc2);
+          c0[k] = sB - cEta1 * eta1 - cEta2 * eta2 - sR * Zn[k];
+          lr[k] = lrho[uu[k]];
+          uw[k] = first ? dd_inf<R>() : bv[uu[k]] + Zn[k];
+        }
+        newton_u2<R>(lr, c0, uw, sR, S.newton_maxit, root);
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          if (!ok[k]) continue;
+          put(Zv, Zv_p, uu[k], Zn[k] * L2E);
+          R b = root[k] - Zn[k];
+          put(bv, bv_p, uu[k], b);
+          put(bl, bl_p, uu[k], (b + lnu[uu[k]]) * L2E);
+        }
+      }
+    } else {
+      const int P = lanes_per_target(ny, nx1, gthr), ni = (ny * P + 31) & ~31;
+      for (int i = gtid; i < ni; i += gthr) {
         const int u0 = i / P, part = i - u0 * P, u = min(u0, ny - 1);
         const int kk = u / W, ll = u - kk * W;
         R Z2 = lse2_group<R>([&](int m) { return T[m * W + ll]; }, nx1, R(kk + offr), q2, Zv[u], !first, part, P);
         __syncwarp();
-        if (part == 0 && u0 < ny) Zv[u] = Z2;
+        if (part == 0 && u0 < ny) put(Zv, Zv_p, u, Z2);
+      }
+      csync();
+      for (int u = gtid; u < ny; u += 2 * gthr) {
+        const int uu[2] = {u, min(u + gthr, ny - 1)};
+        R lr[2], c0[2], uw[2], root[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int kk = uu[k] / W, ll = uu[k] - kk * W;
+          R Zn = Zv[uu[k]] * LN2;
+          R eta1 = R(k0 + kk - yc1), eta2 = R(l0 + ll - yc2);
+          c0[k] = sB - cEta1 * eta1 - cEta2 * eta2 - sR * Zn;
+          lr[k] = lrho[uu[k]];
+          uw[k] = first ? dd_inf<R>() : bv[uu[k]] + Zn;
+        }
+        newton_u2<R>(lr, c0, uw, sR, S.newton_maxit, root);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          if (k == 1 && u + gthr >= ny) break;
+          R b = root[k] - Zv[uu[k]] * LN2;
+          put(bv, bv_p, uu[k], b);
+          put(bl, bl_p, uu[k], (b + lnu[uu[k]]) * L2E);
+        }
       }
     }
-    __syncthreads();
-    // Newton root per y (a3), two roots per thread in lock-step
-    for (int u = tid; u < ny; u += 2 * nthr) {
-      const int uu[2] = {u, min(u + nthr, ny - 1)};
-      R lr[2], c0[2], root[2];
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const int kk = uu[k] / W, ll = uu[k] - kk * W;
-        R Zn = Zv[uu[k]] * LN2;
-        R eta1 = R(k0 + kk - yc1), eta2 = R(l0 + ll - yc2);
-        c0[k] = sB - cEta1 * eta1 - cEta2 * eta2 - sR * Zn;
-        lr[k] = lrho[uu[k]];
-      }
-      newton_u2<R>(lr, c0, sR, S.newton_maxit, root);
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        if (k == 1 && u + nthr >= ny) break;
-        R b = root[k] - Zv[uu[k]] * LN2;
-        bv[uu[k]] = b;
-        bl[uu[k]] = (b + lnu[uu[k]]) * L2E;
-      }
-    }
-    __syncthreads();
+    csync();
     // X-half, pass over columns of B_J: U(kk, c) = log2 sum_ll 2^{bl(kk,ll) - q2 (ll - (c - offc))^2}
     {
-      const int nt = H * nx2, P = lanes_per_target(nt, W, nthr), ni = (nt * P + 31) & ~31;
-      for (int i = tid; i < ni; i += nthr) {
+      const int nt = H * nx2, P = lanes_per_target(nt, W, gthr), ni = (nt * P + 31) & ~31;
+      for (int i = gtid; i < ni; i += gthr) {
         const int tg0 = i / P, part = i - tg0 * P, tg = min(tg0, nt - 1);
         const int kk = tg / nx2, c = tg - kk * nx2;
         const R* row = bl + kk * W;
         R v = lse2_group<R>([&](int m) { return row[m]; }, W, R(c - offc), q2, U[tg], !first, part, P);
         __syncwarp();
-        if (part == 0 && tg0 < nt) U[tg] = v;
+        if (part == 0 && tg0 < nt) put(U, U_p, tg, v);
       }
     }
-    __syncthreads();
-    // X-half, pass over rows of B_J, and the PD gap (a4), accumulated in R
-    R gl[1] = {R(0)};
+    csync();
+    // X-half, pass over rows of B_J: W, the gap terms (a4) and the next a (a2)
     {
-      const int P = lanes_per_target(nx, H, nthr), ni = (nx * P + 31) & ~31;
-      for (int i = tid; i < ni; i += nthr) {
+      R gl = R(0);
+      const int P = lanes_per_target(nx, H, gthr), ni = (nx * P + 31) & ~31;
+      for (int i = gtid; i < ni; i += gthr) {
         const int tg0 = i / P, part = i - tg0 * P, t = min(tg0, nx - 1);
         const int r = t / nx2, c = t - r * nx2;
         R W2 = lse2_group<R>([&](int m) { return U[m * nx2 + c]; }, H, R(r - offr), q2, Wv[t], !first, part, P);
         __syncwarp();
         if (part == 0 && tg0 < nx) {
-          Wv[t] = W2;
-          R a = av[t];
+          put(Wv, Wv_p, t, W2);
+          R a = av_c[t];
           R tt = a + W2 * LN2;         // log(P_X pi / mu)
           R g = g0[t] - sR * a;        // -alpha/lam
-          gl[0] += dd_ex2((lm[t] + g) * L2E) * dd_psi<R>(tt - g);
+          gl += dd_ex2((lm[t] + g) * L2E) * dd_psi<R>(tt - g);
+          R xi1 = R(cd.i0 + r - xc1), xi2 = R(cd.j0 + c - xc2);
+          R an = cA - rR * W2 * LN2 - cD1 * xi1 - cD2 * xi2;
+          put(av_n, av_np, t, an);
+          put(xa_n, xa_np, t, (an + lm[t]) * L2E);
         }
       }
+      gl = warp_sum(gl);
+      if (lane == 0) put(gpart, gpart_p, crank * nwarp + wid, gl);
     }
-    block_sum<1>(gl, reinterpret_cast<R*>(red));
-    gap = (double)gl[0];
+    csync();
+    {
+      R gs = R(0);
+      for (int w = 0; w < csize * nwarp; ++w) gs += gpart[w];
+      gap = (double)gs;
+    }
     first = false;
     if ((S.err >= 0.0 && gap <= tol) || it >= S.maxit || !(gap == gap)) break;
-    // X-update (closed form, a2)
-    for (int t = tid; t < nx; t += nthr) {
-      int r = t / nx2, c = t - r * nx2;
-      R xi1 = R(cd.i0 + r - xc1), xi2 = R(cd.j0 + c - xc2);
-      R a = cA - rR * Wv[t] * LN2 - cD1 * xi1 - cD2 * xi2;
-      av[t] = a;
-      xa[t] = (a + lm[t]) * L2E;
-    }
-    __syncthreads();
+    // accept the X-update: swap the buffers (every thread of both CTAs does the same)
+    R* tp = av_c; av_c = av_n; av_n = tp;
+    tp = av_cp; av_cp = av_np; av_np = tp;
+    tp = xa_c; xa_c = xa_n; xa_n = tp;
+    tp = xa_cp; xa_cp = xa_np; xa_np = tp;
   }
   const bool nonfinite = !(gap == gap);
 
   // ------------------------------------------------------- epilogue (a5)
+  // alpha, P_X of the new plan and the KL_X change: first CTA only.
   double dk[2] = {0.0, 0.0};
-  {
+  if (crank == 0) {
     const double th_s = 1.0 / nbatch;
     for (int t = tid; t < nx; t += nthr) {
       int r = t / nx2, c = t - r * nx2;
       int x = (cd.i0 + r) * N + cd.j0 + c;
       int xi1 = cd.i0 + r - xc1, xi2 = cd.j0 + c - xc2;
-      double a = (double)av[t];
+      double a = (double)av_c[t];
       S.alpha[x] = eps * (A + a + 2.0 * q * (double)(D1 * xi1 + D2 * xi2));
-      double p1 = (double)dd_ex2((lm[t] + av[t]) * L2E + Wv[t]);
+      double p1 = (double)dd_ex2((lm[t] + av_c[t]) * L2E + Wv[t]);
       S.PXnew[x] = p1;
       double p0 = S.PX[x], m = S.mu[x];
       double ps = (1.0 - th_s) * p0 + th_s * p1;
@@ -455,8 +565,8 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbat
       dk[0] += dd_kl_term(p1, m) - k0v;
       dk[1] += dd_kl_term(ps, m) - k0v;
     }
+    block_sum<2>(dk, red);
   }
-  block_sum<2>(dk, red);
 
   R hs[12];
 #pragma unroll
@@ -467,18 +577,20 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbat
   {
     CellOut tmp;
     tmp.slot = slot;
-    nut = cell_nut(S, tmp, blockIdx.x, &nst);
+    nut = cell_nut(S, tmp, cidx, &nst);
   }
   R* Te = T;                 // epilogue scratch spans T, U, bl, lrho, Zv
   R* Ma = T + nx1 * W;
   R* Md = Ma + nx1 * W;
-  const double h2 = S.h * S.h;
+  R* const Te_p = spilled ? nullptr : peer(Te);
+  R* const Ma_p = spilled ? nullptr : peer(Ma);
+  R* const Md_p = spilled ? nullptr : peer(Md);
   for (int hc = 0; hc < nhc; ++hc) {
     const int cb = hc * s, ce = min(nx2, cb + s);
     // rows of X_J against columns of B_J, restricted to the column half hc
-    for (int t = tid; t < nx1 * W; t += nthr) {
+    for (int t = gtid; t < nx1 * W; t += gthr) {
       int r = t / W, ll = t - r * W;
-      const R* row = xa + r * nx2;
+      const R* row = xa_c + r * nx2;
       R ctr = R(ll + offc);
       R T2 = lse2_1d<R>([&](int m) { return row[cb + m]; }, ce - cb, ctr - R(cb), q2, R(0), false);
       R sw = 0, sa = 0, sd = 0;
@@ -486,17 +598,17 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbat
         R d = R(c) - ctr;
         R w = dd_ex2(row[c] - q2 * d * d - T2);
         sw += w;
-        sa += w * (av[r * nx2 + c] - qR * d * d);
+        sa += w * (av_c[r * nx2 + c] - qR * d * d);
         R dt = d + R(D2);
         sd += w * dt * dt;
       }
       R isw = R(1) / sw;
-      Te[t] = T2;
-      Ma[t] = sa * isw;
-      Md[t] = sd * isw;
+      put(Te, Te_p, t, T2);
+      put(Ma, Ma_p, t, sa * isw);
+      put(Md, Md_p, t, sd * isw);
     }
-    __syncthreads();
-    for (int u = tid; u < ny; u += nthr) {
+    csync();
+    for (int u = gtid; u < ny; u += gthr) {
       int kk = u / W, ll = u - kk * W;
       int y = (k0 + kk) * N + l0 + ll;
       R ctr = R(kk + offr);
@@ -522,10 +634,11 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbat
         hs[8 + qd] += nt;
       }
     }
-    __syncthreads();
+    __threadfence();
+    csync();
   }
   // change of P_Y pi for the step-size decision
-  for (int u = tid; u < ny; u += nthr) {
+  for (int u = gtid; u < ny; u += gthr) {
     int kk = u / W, ll = u - kk * W;
     int y1 = k0 + kk, y2 = l0 + ll;
     double dlt = 0.0;
@@ -542,6 +655,16 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbat
 #pragma unroll
   for (int k = 0; k < 12; ++k) hsd[k] = (double)hs[k];
   block_sum<12>(hsd, red);
+  if (csize > 1) {
+    // the second CTA hands its partial sums to the first
+    if (crank == 1 && tid == 0) {
+      double* px = peer(xchg);
+      for (int k = 0; k < 12; ++k) px[k] = hsd[k];
+    }
+    csync();
+    if (crank == 1) return;
+    for (int k = 0; k < 12; ++k) hsd[k] += xchg[k];
+  }
   if (tid == 0) {
     CellOut o;
     o.k0 = k0; o.l0 = l0; o.H = H; o.W = W;
@@ -553,7 +676,7 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbat
     o.dKX[0] = dk[0]; o.dKX[1] = dk[1];
     for (int q4 = 0; q4 < 4; ++q4) {
       int bi = cd.mem[q4];
-      o.Ct[q4] = h2 * hsd[4 + q4];
+      o.Ct[q4] = S.h * S.h * hsd[4 + q4];
       o.mass[q4] = hsd[8 + q4];
       o.Ht[q4] = bi >= 0 ? hsd[q4] - hsd[8 + q4] + S.muinu[bi] : 0.0;
     }
@@ -572,18 +695,59 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbat
 size_t cell_smem_bytes(int s, int cap_side, int cap_ny, int precision) {
   size_t rs = precision ? sizeof(double) : sizeof(float);
   size_t cap_nx = 4 * (size_t)s * s, tsz = 2 * (size_t)s * cap_side;
-  return 32 * 16 * sizeof(double) + rs * (5 * cap_nx + 2 * tsz + 5 * (size_t)cap_ny);
+  return 32 * 16 * sizeof(double) + rs * (7 * cap_nx + 2 * tsz + 5 * (size_t)cap_ny);
 }
 
-cudaError_t launch_cell_solve(const DevState& S, const CellDesc* cells, int begin, int nbatch,
-                              int precision, cudaStream_t st) {
-  size_t smem = cell_smem_bytes(S.s, S.cap_side, S.cap_ny, precision);
+// Largest number of 2-CTA clusters of the cell kernel that can be resident at once.
+int cell_max_pair_clusters(int s, int cap_side, int cap_ny, int precision) {
+  size_t smem = cell_smem_bytes(s, cap_side, cap_ny, precision);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2);
+  cfg.blockDim = dim3(512);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  cudaError_t e;
   if (precision) {
     cudaFuncSetAttribute(k_cell_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_cell_solve<double><<<nbatch, 512, smem, st>>>(S, cells, begin, nbatch);
+    e = cudaOccupancyMaxActiveClusters(&n, k_cell_solve<double>, &cfg);
   } else {
     cudaFuncSetAttribute(k_cell_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_cell_solve<float><<<nbatch, 512, smem, st>>>(S, cells, begin, nbatch);
+    e = cudaOccupancyMaxActiveClusters(&n, k_cell_solve<float>, &cfg);
   }
-  return cudaGetLastError();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+// csize = 2 launches one 2-CTA cluster per cell, csize = 1 one CTA per cell.
+cudaError_t launch_cell_solve(const DevState& S, const CellDesc* cells, int begin, int nbatch,
+                              int precision, int csize, cudaStream_t st) {
+  size_t smem = cell_smem_bytes(S.s, S.cap_side, S.cap_ny, precision);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nbatch * csize);
+  cfg.blockDim = dim3(512);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (precision) {
+    cudaFuncSetAttribute(k_cell_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaLaunchKernelEx(&cfg, k_cell_solve<double>, S, cells, begin, nbatch, csize);
+  }
+  cudaFuncSetAttribute(k_cell_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return cudaLaunchKernelEx(&cfg, k_cell_solve<float>, S, cells, begin, nbatch, csize);
 }

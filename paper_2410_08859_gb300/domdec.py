@@ -37,7 +37,8 @@ class domdec_params(ctypes.Structure):
                 ("newton_maxit", ctypes.c_int), ("precision", ctypes.c_int),
                 ("box_margin", ctypes.c_int), ("max_ny", ctypes.c_int),
                 ("arena_factor", ctypes.c_double), ("eps_init", ctypes.c_double),
-                ("profile", ctypes.c_int), ("spill_slots", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("spill_slots", ctypes.c_int),
+                ("cell_ctas", ctypes.c_int)]
 
 
 class domdec_stats(ctypes.Structure):

@@ -59,10 +59,11 @@ def compare_state(g, st, tol_score, tol_l1, tol_alpha, check_boxes=True, tol_box
 
 
 def run_pair(dd, N, s, mu, nu, eps, lam, sweeps, precision, strategy="staggered", err=2e-5, maxit=2000,
-             tau=0.0, thr=1e-15, tols=(1e-10, 1e-10, 1e-8), tol_box=1e-8, init_duals=None):
+             tau=0.0, thr=1e-15, tols=(1e-10, 1e-10, 1e-8), tol_box=1e-8, init_duals=None, cell_ctas=0):
     geo = odd.Geometry(N, s)
     mu, nu = mu.ravel(), nu.ravel()
-    kw = dict(precision=precision, strategy=strategy, err=err, maxit=maxit, tau=tau, trunc_thr=thr)
+    kw = dict(precision=precision, strategy=strategy, err=err, maxit=maxit, tau=tau, trunc_thr=thr,
+              cell_ctas=cell_ctas)
     if init_duals is None:
         st = odd.init_product(geo, mu, nu, eps, lam, thr)
         g = dd.DomDec(mu, nu, eps, lam, s, **kw)
@@ -93,11 +94,13 @@ def run_pair(dd, N, s, mu, nu, eps, lam, sweeps, precision, strategy="staggered"
     return g, st
 
 
-def test_fp64_sweeps_match_oracle_mix32(dd):
+@pytest.mark.parametrize("cell_ctas", [0, 1])
+def test_fp64_sweeps_match_oracle_mix32(dd, cell_ctas):
     """Small Gaussian-mixture workload (32 x 32, s = 4, eps = (1/32)^2, lam = 1,
-    FP64, pi0 = mu x nu): three sweeps, sub-batch by sub-batch."""
+    FP64, pi0 = mu x nu): three sweeps, sub-batch by sub-batch; cells solved by
+    2-CTA clusters (0: automatic) or by one CTA each (1)."""
     mu, nu = inputs.mixture_small(N=32, seed=1000)
-    g, st = run_pair(dd, 32, 4, mu, nu, (1 / 32) ** 2, 1.0, 3, "fp64")
+    g, st = run_pair(dd, 32, 4, mu, nu, (1 / 32) ** 2, 1.0, 3, "fp64", cell_ctas=cell_ctas)
     g.close()
 
 
@@ -136,12 +139,13 @@ def test_fp64_warm_start_from_duals(dd):
     g.close()
 
 
-def test_fp32_fixed_iterations_match_oracle(dd):
+@pytest.mark.parametrize("cell_ctas", [0, 1])
+def test_fp32_fixed_iterations_match_oracle(dd, cell_ctas):
     """FP32 cell arithmetic with exactly 12 cell iterations per solve: same
     decisions; scores and marginals within FP32 error of the FP64 oracle."""
     mu, nu = inputs.mixture_small(N=32, seed=1000)
     g, st = run_pair(dd, 32, 4, mu, nu, (1 / 32) ** 2, 1.0, 2, "fp32", err=-1.0, maxit=12,
-                     tols=(1e-6, 1e-5, 1e-4), tol_box=None)
+                     tols=(1e-6, 1e-5, 1e-4), tol_box=None, cell_ctas=cell_ctas)
     g.close()
 
 
