@@ -208,6 +208,26 @@ int domdec_full_sinkhorn(const double* mu, const double* nu, int N, double eps_s
                          const double* beta_in, double* alpha, double* beta,
                          double out[4], void* stream);
 
+/* Many independent problems swept together (many-instance batching): every
+ * launch of a sweep covers the cells of one staggered sub-batch of all
+ * instances, taken from a work queue by a persistent grid (larger grids
+ * first).  `handles` (n >= 1) must share precision and strategy and have done
+ * the same number of sweeps; N, eps, lambda, s may differ.  The batch does not
+ * own the handles; the handles stay usable (query them after
+ * domdec_batch_sync) and must outlive the batch.  Work is enqueued on the
+ * first handle's stream (give all handles the same stream). */
+typedef struct domdec_batch_s* domdec_batch_t;
+int domdec_batch_create(domdec_batch_t* out, domdec_t* handles, int n);
+/* n_sweeps sweeps of every instance (A, B, ... as for domdec_iterate).  Enqueues only. */
+int domdec_batch_iterate(domdec_batch_t b, int n_sweeps);
+/* domdec_sync of every handle; returns the first error, else the largest warning.  Synchronises. */
+int domdec_batch_sync(domdec_batch_t b);
+/* Autotuner: runs one sweep with one CTA per cell and one with a 2-CTA cluster
+ * per cell, times both (CUDA events) and keeps the higher cell-iteration rate
+ * for later sweeps; *chosen (if not NULL) receives 1 or 2.  Synchronises. */
+int domdec_batch_autotune(domdec_batch_t b, int* chosen);
+void domdec_batch_free(domdec_batch_t b);
+
 /* Allocation-free variant of domdec_full_sinkhorn (no counterpart in the
  * paper; it exists for callers that cannot allocate device memory while the
  * solver runs -- e.g. a process whose device memory is all handed to its own

@@ -19,8 +19,13 @@ size_t cell_smem_bytes(int s, int cap_side, int cap_ny, int precision);
 cudaError_t launch_cell_solve(const DevState& S, const CellDesc* cells, int begin, int nbatch, int precision,
                               int csize, cudaStream_t st);
 int cell_max_pair_clusters(int s, int cap_side, int cap_ny, int precision);
-cudaError_t launch_decide(const DevState& S, const CellDesc* cells, int begin, int nbatch, int slot,
-                          cudaStream_t st);
+cudaError_t launch_cell_solve_multi(const DevState* states, const CellRef* refs, int nref, int part,
+                                    unsigned int* queue, int s, int cap_side, int cap_ny, int precision, int csize,
+                                    int nctas, cudaStream_t st);
+cudaError_t launch_decide_multi(const DevState* states, int ninst, int maxn, int part, int sub, cudaStream_t st);
+cudaError_t launch_apply_multi(const DevState* states, const CellRef* refs, int nref, int part, cudaStream_t st);
+cudaError_t launch_compact_multi(const DevState* states, int ninst, int max_nbasic, cudaStream_t st);
+cudaError_t launch_decide(const DevState& S, const CellDesc* cells, int begin, int nbatch, cudaStream_t st);
 cudaError_t launch_apply(const DevState& S, const CellDesc* cells, int begin, int nbatch, cudaStream_t st);
 cudaError_t launch_compact(const DevState& S, long long* newoff, cudaStream_t st);
 cudaError_t launch_prepare_inputs(const double* mu, const double* nu, double* logmu, double* lognu, int n,
@@ -236,7 +241,7 @@ int enqueue_sweep(domdec_s* h, int part, long long slot0) {
       return DOMDEC_ECUDA;
     prof_end(h, ev, 0);
     ev = prof_begin(h);
-    if (launch_decide(h->S, h->d_cells[part], begin, nbt, slot, h->st) != cudaSuccess) return DOMDEC_ECUDA;
+    if (launch_decide(h->S, h->d_cells[part], begin, nbt, h->st) != cudaSuccess) return DOMDEC_ECUDA;
     prof_end(h, ev, 1);
     ev = prof_begin(h);
     if (launch_apply(h->S, h->d_cells[part], begin, nbt, h->st) != cudaSuccess) return DOMDEC_ECUDA;
@@ -381,6 +386,7 @@ int domdec_init(domdec_t* out, const double* mu, const double* nu, int N, const 
   DD_ALLOC(S.cout, std::max(1, mb));
   DD_ALLOC(S.nut, (size_t)std::max(1, mb) * 4 * cap_ny);
   DD_ALLOC(S.theta, 1); DD_ALLOC(S.declog, 4 * LOGCAP); DD_ALLOC(S.counters, NCOUNT);
+  DD_ALLOC(S.slotctr, 1);
   DD_ALLOC(S.status, 1); DD_ALLOC(S.red, 2 * 152 * 5 + 8); DD_ALLOC(S.red_count, 1);
   DD_ALLOC(h->d_newoff, h->nbasic + 1); DD_ALLOC(h->d_scratch, 64); DD_ALLOC(h->d_numom, 8);
   {
@@ -419,6 +425,13 @@ int domdec_init(domdec_t* out, const double* mu, const double* nu, int N, const 
     if (h->ncell[w])
       cudaMemcpyAsync(h->d_cells[w], cells[w].data(), cells[w].size() * sizeof(CellDesc),
                       cudaMemcpyHostToDevice, st);
+  for (int w = 0; w < 2; ++w) {
+    S.cells[w] = h->d_cells[w];
+    for (int b = 0; b < 5; ++b) S.sub_start[w][b] = h->sub_start[w][b];
+  }
+  S.staggered = pin->strategy == DOMDEC_STAGGERED;
+  S.newoff = h->d_newoff;
+  cudaMemsetAsync(S.slotctr, 0, sizeof(unsigned long long), st);
   if (e == cudaSuccess) e = launch_prepare_inputs(dmu, dnu, dlogmu, dlognu, n, S.status, st);
   if (e != cudaSuccess) { domdec_free(h); return DOMDEC_ECUDA; }
   // temporary arena pointers for the box pass (no values written yet)
@@ -710,4 +723,197 @@ int domdec_full_sinkhorn(const double* mu, const double* nu, int N, double eps_s
   return rc;
 }
 
+
+// ---------------------------------------------------------------- batches
+struct domdec_batch_s {
+  std::vector<domdec_t> hs;
+  cudaStream_t st = nullptr;
+  DevState* d_states = nullptr;
+  CellRef* d_refs = nullptr;           // all reference lists, back to back
+  int ref_off[2][5] = {{0}};           // list (part, sub) starts at ref_off; sub 4 = whole partition
+  int ref_cnt[2][5] = {{0}};
+  unsigned int* d_queue = nullptr;
+  int precision = 0, s_max = 0, cap_side_max = 0, cap_ny_max = 0;
+  int maxn = 0, max_nbasic = 0, nsm = 152, max_pairs = 0;
+  int csize = 0;                       // 0 = automatic, 1 or 2 fixed (autotuner)
+  long long sweeps = 0;
+  std::vector<DevState> host_states;
+};
+
+int domdec_batch_create(domdec_batch_t* out, domdec_t* handles, int n) {
+  if (!out || !handles || n < 1) return DOMDEC_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!handles[i]) return DOMDEC_EINVAL;
+    if (handles[i]->sticky) return DOMDEC_ESTATE;
+    if (handles[i]->p.precision != handles[0]->p.precision || handles[i]->p.strategy != handles[0]->p.strategy ||
+        handles[i]->sweeps != handles[0]->sweeps)
+      return DOMDEC_EINVAL;
+  }
+  domdec_batch_s* b = new (std::nothrow) domdec_batch_s();
+  if (!b) return DOMDEC_ENOMEM;
+  b->hs.assign(handles, handles + n);
+  b->st = handles[0]->st;
+  b->precision = handles[0]->p.precision;
+  b->sweeps = handles[0]->sweeps;
+  for (auto h : b->hs) {
+    b->s_max = std::max(b->s_max, h->s);
+    b->cap_side_max = std::max(b->cap_side_max, h->S.cap_side);
+    b->cap_ny_max = std::max(b->cap_ny_max, h->S.cap_ny);
+    b->maxn = std::max(b->maxn, h->N);
+    b->max_nbasic = std::max(b->max_nbasic, h->nbasic);
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
+  b->max_pairs = cell_max_pair_clusters(b->s_max, b->cap_side_max, b->cap_ny_max, b->precision);
+  // reference lists: for each (partition, sub-batch) the cells of every
+  // instance, larger grids first (their boxes are larger: longest jobs first)
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return handles[x]->N > handles[y]->N; });
+  std::vector<CellRef> refs;
+  for (int part = 0; part < 2; ++part)
+    for (int sub = 0; sub < 5; ++sub) {
+      b->ref_off[part][sub] = (int)refs.size();
+      for (int i : order) {
+        domdec_t h = handles[i];
+        const int beg = sub < 4 ? h->sub_start[part][sub] : 0;
+        const int end = sub < 4 ? h->sub_start[part][sub + 1] : h->ncell[part];
+        for (int c = beg; c < end; ++c) refs.push_back({i, c, c - beg, end - beg});
+      }
+      b->ref_cnt[part][sub] = (int)refs.size() - b->ref_off[part][sub];
+    }
+  if (cudaMalloc(&b->d_states, n * sizeof(DevState)) != cudaSuccess ||
+      cudaMalloc(&b->d_refs, std::max<size_t>(1, refs.size()) * sizeof(CellRef)) != cudaSuccess ||
+      cudaMalloc(&b->d_queue, sizeof(unsigned int)) != cudaSuccess) {
+    domdec_batch_free(b);
+    return DOMDEC_ENOMEM;
+  }
+  if (!refs.empty() &&
+      cudaMemcpy(b->d_refs, refs.data(), refs.size() * sizeof(CellRef), cudaMemcpyHostToDevice) != cudaSuccess) {
+    domdec_batch_free(b);
+    return DOMDEC_ECUDA;
+  }
+  *out = b;
+  return DOMDEC_OK;
+}
+
+void domdec_batch_free(domdec_batch_t b) {
+  if (!b) return;
+  if (b->st) cudaStreamSynchronize(b->st);
+  if (b->d_states) cudaFree(b->d_states);
+  if (b->d_refs) cudaFree(b->d_refs);
+  if (b->d_queue) cudaFree(b->d_queue);
+  delete b;
+}
+
+static int batch_upload(domdec_batch_t b) {
+  b->host_states.resize(b->hs.size());
+  for (size_t i = 0; i < b->hs.size(); ++i) {
+    if (b->hs[i]->sticky) return DOMDEC_ESTATE;
+    b->host_states[i] = b->hs[i]->S;
+  }
+  if (cudaMemcpyAsync(b->d_states, b->host_states.data(), b->hs.size() * sizeof(DevState),
+                      cudaMemcpyHostToDevice, b->st) != cudaSuccess)
+    return DOMDEC_ECUDA;
+  return DOMDEC_OK;
+}
+
+static int batch_enqueue_sweep(domdec_batch_t b, int csize_fixed) {
+  const int part = (int)(b->sweeps % 2);
+  const int ninst = (int)b->hs.size();
+  const bool stag = b->hs[0]->p.strategy == DOMDEC_STAGGERED;
+  const int subs[4] = {0, 1, 2, 3};
+  const int nsub = stag ? 4 : 1;
+  for (int k = 0; k < nsub; ++k) {
+    const int sub = stag ? subs[k] : 4;
+    const int nref = b->ref_cnt[part][sub];
+    if (nref == 0) continue;
+    const CellRef* refs = b->d_refs + b->ref_off[part][sub];
+    int csize = csize_fixed ? csize_fixed : (b->max_pairs > 0 && nref >= 2 * b->nsm ? 1 : (b->max_pairs > 0 ? 2 : 1));
+    if (csize == 2 && b->max_pairs == 0) csize = 1;
+    const int nctas = csize == 2 ? 2 * std::min(nref, b->max_pairs) : std::min(nref, b->nsm);
+    if (launch_cell_solve_multi(b->d_states, refs, nref, part, b->d_queue, b->s_max, b->cap_side_max,
+                                b->cap_ny_max, b->precision, csize, nctas, b->st) != cudaSuccess)
+      return DOMDEC_ECUDA;
+    if (launch_decide_multi(b->d_states, ninst, b->maxn, part, stag ? sub : -1, b->st) != cudaSuccess)
+      return DOMDEC_ECUDA;
+    if (launch_apply_multi(b->d_states, refs, nref, part, b->st) != cudaSuccess) return DOMDEC_ECUDA;
+  }
+  if (launch_compact_multi(b->d_states, ninst, b->max_nbasic, b->st) != cudaSuccess) return DOMDEC_ECUDA;
+  for (auto h : b->hs) {
+    h->slot += batches_per_sweep(h, part);
+    ++h->sweeps;
+  }
+  ++b->sweeps;
+  return DOMDEC_OK;
+}
+
+int domdec_batch_iterate(domdec_batch_t b, int n_sweeps) {
+  if (!b || n_sweeps < 0) return DOMDEC_EINVAL;
+  int rc = batch_upload(b);
+  if (rc) return rc;
+  for (int k = 0; k < n_sweeps; ++k) {
+    rc = batch_enqueue_sweep(b, b->csize);
+    if (rc) {
+      for (auto h : b->hs) fail(h, rc);
+      return rc;
+    }
+  }
+  return DOMDEC_OK;
+}
+
+int domdec_batch_sync(domdec_batch_t b) {
+  if (!b) return DOMDEC_EINVAL;
+  int worst = DOMDEC_OK;
+  for (auto h : b->hs) {
+    int rc = domdec_sync(h);
+    if (rc < 0) return rc;
+    if (rc > worst) worst = rc;
+  }
+  return worst;
+}
+
+int domdec_batch_autotune(domdec_batch_t b, int* chosen) {
+  if (!b) return DOMDEC_EINVAL;
+  // one sweep with each cell-group size; keep the higher cell-iteration rate
+  double rate[3] = {0, 0, 0};
+  for (int cs = 1; cs <= 2; ++cs) {
+    if (cs == 2 && b->max_pairs == 0) break;
+    int rc = domdec_batch_sync(b);
+    if (rc < 0) return rc;
+    long long it0 = 0;
+    for (auto h : b->hs) {
+      domdec_stats st;
+      if (domdec_get_stats(h, &st)) return DOMDEC_ECUDA;
+      it0 += st.cell_iters;
+    }
+    rc = batch_upload(b);
+    if (rc) return rc;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, b->st);
+    rc = batch_enqueue_sweep(b, cs);
+    cudaEventRecord(e1, b->st);
+    if (rc) return rc;
+    rc = domdec_batch_sync(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc < 0) return rc;
+    long long it1 = 0;
+    for (auto h : b->hs) {
+      domdec_stats st;
+      if (domdec_get_stats(h, &st)) return DOMDEC_ECUDA;
+      it1 += st.cell_iters;
+    }
+    rate[cs] = ms > 0.f ? (double)(it1 - it0) / ms : 0.0;
+  }
+  b->csize = rate[2] > rate[1] ? 2 : 1;
+  if (chosen) *chosen = b->csize;
+  return DOMDEC_OK;
+}
 }  // extern "C"

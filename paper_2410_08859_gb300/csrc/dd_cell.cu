@@ -205,19 +205,16 @@ __device__ __forceinline__ double box_value(const BoxRec& b, const double* arena
 // pass splits its targets between them and writes each result into both
 // CTAs' shared memory (distributed shared memory); pass boundaries are cluster
 // barriers.
+// Body of the cell solve for cell `cd` at position `cidx` of a sub-batch of
+// `nbatch` cells, run by CTA `crank` of a group of `csize` CTAs.
 template <typename R>
-__global__ void __launch_bounds__(512, 1)
-k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbatch, int csize) {
+__device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDesc cd, int cidx, int nbatch,
+                                                int csize, int crank, unsigned char* smem_raw) {
   namespace cg = cooperative_groups;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   double* red = reinterpret_cast<double*>(smem_raw);  // 32 * 16 doubles (block reductions)
   __shared__ BoxRec sbox[4];
   __shared__ int sgeo[8];
   __shared__ double xchg[16];                         // cross-CTA partial sums
-
-  const int crank = csize > 1 ? (int)cg::this_cluster().block_rank() : 0;
-  const int cidx = blockIdx.x / csize;
-  const CellDesc cd = cells[begin + cidx];
   CellOut* out = S.cout + cidx;
   const double* __restrict__ arena = S.arena[*S.cur];
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -692,6 +689,52 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbat
   }
 }
 
+template <typename R>
+__global__ void __launch_bounds__(512, 1)
+k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbatch, int csize) {
+  namespace cg = cooperative_groups;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int crank = csize > 1 ? (int)cg::this_cluster().block_rank() : 0;
+  const int cidx = blockIdx.x / csize;
+  cell_solve_body<R>(S, cells[begin + cidx], cidx, nbatch, csize, crank, smem_raw);
+}
+
+// Many independent instances: a persistent grid takes (instance, cell) items
+// from a queue (one item per CTA or CTA pair at a time) until it is empty.
+template <typename R>
+__global__ void __launch_bounds__(512, 1)
+k_cell_solve_multi(const DevState* __restrict__ states, const CellRef* __restrict__ refs, int nref, int part,
+                   unsigned int* queue, int csize) {
+  namespace cg = cooperative_groups;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ DevState sS;
+  __shared__ int sj;
+  const int crank = csize > 1 ? (int)cg::this_cluster().block_rank() : 0;
+  auto csync = [&]() {
+    if (csize > 1) cg::this_cluster().sync();
+    else __syncthreads();
+  };
+  for (;;) {
+    if (crank == 0 && threadIdx.x == 0) {
+      int j = (int)atomicAdd(queue, 1u);
+      sj = j;
+      if (csize > 1) *cg::this_cluster().map_shared_rank(&sj, 1) = j;
+    }
+    csync();
+    const int j = sj;
+    if (j >= nref) break;
+    const CellRef rf = refs[j];
+    {
+      const int* src = reinterpret_cast<const int*>(states + rf.inst);
+      int* dst = reinterpret_cast<int*>(&sS);
+      for (int w = threadIdx.x; w < (int)(sizeof(DevState) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
+    }
+    __syncthreads();
+    cell_solve_body<R>(sS, sS.cells[part][rf.cell], rf.pos, rf.nbatch, csize, crank, smem_raw);
+    csync();
+  }
+}
+
 size_t cell_smem_bytes(int s, int cap_side, int cap_ny, int precision) {
   size_t rs = precision ? sizeof(double) : sizeof(float);
   size_t cap_nx = 4 * (size_t)s * s, tsz = 2 * (size_t)s * cap_side;
@@ -750,4 +793,29 @@ cudaError_t launch_cell_solve(const DevState& S, const CellDesc* cells, int begi
   }
   cudaFuncSetAttribute(k_cell_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   return cudaLaunchKernelEx(&cfg, k_cell_solve<float>, S, cells, begin, nbatch, csize);
+}
+
+cudaError_t launch_cell_solve_multi(const DevState* states, const CellRef* refs, int nref, int part,
+                                    unsigned int* queue, int s, int cap_side, int cap_ny, int precision, int csize,
+                                    int nctas, cudaStream_t st) {
+  size_t smem = cell_smem_bytes(s, cap_side, cap_ny, precision);
+  cudaMemsetAsync(queue, 0, sizeof(unsigned int), st);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nctas);
+  cfg.blockDim = dim3(512);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (precision) {
+    cudaFuncSetAttribute(k_cell_solve_multi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaLaunchKernelEx(&cfg, k_cell_solve_multi<double>, states, refs, nref, part, queue, csize);
+  }
+  cudaFuncSetAttribute(k_cell_solve_multi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return cudaLaunchKernelEx(&cfg, k_cell_solve_multi<float>, states, refs, nref, part, queue, csize);
 }

@@ -67,6 +67,20 @@ struct DevState {
   int* status;
   double* red;                  // reduction scratch
   unsigned int* red_count;
+  // partitions (for kernels that locate their own sub-batch)
+  const CellDesc* cells[2];     // cells of partitions A and B, sorted by sub-batch
+  int sub_start[2][5];          // sub-batch b of partition p: cells [sub_start[p][b], sub_start[p][b+1])
+  int staggered;                // 1: four sub-batches per sweep, 0: one batch of all cells
+  unsigned long long* slotctr;  // decision-log records written so far
+  long long* newoff;            // compaction scratch: nbasic + 1 offsets
+};
+
+#define DD_LOGCAP 4096          // decision-log records kept per instance
+
+// One cell of a many-instance launch: instance, cell index in its partition
+// list, and its position within the instance's sub-batch.
+struct CellRef {
+  int inst, cell, pos, nbatch;
 };
 
 // ------------------------------------------------------------------ math

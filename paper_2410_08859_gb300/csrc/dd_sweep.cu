@@ -6,42 +6,52 @@
 #include "dd_common.cuh"
 
 // ============================================================== decision (a6)
+// mu phi(p/mu) in float (the current score's marginal terms; see k_decide).
+__device__ __forceinline__ float kl_term_f(double p, double m) {
+  if (p <= 0.0) return (float)m;
+  float pf = (float)p, mf = (float)m;
+  return pf * (dd_lg2(pf / mf) * (float)DD_LN2) - pf + mf;
+}
+
 // Tracked score (the sum of per-basic-cell transport cost and entropy plus the
 // two exact marginal penalties) and its value after mixing with theta = 1 and
 // theta = 1/|b|; decision on the device, deterministic fixed-order reductions.
-__global__ void __launch_bounds__(512)
-k_decide(DevState S, const CellDesc* __restrict__ cells, int begin, int nbatch, int slot) {
+__device__ __forceinline__ void decide_body(const DevState& S, const CellDesc* __restrict__ cells, int begin,
+                                            int nbatch, int bid, int nblk) {
   __shared__ double red[33 * 5];
   __shared__ bool is_last;
   const int n = S.N * S.N;
   const double lam = S.lam, eps = S.eps, th_s = 1.0 / nbatch;
   double v[5] = {0, 0, 0, 0, 0};
-  for (int y = blockIdx.x * blockDim.x + threadIdx.x; y < n; y += gridDim.x * blockDim.x) {
-    v[0] += dd_kl_term(S.PX[y], S.mu[y]);
+  // The current score's marginal terms enter only the tie slack and the
+  // leniency test (they cancel in E(1) - E(1/|b|)), so they are summed with
+  // float logarithms; the theta-dependent changes use double throughout.
+  for (int y = bid * blockDim.x + threadIdx.x; y < n; y += nblk * blockDim.x) {
+    v[0] += (double)kl_term_f(S.PX[y], S.mu[y]);
     double p = S.PY[y], m = S.nu[y];
-    double k0 = dd_kl_term(p, m);
-    v[1] += k0;
+    v[1] += (double)kl_term_f(p, m);
     double d = S.dPY[y];
     if (d != 0.0) {
+      double k0 = dd_kl_term(p, m);
       v[2] += dd_kl_term(fmax(0.0, p + d), m) - k0;
       v[3] += dd_kl_term(fmax(0.0, p + th_s * d), m) - k0;
     }
   }
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.nbasic; i += gridDim.x * blockDim.x)
+  for (int i = bid * blockDim.x + threadIdx.x; i < S.nbasic; i += nblk * blockDim.x)
     v[4] += S.Cc[i] + eps * S.Hh[i];
   block_sum<5>(v, red);
   if (threadIdx.x == 0) {
-    for (int k = 0; k < 5; ++k) S.red[blockIdx.x * 5 + k] = v[k];
+    for (int k = 0; k < 5; ++k) S.red[bid * 5 + k] = v[k];
     __threadfence();
     unsigned int t = atomicAdd(S.red_count, 1u);
-    is_last = (t == gridDim.x - 1);
+    is_last = (t == (unsigned int)nblk - 1);
   }
   __syncthreads();
   if (!is_last) return;
   __threadfence();
   // last block: fixed-order reduction of the block partials and the per-cell terms
   double tot[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x)
     for (int k = 0; k < 5; ++k) tot[k] += ((volatile double*)S.red)[b * 5 + k];
   for (int j = threadIdx.x; j < nbatch; j += blockDim.x) {
     const CellOut& o = S.cout[j];
@@ -60,13 +70,15 @@ k_decide(DevState S, const CellDesc* __restrict__ cells, int begin, int nbatch, 
   if (threadIdx.x != 0) return;
   const double dL = tot[5], dKX1 = tot[6], dKXs = tot[7];
   const double E0 = tot[4] + lam * tot[0] + lam * tot[1];
-  const double Eg = E0 + dL + lam * dKX1 + lam * tot[2];
-  const double Es = E0 + th_s * dL + lam * dKXs + lam * tot[3];
+  const double dg = dL + lam * dKX1 + lam * tot[2];          // E(1) - E
+  const double ds = th_s * dL + lam * dKXs + lam * tot[3];   // E(1/|b|) - E
+  const double Eg = E0 + dg, Es = E0 + ds;
   double theta;
   if (S.strategy == 3) theta = 1.0;                 // greedy
   else if (S.strategy == 2) theta = th_s;           // safe
-  else theta = (Eg <= Es + 1e-12 * fabs(E0) || (S.tau > 0.0 && Eg <= (1.0 + S.tau) * E0)) ? 1.0 : th_s;
+  else theta = (dg <= ds + 1e-12 * fabs(E0) || (S.tau > 0.0 && dg <= S.tau * E0)) ? 1.0 : th_s;
   *S.theta = theta;
+  const unsigned long long slot = (*S.slotctr)++ % DD_LOGCAP;
   double* lg = S.declog + 4 * slot;
   lg[0] = E0; lg[1] = Eg; lg[2] = Es; lg[3] = theta;
   atomicAdd(S.counters + (theta == 1.0 ? 3 : 4), 1ull);
@@ -74,21 +86,45 @@ k_decide(DevState S, const CellDesc* __restrict__ cells, int begin, int nbatch, 
   if (S.spill_count) *S.spill_count = 0u;
 }
 
+__global__ void __launch_bounds__(512)
+k_decide(DevState S, const CellDesc* __restrict__ cells, int begin, int nbatch) {
+  decide_body(S, cells, begin, nbatch, blockIdx.x, gridDim.x);
+}
+
+// Many instances: blockIdx.y selects the instance; sub < 0 means the whole
+// partition (non-staggered strategies).
+__global__ void __launch_bounds__(512)
+k_decide_multi(const DevState* __restrict__ states, int part, int sub) {
+  __shared__ DevState sS;
+  {
+    const int* src = reinterpret_cast<const int*>(states + blockIdx.y);
+    int* dst = reinterpret_cast<int*>(&sS);
+    for (int w = threadIdx.x; w < (int)(sizeof(DevState) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
+  }
+  __syncthreads();
+  const int begin = sub < 0 ? 0 : sS.sub_start[part][sub];
+  const int end = sub < 0 ? sS.sub_start[part][4] : sS.sub_start[part][sub + 1];
+  if (end <= begin) return;
+  const int n = sS.N * sS.N;
+  int nblk = (n + 511) / 512;
+  if (nblk > (int)gridDim.x) nblk = gridDim.x;
+  if ((int)blockIdx.x >= nblk) return;
+  decide_body(sS, sS.cells[part], begin, end - begin, blockIdx.x, nblk);
+}
+
 // ================================================================= apply (a7)
-__global__ void __launch_bounds__(256)
-k_apply(DevState S, const CellDesc* __restrict__ cells, int begin) {
+__device__ __forceinline__ void apply_body(const DevState& S, const CellDesc cd, int pos) {
   __shared__ BoxRec ob[4];
   __shared__ int bb[4][4];       // per quadrant: min kk, max kk, min ll, max ll of kept entries
   __shared__ long long noff[4];
   __shared__ int nbox[4][4];
-  const CellOut o = S.cout[blockIdx.x];
+  const CellOut o = S.cout[pos];
   if (o.status == CELL_EMPTY || o.status == CELL_TOOBIG) return;
-  const CellDesc cd = cells[begin + blockIdx.x];
   const double th = *S.theta, thr = S.thr;
   const int N = S.N, H = o.H, W = o.W, ny = H * W;
   double* arena = S.arena[*S.cur];
   int nst;
-  const double* nut = cell_nut(S, o, blockIdx.x, &nst);
+  const double* nut = cell_nut(S, o, pos, &nst);
   const int tid = threadIdx.x;
   if (tid < 4) {
     BoxRec b = {0, 0, 0, 0, 0};
@@ -177,9 +213,27 @@ k_apply(DevState S, const CellDesc* __restrict__ cells, int begin) {
   }
 }
 
+__global__ void __launch_bounds__(1024)
+k_apply(DevState S, const CellDesc* __restrict__ cells, int begin) {
+  apply_body(S, cells[begin + blockIdx.x], blockIdx.x);
+}
+
+__global__ void __launch_bounds__(1024)
+k_apply_multi(const DevState* __restrict__ states, const CellRef* __restrict__ refs, int part) {
+  __shared__ DevState sS;
+  const CellRef rf = refs[blockIdx.x];
+  {
+    const int* src = reinterpret_cast<const int*>(states + rf.inst);
+    int* dst = reinterpret_cast<int*>(&sS);
+    for (int w = threadIdx.x; w < (int)(sizeof(DevState) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
+  }
+  __syncthreads();
+  apply_body(sS, sS.cells[part][rf.cell], rf.pos);
+}
+
 // ============================================================ arena compaction
 // Exclusive scan of the box sizes (one block), new offsets into `newoff`.
-__global__ void __launch_bounds__(1024) k_scan_boxes(DevState S, long long* newoff) {
+__device__ __forceinline__ void scan_boxes_body(const DevState& S, long long* newoff) {
   __shared__ long long part[1024];
   const int nb = S.nbasic, tid = threadIdx.x, per = (nb + blockDim.x - 1) / blockDim.x;
   const int b0 = min(nb, tid * per), b1 = min(nb, b0 + per);
@@ -197,8 +251,9 @@ __global__ void __launch_bounds__(1024) k_scan_boxes(DevState S, long long* newo
   for (int i = b0; i < b1; ++i) { newoff[i] = run; run += (long long)S.box[i].H * S.box[i].W; }
 }
 
-__global__ void __launch_bounds__(256) k_copy_boxes(DevState S, const long long* newoff) {
-  const int i = blockIdx.x;
+__global__ void __launch_bounds__(1024) k_scan_boxes(DevState S, long long* newoff) { scan_boxes_body(S, newoff); }
+
+__device__ __forceinline__ void copy_box_body(const DevState& S, const long long* newoff, int i) {
   const int cur = *S.cur;
   const double* src = S.arena[cur];
   double* dst = S.arena[1 - cur];
@@ -209,9 +264,34 @@ __global__ void __launch_bounds__(256) k_copy_boxes(DevState S, const long long*
   if (threadIdx.x == 0) S.box[i].off = no;
 }
 
+__global__ void __launch_bounds__(256) k_copy_boxes(DevState S, const long long* newoff) {
+  copy_box_body(S, newoff, blockIdx.x);
+}
+
 __global__ void k_flip_arena(DevState S, const long long* newoff) {
   *S.cur = 1 - *S.cur;
   *S.head = (unsigned long long)newoff[S.nbasic];
+}
+
+__global__ void __launch_bounds__(1024) k_scan_boxes_multi(const DevState* __restrict__ states) {
+  const DevState& S = states[blockIdx.x];
+  scan_boxes_body(S, S.newoff);
+}
+
+__global__ void __launch_bounds__(256) k_copy_boxes_multi(const DevState* __restrict__ states) {
+  const DevState& S = states[blockIdx.y];
+  for (int i = blockIdx.x; i < S.nbasic; i += gridDim.x) {
+    copy_box_body(S, S.newoff, i);
+    __syncthreads();
+  }
+}
+
+__global__ void k_flip_arena_multi(const DevState* __restrict__ states, int n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const DevState& S = states[k];
+  *S.cur = 1 - *S.cur;
+  *S.head = (unsigned long long)S.newoff[S.nbasic];
 }
 
 // ============================================================ inputs and init
@@ -444,17 +524,33 @@ k_cert(DevState S, const double* z, double* beta_out, double* out) {
 }
 
 // ======================================================= host launch wrappers
-cudaError_t launch_decide(const DevState& S, const CellDesc* cells, int begin, int nbatch, int slot,
-                          cudaStream_t st) {
+cudaError_t launch_decide(const DevState& S, const CellDesc* cells, int begin, int nbatch, cudaStream_t st) {
   int nblk = 2 * 152;
   int n = S.N * S.N;
   if (n < nblk * 512) nblk = (n + 511) / 512;
   if (nblk < 1) nblk = 1;
-  k_decide<<<nblk, 512, 0, st>>>(S, cells, begin, nbatch, slot);
+  k_decide<<<nblk, 512, 0, st>>>(S, cells, begin, nbatch);
+  return cudaGetLastError();
+}
+cudaError_t launch_decide_multi(const DevState* states, int ninst, int maxn, int part, int sub, cudaStream_t st) {
+  int nblk = (maxn * maxn + 511) / 512;
+  if (nblk > 2 * 152) nblk = 2 * 152;
+  if (nblk < 1) nblk = 1;
+  k_decide_multi<<<dim3(nblk, ninst), 512, 0, st>>>(states, part, sub);
+  return cudaGetLastError();
+}
+cudaError_t launch_apply_multi(const DevState* states, const CellRef* refs, int nref, int part, cudaStream_t st) {
+  if (nref > 0) k_apply_multi<<<nref, 1024, 0, st>>>(states, refs, part);
+  return cudaGetLastError();
+}
+cudaError_t launch_compact_multi(const DevState* states, int ninst, int max_nbasic, cudaStream_t st) {
+  k_scan_boxes_multi<<<ninst, 1024, 0, st>>>(states);
+  k_copy_boxes_multi<<<dim3(max_nbasic < 4096 ? max_nbasic : 4096, ninst), 256, 0, st>>>(states);
+  k_flip_arena_multi<<<(ninst + 127) / 128, 128, 0, st>>>(states, ninst);
   return cudaGetLastError();
 }
 cudaError_t launch_apply(const DevState& S, const CellDesc* cells, int begin, int nbatch, cudaStream_t st) {
-  k_apply<<<nbatch, 256, 0, st>>>(S, cells, begin);
+  k_apply<<<nbatch, 1024, 0, st>>>(S, cells, begin);
   return cudaGetLastError();
 }
 cudaError_t launch_compact(const DevState& S, long long* newoff, cudaStream_t st) {

@@ -78,6 +78,11 @@ _SIGS = {
     "domdec_error_string": (ctypes.c_char_p, [_I]),
     "domdec_full_sinkhorn": (_I, [_P, _P, _I, _D, _D, _D, _I, _I, _I, _D, _I, _P, _P, _P, _DP, _P]),
     "domdec_full_sinkhorn_noalloc": (_I, [_P, _P, _I, _D, _D, _D, _I, _I, _I, _D, _I, _P, _P, _P, _DP, _P]),
+    "domdec_batch_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(_P), _I]),
+    "domdec_batch_iterate": (_I, [_P, _I]),
+    "domdec_batch_sync": (_I, [_P]),
+    "domdec_batch_autotune": (_I, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "domdec_batch_free": (None, [_P]),
 }
 
 
@@ -272,6 +277,41 @@ def domdec_full_sinkhorn_noalloc(mu, nu, N, eps, lam, alpha, beta, eps_start=Non
                                             _ptr(beta, n, True), out, _stream_ptr(stream))
     _check(rc, "domdec_full_sinkhorn_noalloc")
     return int(out[0]), out[1], out[2], out[3], rc
+
+
+class DomDecBatch:
+    """Many independent DomDec problems swept together (the handles stay
+    owned by their DomDec objects, which must outlive the batch)."""
+
+    def __init__(self, problems):
+        self.problems = list(problems)
+        arr = (_P * len(self.problems))(*[p.h for p in self.problems])
+        b = _P()
+        _check(lib().domdec_batch_create(ctypes.byref(b), arr, len(self.problems)), "domdec_batch_create")
+        self.b = b
+
+    def iterate(self, n=1):
+        _check(lib().domdec_batch_iterate(self.b, int(n)), "domdec_batch_iterate")
+        return self
+
+    def sync(self):
+        return _check(lib().domdec_batch_sync(self.b), "domdec_batch_sync")
+
+    def autotune(self):
+        c = ctypes.c_int(0)
+        _check(lib().domdec_batch_autotune(self.b, ctypes.byref(c)), "domdec_batch_autotune")
+        return c.value
+
+    def close(self):
+        if self.b:
+            lib().domdec_batch_free(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class DomDec:

@@ -247,6 +247,39 @@ def test_fp64_spilled_boxes_match_oracle(dd):
     g.close()
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", 2e-6)])
+def test_batch_of_instances_matches_single_runs(dd, precision, tol):
+    """Many-instance batching: three different problems (grid, cell size, eps,
+    lam) swept together give the states of the same problems swept alone."""
+    specs = [(32, 4, (1 / 32) ** 2, 1.0, 1000), (16, 2, (2 / 16) ** 2, 0.5, 1001), (24, 3, (1 / 24) ** 2, 5.0, 1002)]
+    alone, batched = [], []
+    for N, s, eps, lam, seed in specs:
+        mu, nu = inputs.mixture_small(N=N, seed=seed)
+        for lst in (alone, batched):
+            lst.append(dd.DomDec(mu, nu, eps, lam, s, precision=precision))
+    for g in alone:
+        g.iterate(3)
+        g.sync()
+    B = dd.DomDecBatch(batched)
+    B.iterate(3)
+    assert B.sync() in (0, 1)
+    for g1, g2 in zip(alone, batched):
+        s1, s2 = g1.score(), g2.score()
+        assert abs(s1[0] - s2[0]) <= tol * abs(s1[0])
+        np.testing.assert_array_equal(g1.decisions()[:, 3], g2.decisions()[:, 3])
+        PX1, PY1 = g1.marginals()
+        PX2, PY2 = g2.marginals()
+        assert np.abs(PX1 - PX2).sum() <= tol * PX1.sum()
+        assert np.abs(PY1 - PY2).sum() <= tol * PY1.sum()
+        assert g1.stats()["cell_iters"] == g2.stats()["cell_iters"] or precision == "fp32"
+    assert B.autotune() in (1, 2)
+    B.iterate(1)
+    B.sync()
+    B.close()
+    for g in alone + batched:
+        g.close()
+
+
 def test_maxit_warning(dd):
     mu, nu = inputs.mixture_small(N=16, seed=1010)
     g = dd.DomDec(mu, nu, (1 / 16) ** 2, 1.0, 2, precision="fp32", err=1e-12, maxit=2)
