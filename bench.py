@@ -192,6 +192,75 @@ def oracle_sample(max_seconds=20.0, sweeps=None, maxit=None):
     return its / el, desc, its, el
 
 
+def run_batch(args, dd, torch):
+    """Many-instance batching: 64 independent problems (sides from {64, 128,
+    256, 512}, eps = (2/n)^2, lam in {0.5, 1, 5}) swept together, each warm-
+    started by global Sinkhorn down to 2 eps; against the same problems swept
+    one after another with single handles."""
+    from paper_2410_08859_gb300 import inputs
+    probs = inputs.batch_instances(64)
+    t0 = time.perf_counter()
+    handles_b, handles_s = [], []
+    for p in probs:
+        N = p["N"]
+        mu_d = torch.from_numpy(p["mu"].ravel().copy()).cuda()
+        nu_d = torch.from_numpy(p["nu"].ravel().copy()).cuda()
+        a = torch.empty(N * N, dtype=torch.float64, device="cuda")
+        b = torch.empty_like(a)
+        dd.domdec_full_sinkhorn(mu_d, nu_d, N, 2 * p["eps"], p["lam"], eps_start=1.0,
+                                variant=dd.SINKHORN_SEPARABLE, precision=dd.MIXED, maxit=1000, err=2e-5,
+                                check_every=20, alpha=a, beta=b)
+        for lst in (handles_b, handles_s):
+            lst.append(dd.DomDec(mu_d, nu_d, p["eps"], p["lam"], 8, alpha0=a, beta0=b, eps_init=2 * p["eps"],
+                                 precision="fp32", tau=0.0, err=2e-5))
+    torch.cuda.synchronize()
+    t_warm = time.perf_counter() - t0
+    B = dd.DomDecBatch(handles_b)
+    chosen = B.autotune()
+    B.iterate(args.warmup)
+    B.sync()
+    it0 = sum(h.stats()["cell_iters"] for h in handles_b)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    B.iterate(args.steps)
+    e1.record()
+    torch.cuda.synchronize()
+    B.sync()
+    t_b = e0.elapsed_time(e1)
+    it_b = sum(h.stats()["cell_iters"] for h in handles_b) - it0
+    # the same problems, one handle after another
+    for h in handles_s:
+        h.iterate(2 + args.warmup)
+        h.sync()
+    it0 = sum(h.stats()["cell_iters"] for h in handles_s)
+    torch.cuda.synchronize()
+    e0.record()
+    for h in handles_s:
+        h.iterate(args.steps)
+    e1.record()
+    torch.cuda.synchronize()
+    for h in handles_s:
+        h.sync()
+    t_s = e0.elapsed_time(e1)
+    it_s = sum(h.stats()["cell_iters"] for h in handles_s) - it0
+    B.close()
+    for h in handles_b + handles_s:
+        h.close()
+    sides = sorted(set(p["N"] for p in probs))
+    line = {"metric": METRIC, "value": it_b / (t_b / 1000.0), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_b / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch64", "instances": len(probs), "sides": sides, "basic_cell": 8,
+                       "eps": "(2/n)^2", "lam": "{0.5, 1, 5}", "cell_ctas_autotuned": chosen,
+                       "l2": "state of 64 instances exceeds L2 (no flush)"},
+            "sequential_single_handles": {"value": it_s / (t_s / 1000.0), "unit": UNIT,
+                                          "ms_per_step": t_s / args.steps},
+            "batch_speedup": (it_b / t_b) / max(it_s / t_s, 1e-30),
+            "warm_start_s": t_warm}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -224,6 +293,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--lam", type=float, default=1.0)
+    ap.add_argument("--workload", default="blobs256", choices=["blobs256", "batch64"])
     ap.add_argument("--no-extras", action="store_true", help="skip time-to-gap, e2e and CPU baseline")
     ap.add_argument("--quick-warm", action="store_true",
                     help="float-only, capped warm start (profiling runs; not a bench number)")
@@ -246,6 +316,14 @@ def main():
         dist.barrier()
     from paper_2410_08859_gb300 import domdec as dd
     dd.lib()
+
+    if args.workload == "batch64":
+        if rank == 0:
+            run_batch(args, dd, torch)
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
 
     mu, nu, spec = workload_inputs(rank)
     N, s, eps, lam = spec["N"], spec["s"], spec["eps"], args.lam

@@ -101,6 +101,20 @@ WORKLOADS = {
 }
 
 
+def batch_instances(n_inst: int = 64, seed: int = 4000, sides=(64, 128, 256, 512)):
+    """Many independent problems: side n ~ U(sides), eps = (2/n)^2,
+    lam ~ U{0.5, 1, 5}, blob mixtures of unequal mass (mass ratio in
+    [0.7, 1.5]).  Returns a list of dicts (mu, nu, N, eps, lam)."""
+    rng = _rng(seed)
+    out = []
+    for k in range(n_inst):
+        N = int(rng.choice(sides))
+        lam = float(rng.choice([0.5, 1.0, 5.0]))
+        mu, nu = mixture_blobs(N=N, seed=seed + 1 + k)
+        out.append(dict(mu=mu, nu=nu, N=N, eps=(2.0 / N) ** 2, lam=lam))
+    return out
+
+
 def workload(name: str, instance: int = 0, N: int | None = None):
     """Return (mu, nu, params) for a named workload; ``N`` overrides the size
     (used for small parity cases of the same distribution)."""
