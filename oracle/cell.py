@@ -12,6 +12,22 @@ generalised Sinkhorn iteration of Section 5.1:
           rho = d nu_{-J} / d nu.
   stop    (Eq. PD-gap-KL): PD/lam = KL(P_X pi | exp(-alpha/lam) mu_J)
           <= err * |mu_J|, evaluated after each Y-half.
+
+Optional translation step (``ti=True``; not in the paper).  With lam KL
+penalties and eps << lam, plain alternation contracts the total-mass mode of
+the cell problem only by about 1 - eps/lam per iteration.  The cell dual
+  F(alpha, beta) = -lam <e^{-alpha/lam} - 1, mu_J> - lam <e^{-beta/lam} - 1, nu>
+                   - <nu_{-J}, beta> - eps <e^{(alpha + beta - c)/eps} - 1, mu_J x nu>
+(the Y term is the conjugate of lam KL(. + nu_{-J} | nu) on the branch where
+the cell's own Y-marginal is positive, which holds after every Y-half) keeps
+its entropic term under alpha + t, beta - t.  Along that line
+  G(t) = -lam A e^{-t/lam} - lam B e^{t/lam} + t a + const,
+  A = <e^{-alpha/lam}, mu_J>, B = <e^{-beta/lam}, nu>, a = |nu_{-J}| on B_J,
+is maximised at e^{t/lam} = (a + sqrt(a^2 + 4 A B)) / (2 B) (the quadratic
+B u^2 - a u - A = 0).  After each X-half, alpha += t* (the translation-
+invariant Sinkhorn idea of Sejourne, Vialard and Peyre, 2022, written here for
+the cell problem).  The fixed points are those of plain alternation (at the
+optimum G'(0) = 0, so t* = 0), and F does not decrease.
 """
 from __future__ import annotations
 
@@ -72,14 +88,25 @@ class CellResult:
         self.iters, self.converged, self.gap = iters, converged, gap
 
 
-def cell_sinkhorn(mu_J, nu_B, rho, C, eps, lam, alpha0, err=2e-5, maxit=2000):
+def ti_shift(alpha, beta, mu_J, nu_B, rho, lam):
+    """t* of the translation step (module docstring): maximiser of the cell
+    dual along (alpha + t, beta - t)."""
+    A = float(np.sum(mu_J * np.exp(-alpha / lam)))
+    B = float(np.sum(nu_B * np.exp(-beta / lam)))
+    a = float(np.sum(np.asarray(rho) * nu_B))
+    u = (a + np.sqrt(a * a + 4.0 * A * B)) / (2.0 * B)
+    return lam * np.log(u)
+
+
+def cell_sinkhorn(mu_J, nu_B, rho, C, eps, lam, alpha0, err=2e-5, maxit=2000, ti=False):
     """Cell Sinkhorn on X_J x B_J (Section 5.1, 'Solving cell subproblems').
 
     mu_J (n_x), nu_B (n_y) positive; rho = nu_{-J}/nu on B_J (n_y, >= 0);
     C (n_x, n_y) the cost; alpha0 the warm start on X_J.  Each iteration is a
     Y-half from the current alpha, the X-marginal of the resulting plan, the
     stopping test (Eq. PD-gap-KL with per-cell tolerance err*|mu_J|) and, if
-    not stopped, the X-half.  The solve therefore ends after a Y-half."""
+    not stopped, the X-half (followed by the translation step if ``ti``).
+    The solve therefore ends after a Y-half."""
     mu_J = np.asarray(mu_J, np.float64)
     nu_B = np.asarray(nu_B, np.float64)
     logmu = np.log(mu_J)
@@ -101,3 +128,5 @@ def cell_sinkhorn(mu_J, nu_B, rho, C, eps, lam, alpha0, err=2e-5, maxit=2000):
         if it >= maxit:
             return CellResult(alpha, beta, px, it, False, gap)
         alpha = -kap * w
+        if ti and not np.isinf(lam):
+            alpha = alpha + ti_shift(alpha, beta, mu_J, nu_B, rho, lam)

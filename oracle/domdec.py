@@ -272,7 +272,7 @@ def cell_problem(st, cell, margin=0):
     return dict(lo=lo, hi=hi, Y=Y, rho=rho)
 
 
-def solve_cell(st, cell, prob, err=2e-5, maxit=2000):
+def solve_cell(st, cell, prob, err=2e-5, maxit=2000, ti=False):
     """Solve the cell subproblem and return the new cell plan's data: final
     duals, P_X of the new plan on X_J, and per member basic cell its new
     Y-marginal on B_J, C_i and H_i (H_i via log(pi/(mu nu)) =
@@ -281,7 +281,7 @@ def solve_cell(st, cell, prob, err=2e-5, maxit=2000):
     X, Y = cell["X"], prob["Y"]
     C = uot.sq_cost(g.pix[X], g.pix[Y], g.h)
     res = cell_sinkhorn(st.mu[X], st.nu[Y], prob["rho"], C, st.eps, st.lam,
-                        st.alpha[X], err, maxit)
+                        st.alpha[X], err, maxit, ti)
     pi = uot.plan(res.alpha, res.beta, C, st.mu[X], st.nu[Y], st.eps)
     logratio = (res.alpha[:, None] + res.beta[None, :] - C) / st.eps
     shape = tuple(prob["hi"] - prob["lo"])
@@ -365,14 +365,14 @@ def batches_of(st, which, strategy):
     return [cells]
 
 
-def sweep(st, which, strategy="staggered", tau=0.0, err=2e-5, maxit=2000, margin=0):
+def sweep(st, which, strategy="staggered", tau=0.0, err=2e-5, maxit=2000, margin=0, ti=False):
     """One parallel DomDec iteration over partition ``which`` (Algorithm 4;
     for ``staggered`` once per sub-batch, in sub-batch order).  Returns one
     log record per batch."""
     log = []
     for batch in batches_of(st, which, strategy):
         probs = [cell_problem(st, c, margin) for c in batch]
-        sols = [None if p is None else solve_cell(st, c, p, err, maxit)
+        sols = [None if p is None else solve_cell(st, c, p, err, maxit, ti)
                 for c, p in zip(batch, probs)]
         theta, E0, Eg, Es = get_weights(st, batch, probs, sols, strategy, tau)
         apply_step(st, batch, probs, sols, theta)
@@ -382,7 +382,7 @@ def sweep(st, which, strategy="staggered", tau=0.0, err=2e-5, maxit=2000, margin
     return log
 
 
-def sequential_sweep(st, which, err=2e-5, maxit=2000, margin=0):
+def sequential_sweep(st, which, err=2e-5, maxit=2000, margin=0, ti=False):
     """Sequential DomDec iteration (Algorithm 3): cells in partition order,
     each solved from the current state and accepted with theta = 1."""
     iters = []
@@ -390,23 +390,23 @@ def sequential_sweep(st, which, err=2e-5, maxit=2000, margin=0):
         prob = cell_problem(st, cell, margin)
         if prob is None:
             continue
-        sol = solve_cell(st, cell, prob, err, maxit)
+        sol = solve_cell(st, cell, prob, err, maxit, ti)
         apply_step(st, [cell], [prob], [sol], 1.0)
         iters.append(sol["iters"])
     return iters
 
 
 def run(st, n_sweeps, strategy="staggered", tau=0.0, err=2e-5, maxit=2000,
-        margin=0, first=0, record=None):
+        margin=0, first=0, record=None, ti=False):
     """Alternate A and B sweeps (Algorithm 2): sweep k uses A for even
     first+k, B otherwise.  ``record(k, st, log)`` is called after each sweep."""
     logs = []
     for k in range(n_sweeps):
         which = "A" if (first + k) % 2 == 0 else "B"
         if strategy == "sequential":
-            lg = sequential_sweep(st, which, err, maxit, margin)
+            lg = sequential_sweep(st, which, err, maxit, margin, ti)
         else:
-            lg = sweep(st, which, strategy, tau, err, maxit, margin)
+            lg = sweep(st, which, strategy, tau, err, maxit, margin, ti)
         logs.append(lg)
         if record is not None:
             record(k, st, lg)

@@ -126,7 +126,7 @@ def pd_gap_over_lam(alpha, px, mu, lam):
 
 
 def full_sinkhorn(mu, nu, C, eps, lam, err=2e-5, maxit=10000, beta0=None,
-                  min_iters=1):
+                  min_iters=1, ti=False):
     """Generalised Sinkhorn for the global problem (nu_- = 0), Eq.
     sinkhorn-iters-ot, starting from beta0 (default 0, Definition 2.3).
 
@@ -134,6 +134,9 @@ def full_sinkhorn(mu, nu, C, eps, lam, err=2e-5, maxit=10000, beta0=None,
     quantity PD/lam = KL(P_X pi | e^{-alpha/lam} mu) is evaluated (Eq. PD-gap-KL,
     with nu_- = 0 and a single cell); the loop stops once it is
     <= err * |mu| (Section 5.3, 'Stopping criterion') or after maxit iterations.
+    ``ti``: after each X-half, alpha += (lam/2) log(<e^{-alpha/lam}, mu> /
+    <e^{-beta/lam}, nu>), the maximiser of the dual along (alpha + t, beta - t)
+    (the cell problem's translation step with nu_{-J} = 0; not in the paper).
     Returns (alpha, beta, iterations, last PD/lam)."""
     mu = np.asarray(mu, np.float64)
     nu = np.asarray(nu, np.float64)
@@ -143,6 +146,9 @@ def full_sinkhorn(mu, nu, C, eps, lam, err=2e-5, maxit=10000, beta0=None,
     it = 0
     while it < maxit:
         alpha = x_half(beta, C, nu, eps, lam)
+        if ti and not np.isinf(lam):
+            alpha = alpha + 0.5 * lam * np.log(np.sum(mu * np.exp(-alpha / lam))
+                                               / np.sum(nu * np.exp(-beta / lam)))
         beta = y_half(alpha, C, mu, eps, lam)
         it += 1
         px = x_marginal(alpha, beta, C, mu, nu, eps)
