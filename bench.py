@@ -261,6 +261,71 @@ def run_batch(args, dd, torch):
     print(json.dumps(line), flush=True)
 
 
+def run_grad(args, dd, torch):
+    """Differentiation workload: 512 x 512, eps = (2/512)^2, lam = 1, blob
+    mixtures of masses 1.0 / 1.1; DomDec (FP32 cells) to a relative PD gap of
+    1e-6, then the backward pass (beta_star by one global Y-half, adjoint
+    kernels for d/dmu, d/dnu, d/dx) timed per call, FP32 and FP64 summation."""
+    from paper_2410_08859_gb300 import autograd as ag
+    from paper_2410_08859_gb300 import inputs
+    N, s = 512, 8
+    mu, nu = inputs.mixture_blobs(N=N, seed=5000, mass_ratio=1.1)
+    eps, lam = (2.0 / N) ** 2, 1.0
+    mu_d = torch.from_numpy(mu.ravel().copy()).cuda()
+    nu_d = torch.from_numpy(nu.ravel().copy()).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g, info = ag.solve(mu_d, nu_d, eps, lam, s=s, gap=1e-6, precision="fp32")
+    torch.cuda.synchronize()
+    t_solve = time.perf_counter() - t0
+    n = N * N
+    bufs = {p: (torch.empty(n, dtype=torch.float64, device="cuda"), torch.empty(n, dtype=torch.float64, device="cuda"),
+                torch.empty(2 * n, dtype=torch.float64, device="cuda")) for p in (dd.FP32, dd.FP64)}
+    times = {}
+    for p in (dd.FP32, dd.FP64):
+        for _ in range(args.warmup):
+            g.gradients(p, *bufs[p])
+        ts = []
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            g.gradients(p, *bufs[p])
+            ts.append(time.perf_counter() - t1)
+        times[p] = 1000 * float(np.median(ts))
+    # the adjoint alone (potentials given), CUDA events on the current stream
+    a = torch.empty(n, dtype=torch.float64, device="cuda")
+    b = torch.empty_like(a)
+    dd.domdec_duals(g.h, a)
+    g.gradients(dd.FP64, beta=b)
+    adj = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for p in (dd.FP32, dd.FP64):
+        for _ in range(args.warmup):
+            dd.domdec_uot_gradients(mu_d, nu_d, a, b, N, eps, lam, p, *bufs[p])
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            dd.domdec_uot_gradients(mu_d, nu_d, a, b, N, eps, lam, p, *bufs[p])
+        e1.record()
+        torch.cuda.synchronize()
+        adj[p] = e0.elapsed_time(e1) / args.steps
+    errs = {}
+    for k, name in enumerate(("mu", "nu", "x")):
+        ref = bufs[dd.FP64][k]
+        errs[name] = float((bufs[dd.FP32][k] - ref).abs().max() / ref.abs().max())
+    sc = g.score()
+    g.close()
+    line = {"metric": "backward (adjoint) time, 512x512 UOT score gradient", "value": times[dd.FP32],
+            "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": times[dd.FP32],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "grad512", "N": N, "eps": eps, "lam": lam, "masses": [1.0, 1.1], "basic_cell": s},
+            "backward_fp64_ms": times[dd.FP64],
+            "adjoint_only_ms": {"fp32": adj[dd.FP32], "fp64": adj[dd.FP64]},
+            "fp32_vs_fp64_rel_err": errs,
+            "solve": {"seconds": t_solve, "sweeps": info["sweeps"], "rel_gap": info["rel_gap"], "score": sc[0]}}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -293,7 +358,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--lam", type=float, default=1.0)
-    ap.add_argument("--workload", default="blobs256", choices=["blobs256", "batch64"])
+    ap.add_argument("--workload", default="blobs256", choices=["blobs256", "batch64", "grad512"])
     ap.add_argument("--no-extras", action="store_true", help="skip time-to-gap, e2e and CPU baseline")
     ap.add_argument("--quick-warm", action="store_true",
                     help="float-only, capped warm start (profiling runs; not a bench number)")
@@ -317,9 +382,9 @@ def main():
     from paper_2410_08859_gb300 import domdec as dd
     dd.lib()
 
-    if args.workload == "batch64":
+    if args.workload in ("batch64", "grad512"):
         if rank == 0:
-            run_batch(args, dd, torch)
+            (run_batch if args.workload == "batch64" else run_grad)(args, dd, torch)
         if world > 1:
             dist.barrier()
             dist.destroy_process_group()

@@ -74,10 +74,14 @@ typedef struct {
   double arena_factor; /* box arena capacity in units of N*N doubles (0: default 48) */
   double eps_init;     /* eps of the warm-start duals passed to domdec_init (ignored without duals) */
   int    profile;      /* 1: time every kernel of a sweep with CUDA events on the handle's stream */
-  int    spill_slots;  /* cells whose Y-box exceeds max_ny run from global memory slots: 0 = default
-                          (up to 4 GiB), > 0 = that many, < 0 = none (such cells fail with DOMDEC_ETOOBIG) */
+  int    spill_slots;  /* cells whose Y-box exceeds max_ny run from global memory slots (per sub-batch): 0 = default
+                          (up to 32 slots and 4 GiB), > 0 = that many, < 0 = none (such cells fail with DOMDEC_ETOOBIG) */
   int    cell_ctas;    /* CTAs per cell: 0 = a 2-CTA cluster when all cells of a sub-batch fit as resident
                           clusters (else 1), 1 = always one CTA per cell */
+  int    cell_ti;      /* 1: after each X-half of a cell solve, shift alpha by the t maximising the cell
+                          dual along (alpha + t, beta - t) (closed form; not in the paper: it removes the
+                          slow total-mass mode of the alternation when eps << lam, same fixed point);
+                          0 (default): the paper's plain alternation */
 } domdec_params;
 
 typedef struct {
@@ -122,6 +126,12 @@ int domdec_iterate(domdec_t h, int n_sweeps);
  * the tracked score valid for the new eps without re-instantiating the plan. */
 int domdec_set_eps(domdec_t h, double eps);
 
+/* Change the cell stopping tolerance `err` of domdec_params between sweeps
+ * (Section 5.3, "Stopping criterion"; the paper keeps it fixed at 2e-5, a
+ * caller may tighten it as the global gap falls).  err < 0 runs maxit
+ * iterations per cell. */
+int domdec_set_tolerance(domdec_t h, double err);
+
 /* Wait for the stream and report device-side errors / warnings.  Synchronises. */
 int domdec_sync(domdec_t h);
 
@@ -146,6 +156,37 @@ int domdec_duals(domdec_t h, double* alpha);
  * |P_Y - e^{-beta_star/lam} nu|_1.  beta (N*N, host or device) receives beta_star
  * if not NULL.  Uses the separable FP64 log-sum-exp.  Synchronises. */
 int domdec_pd_gap(domdec_t h, double out[5], double* beta);
+
+/* Gradients of the unbalanced OT value S(mu, nu, x) = max D(alpha, beta)
+ * (Eq. dual-problem, nu_- = 0, D_i = lam KL) with respect to the weights mu, nu
+ * and the source positions x = (i, j)/N of the grid (row-major).  The paper
+ * does not differentiate S; by the envelope theorem its derivatives at the
+ * optimal potentials are those of D at fixed (alpha, beta):
+ *   grad_mu(x) = eps |nu| - eps P_X(x)/mu(x) - lam (e^{-alpha(x)/lam} - 1)
+ *   grad_nu(y) = eps |mu| - eps P_Y(y)/nu(y) - lam (e^{-beta(y)/lam} - 1)
+ *   grad_x(x)  = 2 P_X(x) (x - T(x)),  T(x) = sum_y pi(x,y) y / P_X(x)
+ * with pi = exp((alpha + beta - c)/eps) mu x nu never formed (separable
+ * log-sum-exp passes over the grid; T carried as conditional means).
+ * mu, nu (> 0), alpha, beta: N*N doubles, host or device.  precision:
+ * DOMDEC_FP32 or DOMDEC_FP64 for the exponentials and sums of the summed
+ * terms (either way their exponents are formed in double and terms below
+ * 2^-32 (FP32) / 2^-64 (FP64) of the largest are skipped after a float test).  grad_mu, grad_nu (N*N), grad_x (2*N*N: d/dx_i,
+ * d/dx_j per point) are host or device buffers, each may be NULL.
+ * out[0] = D(alpha, beta), out[1] = |mu|, out[2] = |nu|, out[3] = |P_X pi|,
+ * out[4] = |P_Y pi| (out may be NULL).  N <= 4096.  DOMDEC_EINVAL on a bad
+ * argument or a non-positive weight / non-finite potential.  Allocates its
+ * scratch with cudaMallocAsync on `stream`; synchronises. */
+int domdec_uot_gradients(const double* mu, const double* nu, const double* alpha,
+                         const double* beta, int N, double eps, double lambda,
+                         int precision, double* grad_mu, double* grad_nu,
+                         double* grad_x, double out[5], void* stream);
+
+/* domdec_uot_gradients at the handle's state: alpha = the stitched X-potential
+ * (as domdec_duals), beta = beta_star of one global closed-form Y-half of it
+ * (as domdec_pd_gap; written to `beta` if not NULL).  On the handle's stream;
+ * synchronises. */
+int domdec_gradients(domdec_t h, int precision, double* grad_mu, double* grad_nu,
+                     double* grad_x, double out[5], double* beta);
 
 /* Basic-cell Y-marginals: box[4*i..4*i+3] = (k0, l0, H, W) of nu_i in Y pixel
  * coordinates (H*W == 0: empty), values of all boxes concatenated in basic-cell
@@ -202,6 +243,10 @@ const char* domdec_error_string(int code);
  * maxit. */
 #define DOMDEC_SINKHORN_DENSE     0
 #define DOMDEC_SINKHORN_SEPARABLE 1
+#define DOMDEC_SINKHORN_TI        4  /* or-ed into `variant`: translation step after each X-half (not in the
+                                        paper): alpha += (lam/2) log(<e^{-alpha/lam},mu> / <e^{-beta/lam},nu>),
+                                        the dual's maximiser along (alpha + t, beta - t); same fixed point.
+                                        Not accepted by domdec_full_sinkhorn_noalloc. */
 int domdec_full_sinkhorn(const double* mu, const double* nu, int N, double eps_start,
                          double eps, double lambda, int variant, int precision,
                          int maxit, double err, int check_every,

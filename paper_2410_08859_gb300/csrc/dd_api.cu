@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -38,8 +39,9 @@ cudaError_t launch_init_duals_boxes(const DevState& S, const double* alpha0, con
                                     double* nu_mom, double* mumass, long long* newoff, cudaStream_t st);
 cudaError_t launch_init_duals_fill(const DevState& S, const double* alpha0, const double* beta0, double eps0,
                                    const double* w, long long* newoff, cudaStream_t st);
-cudaError_t launch_score(const DevState& S, double* out, cudaStream_t st);
-cudaError_t launch_cert(const DevState& S, const double* z, double* beta_out, double* out, cudaStream_t st);
+cudaError_t launch_score(const DevState& S, double* out, cudaStream_t st, double* partials);
+cudaError_t launch_cert(const DevState& S, const double* z, double* beta_out, double* out, cudaStream_t st,
+                        double* partials);
 cudaError_t launch_regrow(const DevState& S, double* new0, double* new1, long long* newoff, cudaStream_t st);
 cudaError_t global_lse64(const double* pot, const double* logm, double eps, double h, int N, double* out,
                          double* buf_a, double* buf_b, double* buf_c, cudaStream_t st);
@@ -47,6 +49,10 @@ int full_sinkhorn_dev(const double* mu, const double* nu, const double* logmu, c
                       double eps_start, double eps, double lam, int variant, int precision, int maxit,
                       double err, int check_every, double* alpha, double* beta, double* out, double* d_eval,
                       cudaStream_t st, cudaError_t* cerr);
+size_t adjoint_scratch_size(int N, int precision);
+cudaError_t adjoint_dev(const double* mu, const double* nu, const double* alpha, const double* beta, int N,
+                        double eps, double lam, int precision, double* grad_mu, double* grad_nu, double* grad_x,
+                        double* d_out, void* scratch, int* d_bad, cudaStream_t st);
 
 namespace {
 constexpr int LOGCAP = 4096;
@@ -65,6 +71,7 @@ struct domdec_s {
   int max_batch = 0;
   long long* d_newoff = nullptr;
   double* d_scratch = nullptr;  // 64 doubles
+  double* d_partials = nullptr; // kRedBlocks * 8 doubles: block partials of the grid reductions
   double* d_numom = nullptr;
   double* d_mumass = nullptr;
   double* h_pinned = nullptr;   // 64 doubles
@@ -331,6 +338,7 @@ int domdec_init(domdec_t* out, const double* mu, const double* nu, int N, const 
   std::memset(&S, 0, sizeof(S));
   S.N = N; S.s = h->s; S.nb = h->nb; S.nbasic = h->nbasic;
   S.h = 1.0 / N; S.eps = pin->eps; S.lam = pin->lambda; S.thr = pin->trunc_thr; S.err = pin->err;
+  S.ti = pin->cell_ti ? 1 : 0;
   S.tau = pin->tau; S.maxit = pin->maxit; S.newton_maxit = pin->newton_maxit; S.strategy = pin->strategy;
   S.margin = pin->box_margin;
   // shared-memory capacity of the cell kernel
@@ -388,7 +396,8 @@ int domdec_init(domdec_t* out, const double* mu, const double* nu, int N, const 
   DD_ALLOC(S.theta, 1); DD_ALLOC(S.declog, 4 * LOGCAP); DD_ALLOC(S.counters, NCOUNT);
   DD_ALLOC(S.slotctr, 1);
   DD_ALLOC(S.status, 1); DD_ALLOC(S.red, 2 * 152 * 5 + 8); DD_ALLOC(S.red_count, 1);
-  DD_ALLOC(h->d_newoff, h->nbasic + 1); DD_ALLOC(h->d_scratch, 64); DD_ALLOC(h->d_numom, 8);
+  DD_ALLOC(h->d_newoff, h->nbasic + 1); DD_ALLOC(h->d_scratch, 64);
+  DD_ALLOC(h->d_partials, kRedBlocks * 8); DD_ALLOC(h->d_numom, 8);
   {
     // spill slots for cell boxes beyond the shared-memory capacity: Y-side arrays
     // (4 s N + 5 N^2 values) followed by 4 N^2 doubles of new marginals
@@ -396,8 +405,8 @@ int domdec_init(domdec_t* out, const double* mu, const double* nu, int N, const 
     size_t ybytes = rs * (4 * (size_t)h->s * N + 5 * (size_t)n);
     ybytes = (ybytes + 255) / 256 * 256;
     const size_t stride = ybytes + 4 * (size_t)n * sizeof(double);
-    const size_t budget = (size_t)4 << 30;  // at most 4 GiB of slots
-    int slots = (int)std::min<size_t>((size_t)std::max(1, mb), std::max<size_t>(1, budget / stride));
+    const size_t budget = (size_t)4 << 30;  // at most 4 GiB and 32 slots by default (spilled cells are rare)
+    int slots = (int)std::min<size_t>(std::min<size_t>((size_t)std::max(1, mb), 32), std::max<size_t>(1, budget / stride));
     if (pin->spill_slots > 0) slots = pin->spill_slots;
     if (pin->spill_slots < 0) slots = 0;
     S.spill_stride = (long long)stride;
@@ -499,6 +508,17 @@ int domdec_set_eps(domdec_t h, double eps) {
   return DOMDEC_OK;
 }
 
+int domdec_set_tolerance(domdec_t h, double err) {
+  if (!h) return DOMDEC_EINVAL;
+  if (h->sticky) return DOMDEC_ESTATE;
+  if (!(err == err) || std::isinf(err)) return DOMDEC_EINVAL;
+  h->S.err = err;
+  h->p.err = err;
+  for (int k = 0; k < 2; ++k)
+    if (h->graph[k]) { cudaGraphExecDestroy(h->graph[k]); h->graph[k] = nullptr; }
+  return DOMDEC_OK;
+}
+
 int domdec_sync(domdec_t h) {
   if (!h) return DOMDEC_EINVAL;
   if (h->sticky) return DOMDEC_ESTATE;
@@ -515,7 +535,7 @@ int domdec_sync(domdec_t h) {
 int domdec_score(domdec_t h, double out[6]) {
   if (!h || !out) return DOMDEC_EINVAL;
   if (h->sticky) return DOMDEC_ESTATE;
-  if (launch_score(h->S, h->d_scratch, h->st) != cudaSuccess) return fail(h, DOMDEC_ECUDA);
+  if (launch_score(h->S, h->d_scratch, h->st, h->d_partials) != cudaSuccess) return fail(h, DOMDEC_ECUDA);
   cudaMemcpyAsync(h->h_pinned, h->d_scratch, 5 * sizeof(double), cudaMemcpyDeviceToHost, h->st);
   cudaMemcpyAsync(h->h_pinned + 8, h->S.theta, sizeof(double), cudaMemcpyDeviceToHost, h->st);
   if (cudaStreamSynchronize(h->st) != cudaSuccess) return fail(h, DOMDEC_ECUDA);
@@ -559,8 +579,8 @@ int domdec_pd_gap(domdec_t h, double out[5], double* beta) {
   if (cudaMallocAsync(&buf, 5 * (size_t)n * sizeof(double), h->st) != cudaSuccess) return fail(h, DOMDEC_ENOMEM);
   double *z = buf, *ba = buf + n, *bb = buf + 2 * (size_t)n, *bt = buf + 3 * (size_t)n, *bc = buf + 4 * (size_t)n;
   cudaError_t e = global_lse64(h->S.alpha, h->S.logmu, h->S.eps, h->S.h, h->N, z, ba, bb, bc, h->st);
-  if (e == cudaSuccess) e = launch_cert(h->S, z, bt, h->d_scratch + 16, h->st);
-  if (e == cudaSuccess) e = launch_score(h->S, h->d_scratch, h->st);
+  if (e == cudaSuccess) e = launch_cert(h->S, z, bt, h->d_scratch + 16, h->st, h->d_partials);
+  if (e == cudaSuccess) e = launch_score(h->S, h->d_scratch, h->st, h->d_partials);
   if (e == cudaSuccess && beta) e = cudaMemcpyAsync(beta, bt, n * sizeof(double), cudaMemcpyDefault, h->st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->h_pinned, h->d_scratch, 24 * sizeof(double), cudaMemcpyDeviceToHost, h->st);
@@ -657,7 +677,7 @@ int domdec_get_stats(domdec_t h, domdec_stats* s) {
   if (!h || !s) return DOMDEC_EINVAL;
   if (h->sticky) return DOMDEC_ESTATE;
   unsigned long long c[NCOUNT];
-  if (launch_score(h->S, h->d_scratch, h->st) != cudaSuccess) return fail(h, DOMDEC_ECUDA);
+  if (launch_score(h->S, h->d_scratch, h->st, h->d_partials) != cudaSuccess) return fail(h, DOMDEC_ECUDA);
   cudaMemcpyAsync(h->h_pinned, h->d_scratch, 5 * sizeof(double), cudaMemcpyDeviceToHost, h->st);
   if (cudaStreamSynchronize(h->st) != cudaSuccess ||
       cudaMemcpy(c, h->S.counters, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -679,8 +699,8 @@ int domdec_full_sinkhorn(const double* mu, const double* nu, int N, double eps_s
                          int variant, int precision, int maxit, double err, int check_every,
                          const double* beta_in, double* alpha, double* beta, double out[4], void* stream) {
   if (!mu || !nu || !out || N <= 0) return DOMDEC_EINVAL;
-  if (!(eps > 0.0) || !(lambda > 0.0) || (variant != 0 && variant != 1) || precision < 0 || precision > 2 ||
-      maxit < 1)
+  const int var = variant & ~DOMDEC_SINKHORN_TI;
+  if (!(eps > 0.0) || !(lambda > 0.0) || (var != 0 && var != 1) || precision < 0 || precision > 2 || maxit < 1)
     return DOMDEC_EINVAL;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int n = N * N;
@@ -723,6 +743,90 @@ int domdec_full_sinkhorn(const double* mu, const double* nu, int N, double eps_s
   return rc;
 }
 
+
+// ---------------------------------------------------------------- gradients
+namespace {
+// Runs the adjoint on device arrays and copies the results to the caller's
+// buffers (host or device; each may be NULL).  Returns a DOMDEC_* code.
+int gradients_run(const double* dmu, const double* dnu, const double* dalpha, const double* dbeta, int N,
+                  double eps, double lam, int precision, double* grad_mu, double* grad_nu, double* grad_x,
+                  double out[5], cudaStream_t st) {
+  const size_t n = (size_t)N * N;
+  const size_t sb = adjoint_scratch_size(N, precision);
+  unsigned char* buf = nullptr;
+  const size_t head = (4 * n + 8) * sizeof(double) + 256;  // gm, gn, gx (2n), out; then 256-aligned scratch
+  if (cudaMallocAsync(&buf, head + sb, st) != cudaSuccess) return DOMDEC_ENOMEM;
+  double* gm = reinterpret_cast<double*>(buf);
+  double* gn = gm + n;
+  double* gx = gn + n;           // 2 n
+  double* dout = gx + 2 * n;     // 8
+  int* dbad = reinterpret_cast<int*>(dout + 7);
+  unsigned char* scratch =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dout + 8) + 255) & ~uintptr_t(255));
+  cudaError_t e = cudaMemsetAsync(dbad, 0, sizeof(int), st);
+  if (e == cudaSuccess)
+    e = adjoint_dev(dmu, dnu, dalpha, dbeta, N, eps, lam, precision, gm, gn, gx, dout, scratch, dbad, st);
+  double hout[8];
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hout, dout, 8 * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && grad_mu) e = cudaMemcpyAsync(grad_mu, gm, n * sizeof(double), cudaMemcpyDefault, st);
+  if (e == cudaSuccess && grad_nu) e = cudaMemcpyAsync(grad_nu, gn, n * sizeof(double), cudaMemcpyDefault, st);
+  if (e == cudaSuccess && grad_x) e = cudaMemcpyAsync(grad_x, gx, 2 * n * sizeof(double), cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFreeAsync(buf, st);
+  if (e != cudaSuccess) return DOMDEC_ECUDA;
+  int bad = 0;
+  std::memcpy(&bad, &hout[7], sizeof(int));
+  if (bad) return DOMDEC_EINVAL;
+  if (out) for (int k = 0; k < 5; ++k) out[k] = hout[k];
+  return DOMDEC_OK;
+}
+}  // namespace
+
+int domdec_uot_gradients(const double* mu, const double* nu, const double* alpha, const double* beta, int N,
+                         double eps, double lambda, int precision, double* grad_mu, double* grad_nu,
+                         double* grad_x, double out[5], void* stream) {
+  if (!mu || !nu || !alpha || !beta || N <= 0 || N > 4096) return DOMDEC_EINVAL;
+  if (!(eps > 0.0) || !(lambda > 0.0) || (precision != DOMDEC_FP32 && precision != DOMDEC_FP64))
+    return DOMDEC_EINVAL;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const size_t n = (size_t)N * N;
+  double* buf = nullptr;
+  if (cudaMallocAsync(&buf, 4 * n * sizeof(double), st) != cudaSuccess) return DOMDEC_ENOMEM;
+  cudaError_t e = cudaMemcpyAsync(buf, mu, n * sizeof(double), cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(buf + n, nu, n * sizeof(double), cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(buf + 2 * n, alpha, n * sizeof(double), cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(buf + 3 * n, beta, n * sizeof(double), cudaMemcpyDefault, st);
+  int rc = e == cudaSuccess ? gradients_run(buf, buf + n, buf + 2 * n, buf + 3 * n, N, eps, lambda, precision,
+                                            grad_mu, grad_nu, grad_x, out, st)
+                            : DOMDEC_ECUDA;
+  cudaFreeAsync(buf, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess && rc == DOMDEC_OK) rc = DOMDEC_ECUDA;
+  return rc;
+}
+
+int domdec_gradients(domdec_t h, int precision, double* grad_mu, double* grad_nu, double* grad_x,
+                     double out[5], double* beta) {
+  if (!h) return DOMDEC_EINVAL;
+  if (precision != DOMDEC_FP32 && precision != DOMDEC_FP64) return DOMDEC_EINVAL;
+  if (h->sticky) return DOMDEC_ESTATE;
+  if (h->N > 4096) return DOMDEC_EINVAL;
+  const int n = h->n;
+  double* buf = nullptr;
+  if (cudaMallocAsync(&buf, 5 * (size_t)n * sizeof(double), h->st) != cudaSuccess) return fail(h, DOMDEC_ENOMEM);
+  double *z = buf, *ba = buf + n, *bb = buf + 2 * (size_t)n, *bt = buf + 3 * (size_t)n, *bc = buf + 4 * (size_t)n;
+  // beta_star: one global closed-form Y-half of the stitched alpha (Eq. sinkhorn-iters-ot)
+  cudaError_t e = global_lse64(h->S.alpha, h->S.logmu, h->S.eps, h->S.h, h->N, z, ba, bb, bc, h->st);
+  if (e == cudaSuccess) e = launch_cert(h->S, z, bt, h->d_scratch + 16, h->st, h->d_partials);
+  if (e == cudaSuccess && beta) e = cudaMemcpyAsync(beta, bt, n * sizeof(double), cudaMemcpyDefault, h->st);
+  int rc = e == cudaSuccess ? gradients_run(h->S.mu, h->S.nu, h->S.alpha, bt, h->N, h->S.eps, h->S.lam, precision,
+                                            grad_mu, grad_nu, grad_x, out, h->st)
+                            : DOMDEC_ECUDA;
+  cudaFreeAsync(buf, h->st);
+  if (cudaStreamSynchronize(h->st) != cudaSuccess) rc = DOMDEC_ECUDA;
+  if (rc == DOMDEC_ECUDA || rc == DOMDEC_ENOMEM) return fail(h, rc);
+  if (rc) return rc;
+  return read_status(h);
+}
 
 // ---------------------------------------------------------------- batches
 struct domdec_batch_s {

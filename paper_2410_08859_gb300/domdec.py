@@ -20,7 +20,7 @@ DOMDEC_ETOOBIG, DOMDEC_EARENA, DOMDEC_ESTATE, DOMDEC_ENOLIB = -4, -5, -6, -7
 STAGGERED, SWIFT, SAFE, GREEDY = 0, 1, 2, 3
 STRATEGIES = {"staggered": STAGGERED, "swift": SWIFT, "safe": SAFE, "greedy": GREEDY}
 FP32, FP64, MIXED = 0, 1, 2
-SINKHORN_DENSE, SINKHORN_SEPARABLE = 0, 1
+SINKHORN_DENSE, SINKHORN_SEPARABLE, SINKHORN_TI = 0, 1, 4
 
 
 class DomDecError(RuntimeError):
@@ -38,7 +38,7 @@ class domdec_params(ctypes.Structure):
                 ("box_margin", ctypes.c_int), ("max_ny", ctypes.c_int),
                 ("arena_factor", ctypes.c_double), ("eps_init", ctypes.c_double),
                 ("profile", ctypes.c_int), ("spill_slots", ctypes.c_int),
-                ("cell_ctas", ctypes.c_int)]
+                ("cell_ctas", ctypes.c_int), ("cell_ti", ctypes.c_int)]
 
 
 class domdec_stats(ctypes.Structure):
@@ -64,6 +64,7 @@ _SIGS = {
     "domdec_init": (_I, [ctypes.POINTER(_P), _P, _P, _I, ctypes.POINTER(domdec_params), _P, _P, _P]),
     "domdec_iterate": (_I, [_P, _I]),
     "domdec_set_eps": (_I, [_P, _D]),
+    "domdec_set_tolerance": (_I, [_P, _D]),
     "domdec_sync": (_I, [_P]),
     "domdec_score": (_I, [_P, _DP]),
     "domdec_plan_marginals": (_I, [_P, _P, _P]),
@@ -78,6 +79,8 @@ _SIGS = {
     "domdec_error_string": (ctypes.c_char_p, [_I]),
     "domdec_full_sinkhorn": (_I, [_P, _P, _I, _D, _D, _D, _I, _I, _I, _D, _I, _P, _P, _P, _DP, _P]),
     "domdec_full_sinkhorn_noalloc": (_I, [_P, _P, _I, _D, _D, _D, _I, _I, _I, _D, _I, _P, _P, _P, _DP, _P]),
+    "domdec_uot_gradients": (_I, [_P, _P, _P, _P, _I, _D, _D, _I, _P, _P, _P, _DP, _P]),
+    "domdec_gradients": (_I, [_P, _I, _P, _P, _P, _DP, _P]),
     "domdec_batch_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(_P), _I]),
     "domdec_batch_iterate": (_I, [_P, _I]),
     "domdec_batch_sync": (_I, [_P]),
@@ -182,6 +185,10 @@ def domdec_set_eps(h, eps):
     return _check(lib().domdec_set_eps(h, float(eps)), "domdec_set_eps")
 
 
+def domdec_set_tolerance(h, err):
+    _check(lib().domdec_set_tolerance(h, float(err)), "domdec_set_tolerance")
+
+
 def domdec_sync(h):
     return _check(lib().domdec_sync(h), "domdec_sync")
 
@@ -279,6 +286,29 @@ def domdec_full_sinkhorn_noalloc(mu, nu, N, eps, lam, alpha, beta, eps_start=Non
     return int(out[0]), out[1], out[2], out[3], rc
 
 
+def domdec_uot_gradients(mu, nu, alpha, beta, N, eps, lam, precision=FP64, grad_mu=None, grad_nu=None,
+                         grad_x=None, stream=None):
+    """Envelope-theorem gradients of the UOT value at potentials (alpha, beta)
+    into grad_mu, grad_nu (N*N) and grad_x (2*N*N); returns
+    [D(alpha, beta), |mu|, |nu|, |P_X pi|, |P_Y pi|]."""
+    out = (ctypes.c_double * 5)()
+    n = N * N
+    rc = lib().domdec_uot_gradients(_ptr(mu, n), _ptr(nu, n), _ptr(alpha, n), _ptr(beta, n), int(N), float(eps),
+                                    float(lam), int(precision), _ptr(grad_mu, n, True), _ptr(grad_nu, n, True),
+                                    _ptr(grad_x, 2 * n, True), out, _stream_ptr(stream))
+    _check(rc, "domdec_uot_gradients")
+    return list(out)
+
+
+def domdec_gradients(h, N, precision=FP64, grad_mu=None, grad_nu=None, grad_x=None, beta=None):
+    """domdec_uot_gradients at a handle's state (alpha stitched, beta_star)."""
+    out = (ctypes.c_double * 5)()
+    n = N * N
+    _check(lib().domdec_gradients(h, int(precision), _ptr(grad_mu, n, True), _ptr(grad_nu, n, True),
+                                  _ptr(grad_x, 2 * n, True), out, _ptr(beta, n, True)), "domdec_gradients")
+    return list(out)
+
+
 class DomDecBatch:
     """Many independent DomDec problems swept together (the handles stay
     owned by their DomDec objects, which must outlive the batch)."""
@@ -341,6 +371,9 @@ class DomDec:
     def set_eps(self, eps):
         domdec_set_eps(self.h, eps)
 
+    def set_tolerance(self, err):
+        domdec_set_tolerance(self.h, err)
+
     def score(self):
         return domdec_score(self.h)
 
@@ -362,6 +395,16 @@ class DomDec:
 
     def basic_marginals(self):
         return domdec_basic_marginals(self.h, self.nbasic)
+
+    def gradients(self, precision=FP64, grad_mu=None, grad_nu=None, grad_x=None, beta=None):
+        """d(score)/d mu, d(score)/d nu, d(score)/d x at the current state
+        (NumPy arrays unless buffers are given); returns (g_mu, g_nu, g_x, out)."""
+        n = self.N * self.N
+        g_mu = np.empty(n) if grad_mu is None else grad_mu
+        g_nu = np.empty(n) if grad_nu is None else grad_nu
+        g_x = np.empty(2 * n) if grad_x is None else grad_x
+        out = domdec_gradients(self.h, self.N, precision, g_mu, g_nu, g_x, beta)
+        return g_mu, g_nu, g_x, out
 
     def stats(self):
         return domdec_get_stats(self.h)
