@@ -330,8 +330,9 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
   // the barycentre of nu_J, whose nearest pixel is the Y frame origin (so
   // that 2 q D.xi carries the cell's mean displacement).  Both CTAs of a
   // pair load everything.
+  double a_tot = 0.0;   // |nu_{-J}| on B_J (translation step)
   {
-    double m3[3] = {0.0, 0.0, 0.0};
+    double m3[4] = {0.0, 0.0, 0.0, 0.0};
     for (int u = tid; u < ny; u += nthr) {
       int kk = u / W, ll = u - kk * W;
       int y1 = k0 + kk, y2 = l0 + ll, y = y1 * N + y2;
@@ -339,14 +340,16 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
 #pragma unroll
       for (int q4 = 0; q4 < 4; ++q4) nuJ += box_value(sbox[q4], arena, y1, y2);
       double nuy = S.nu[y];
-      R rho = R(fmax(0.0, S.PY[y] - nuJ)) / R(nuy);
+      const double num = fmax(0.0, S.PY[y] - nuJ);
+      R rho = R(num) / R(nuy);
       if (!spilled || crank == 0) {
         lrho[u] = rho > R(0) ? dd_lg2(rho) * R(DD_LN2) : -dd_inf<R>();
         lnu[u] = R(S.lognu[y]);
       }
-      m3[0] += nuJ; m3[1] += nuJ * kk; m3[2] += nuJ * ll;
+      m3[0] += nuJ; m3[1] += nuJ * kk; m3[2] += nuJ * ll; m3[3] += num;
     }
-    block_sum<3>(m3, red);
+    block_sum<4>(m3, red);
+    a_tot = m3[3];
     if (tid == 0) {
       int c1 = H / 2, c2 = W / 2;
       if (m3[0] > 0.0) {
@@ -377,11 +380,13 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
     acc2[1] += S.mu[x];
   }
   block_sum<2>(acc2, red);
-  const double A = acc2[0] / nx, muJ = acc2[1];
-  const double B = q * (double)(D1 * D1 + D2 * D2) - A;
-  const R sB = R(sl * B);
+  double A = acc2[0] / nx;
+  const double muJ = acc2[1];
+  const double qD2 = q * (double)(D1 * D1 + D2 * D2);
+  R sB = R(sl * (qD2 - A));   // s B with B = q|D|^2 - A
   const R cEta1 = R(sl * 2.0 * q * D1), cEta2 = R(sl * 2.0 * q * D2);
-  const R cA = R(-(1.0 - rr) * A);
+  R cA = R(-(1.0 - rr) * A);
+  R gA = R(-sl * A);          // -s A: the A part of -alpha/lam
   const R cD1 = R(2.0 * (1.0 - rr) * q * D1), cD2 = R(2.0 * (1.0 - rr) * q * D2);
   for (int t = tid; t < nx; t += nthr) {
     int r = t / nx2, c = t - r * nx2;
@@ -392,7 +397,7 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
     R l = R(S.logmu[x]);
     av[t] = a;
     lm[t] = l;
-    g0[t] = R(-sl * (A + lin));
+    g0[t] = R(-sl * lin);
     xa[t] = (a + l) * R(DD_LOG2E);
   }
   csync();
@@ -405,6 +410,11 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
   const R LN2 = R(DD_LN2), L2E = R(DD_LOG2E);
   R* gpart = reinterpret_cast<R*>(red) + 32 * 12;   // per-warp gap partials of both CTAs
   R* const gpart_p = peer(gpart);
+  R* apart = gpart + 32;                             // per-warp <e^{-alpha/lam}, mu> (translation step)
+  R* bpart = gpart + 64;                             // per-warp <e^{-beta/lam}, nu>
+  R* const apart_p = peer(apart);
+  R* const bpart_p = peer(bpart);
+  const bool ti = S.ti && sl > 0.0;
   const int lane = tid & 31, wid = tid >> 5, nwarp = nthr >> 5;
   int it = 0;
   double gap = 0.0;
@@ -428,6 +438,7 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
     }
     csync();
     // Y-half, pass over rows of X: Z(kk, ll), then the Newton root per y (a3)
+    R bsum = R(0);
     if (fused_y) {
       // every lane runs the same number of rounds (lse2_group is warp-collective)
       const int rounds = (ny + 2 * gthr - 1) / (2 * gthr);
@@ -455,6 +466,8 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
           R b = root[k] - Zn[k];
           put(bv, bv_p, uu[k], b);
           put(bl, bl_p, uu[k], (b + lnu[uu[k]]) * L2E);
+          // nu e^{-beta/lam}: -s beta/eps = -(s root + c0)
+          if (ti) bsum += dd_ex2((lnu[uu[k]] - sR * root[k] - c0[k]) * L2E);
         }
       }
     } else {
@@ -486,8 +499,13 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
           R b = root[k] - Zv[uu[k]] * LN2;
           put(bv, bv_p, uu[k], b);
           put(bl, bl_p, uu[k], (b + lnu[uu[k]]) * L2E);
+          if (ti) bsum += dd_ex2((lnu[uu[k]] - sR * root[k] - c0[k]) * L2E);
         }
       }
+    }
+    if (ti) {
+      bsum = warp_sum(bsum);
+      if (lane == 0) put(bpart, bpart_p, crank * nwarp + wid, bsum);
     }
     csync();
     // X-half, pass over columns of B_J: U(kk, c) = log2 sum_ll 2^{bl(kk,ll) - q2 (ll - (c - offc))^2}
@@ -505,7 +523,7 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
     csync();
     // X-half, pass over rows of B_J: W, the gap terms (a4) and the next a (a2)
     {
-      R gl = R(0);
+      R gl = R(0), asum = R(0);
       const int P = lanes_per_target(nx, H, gthr), ni = (nx * P + 31) & ~31;
       for (int i = gtid; i < ni; i += gthr) {
         const int tg0 = i / P, part = i - tg0 * P, t = min(tg0, nx - 1);
@@ -516,16 +534,21 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
           put(Wv, Wv_p, t, W2);
           R a = av_c[t];
           R tt = a + W2 * LN2;         // log(P_X pi / mu)
-          R g = g0[t] - sR * a;        // -alpha/lam
+          R g = gA + g0[t] - sR * a;   // -alpha/lam
           gl += dd_ex2((lm[t] + g) * L2E) * dd_psi<R>(tt - g);
           R xi1 = R(cd.i0 + r - xc1), xi2 = R(cd.j0 + c - xc2);
           R an = cA - rR * W2 * LN2 - cD1 * xi1 - cD2 * xi2;
           put(av_n, av_np, t, an);
           put(xa_n, xa_np, t, (an + lm[t]) * L2E);
+          if (ti) asum += dd_ex2((lm[t] + gA + g0[t] - sR * an) * L2E);   // mu e^{-alpha_new/lam}
         }
       }
       gl = warp_sum(gl);
       if (lane == 0) put(gpart, gpart_p, crank * nwarp + wid, gl);
+      if (ti) {
+        asum = warp_sum(asum);
+        if (lane == 0) put(apart, apart_p, crank * nwarp + wid, asum);
+      }
     }
     csync();
     {
@@ -535,6 +558,23 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
     }
     first = false;
     if ((S.err >= 0.0 && gap <= tol) || it >= S.maxit || !(gap == gap)) break;
+    if (ti) {
+      // translation step: alpha += t*, e^{t*/lam} = (a + sqrt(a^2 + 4 A_s B_s)) / (2 B_s); in the
+      // cell frame alpha/eps = A + a(xi) + 2qD.xi it moves A by t*/eps = log(u)/s (same in
+      // every thread of both CTAs: the partials are replicated)
+      double As = 0.0, Bs = 0.0;
+      for (int w = 0; w < csize * nwarp; ++w) {
+        As += (double)apart[w];
+        Bs += (double)bpart[w];
+      }
+      const double uu = (a_tot + sqrt(a_tot * a_tot + 4.0 * As * Bs)) / (2.0 * Bs);
+      if (uu > 0.0 && uu < INFINITY) {
+        A += log(uu) / sl;
+        sB = R(sl * (qD2 - A));
+        cA = R(-(1.0 - rr) * A);
+        gA = R(-sl * A);
+      }
+    }
     // accept the X-update: swap the buffers (every thread of both CTAs does the same)
     R* tp = av_c; av_c = av_n; av_n = tp;
     tp = av_cp; av_cp = av_np; av_np = tp;

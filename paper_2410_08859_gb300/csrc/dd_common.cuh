@@ -43,6 +43,7 @@ struct DevState {
   int N, s, nb, nbasic;
   double h, eps, lam, thr, err, tau;
   int maxit, newton_maxit, strategy, margin;
+  int ti;                       // translation step after each cell X-half (0/1)
   int cap_ny, cap_side;
   unsigned char* spill;         // spill slots: Y-side arrays and new marginals of cells too large
   long long spill_stride;       //   for shared memory (bytes per slot)
@@ -168,6 +169,24 @@ __device__ __forceinline__ void block_sum(T (&v)[K], T* scratch) {
   for (int k = 0; k < K; ++k) v[k] = scratch[32 * K + k];
   __syncthreads();
 }
+
+// Two-stage grid reduction (deterministic): each of G blocks writes its K
+// block sums to partials[blockIdx.x * K + k]; k_sum_partials then adds the G
+// rows in block order.  With G = 1 the single block writes the result itself.
+constexpr int kRedBlocks = 2 * 152;
+inline int red_blocks(long long n, int threads, const double* partials) {
+  if (!partials) return 1;
+  long long g = (n + threads - 1) / threads;
+  return (int)(g < 1 ? 1 : (g > kRedBlocks ? kRedBlocks : g));
+}
+template <int K>
+__device__ __forceinline__ void block_sum_to(double (&v)[K], double* scratch, double* dst) {
+  block_sum<K>(v, scratch);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) dst[blockIdx.x * K + k] = v[k];
+}
+__global__ void k_sum_partials(const double* partials, int G, int K, double* out);
 
 // New marginals of cell position j of the current launch (quadrant stride in *stride).
 __device__ __forceinline__ double* cell_nut(const DevState& S, const CellOut& o, int j, int* stride) {

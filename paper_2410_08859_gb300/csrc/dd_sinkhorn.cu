@@ -173,7 +173,7 @@ k_sk_eval(const double* __restrict__ mu, const double* __restrict__ nu, const do
   __shared__ double red[33 * 6];
   double v[6] = {0, 0, 0, 0, 0, 0};
   const bool fin = isfinite(lam);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     double a = alpha[i], m = mu[i];
     double t = a / eps + (double)w2[i] * DD_LN2;  // log(P_X/mu)
     double g = fin ? -a / lam : 0.0;              // log(e^{-alpha/lam})
@@ -187,8 +187,50 @@ k_sk_eval(const double* __restrict__ mu, const double* __restrict__ nu, const do
     v[4] += m;
     v[5] += nu[i];
   }
-  block_sum<6>(v, red);
-  if (threadIdx.x == 0) for (int k = 0; k < 6; ++k) out[k] = v[k];
+  block_sum_to<6>(v, red, out);
+}
+
+// k_sk_eval over the grid; partials: kRedBlocks * 6 doubles (NULL: one block).
+template <typename R>
+void sk_eval(const double* mu, const double* nu, const double* alpha, const double* beta, const R* w2,
+             const R* z2, double eps, double lam, int n, double* d_eval, double* partials, cudaStream_t st) {
+  const int G = red_blocks(n, 512, partials);
+  if (G == 1) {
+    k_sk_eval<R><<<1, 512, 0, st>>>(mu, nu, alpha, beta, w2, z2, eps, lam, n, d_eval);
+  } else {
+    k_sk_eval<R><<<G, 512, 0, st>>>(mu, nu, alpha, beta, w2, z2, eps, lam, n, partials);
+    k_sum_partials<<<1, 32, 0, st>>>(partials, G, 6, d_eval);
+  }
+}
+
+// Translation step (optional, not in the paper): after an X-half,
+// alpha += (lam/2) log(<e^{-alpha/lam}, mu> / <e^{-beta/lam}, nu>), the maximiser
+// of the dual of Eq. dual-problem along (alpha + t, beta - t).
+__global__ void __launch_bounds__(512) k_ti_sums(const double* __restrict__ mu, const double* __restrict__ nu,
+                                                 const double* __restrict__ alpha, const double* __restrict__ beta,
+                                                 double lam, int n, double* out) {
+  __shared__ double red[33 * 2];
+  double v[2] = {0.0, 0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    v[0] += mu[i] * exp(-alpha[i] / lam);
+    v[1] += nu[i] * exp(-beta[i] / lam);
+  }
+  block_sum_to<2>(v, red, out);
+}
+
+__global__ void k_ti_apply(double* __restrict__ alpha, const double* __restrict__ sums, double lam, int n) {
+  const double t = 0.5 * lam * log(sums[0] / sums[1]);
+  if (!(t == t) || isinf(t)) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) alpha[i] += t;
+}
+
+// sums: 2 doubles of device scratch; partials: kRedBlocks * 2 doubles.
+void ti_step(const double* mu, const double* nu, double* alpha, const double* beta, double lam, int n,
+             double* sums, double* partials, cudaStream_t st) {
+  const int G = red_blocks(n, 512, partials);
+  k_ti_sums<<<G, 512, 0, st>>>(mu, nu, alpha, beta, lam, n, partials);
+  k_sum_partials<<<1, 32, 0, st>>>(partials, G, 2, sums);
+  k_ti_apply<<<(n + 255) / 256, 256, 0, st>>>(alpha, sums, lam, n);
 }
 
 template <typename R>
@@ -245,12 +287,16 @@ static int full_sinkhorn_impl(const double* mu, const double* nu, const double* 
                               double* d_eval, cudaStream_t st, cudaError_t* cerr) {
   const int n = N * N;
   const double h = 1.0 / N;
+  const bool ti = (variant & DOMDEC_SINKHORN_TI) && std::isfinite(lam);
+  variant &= ~DOMDEC_SINKHORN_TI;
   Work<R> w;
-  *cerr = cudaMallocAsync(&w.in2, sizeof(R) * 4 * (size_t)n + sizeof(float) * 2 * (size_t)n, st);
+  const size_t wbytes = (sizeof(R) * 4 * (size_t)n + sizeof(float) * 2 * (size_t)n + 255) & ~size_t(255);
+  *cerr = cudaMallocAsync(&w.in2, wbytes + sizeof(double) * 6 * kRedBlocks, st);
   if (*cerr != cudaSuccess) return -1;
   w.tmp = w.in2 + n; w.w2 = w.tmp + n; w.z2 = w.w2 + n;
   w.in2f = reinterpret_cast<float*>(w.z2 + n);
   w.tmpf = w.in2f + n;
+  double* partials = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(w.in2) + wbytes);
   const int grid = (n + 255) / 256;
   double evalh[6];
   long long total = 0;
@@ -270,6 +316,7 @@ static int full_sinkhorn_impl(const double* mu, const double* nu, const double* 
     int shift_ok = 0;
     while (it < maxit) {
       k_half<R><<<grid, 256, 0, st>>>(w.w2, kap, alpha, n);
+      if (ti) ti_step(mu, nu, alpha, beta, lam, n, d_eval + 6, partials, st);
       k_to_log2<R><<<grid, 256, 0, st>>>(alpha, logmu, 1.0 / e, w.in2, n, w.in2f);
       lse_all<R>(w.in2, w.tmp, w.z2, N, q, variant, shift_ok, st, w.in2f, w.tmpf);
       k_half<R><<<grid, 256, 0, st>>>(w.z2, kap, beta, n);
@@ -278,7 +325,7 @@ static int full_sinkhorn_impl(const double* mu, const double* nu, const double* 
       shift_ok = 1;
       ++it;
       if (it % check_every == 0 || it == maxit) {
-        k_sk_eval<R><<<1, 512, 0, st>>>(mu, nu, alpha, beta, w.w2, nullptr, e, lam, n, d_eval);
+        sk_eval<R>(mu, nu, alpha, beta, w.w2, nullptr, e, lam, n, d_eval, partials, st);
         cudaMemcpyAsync(evalh, d_eval, 6 * sizeof(double), cudaMemcpyDeviceToHost, st);
         *cerr = cudaStreamSynchronize(st);
         if (*cerr != cudaSuccess) { cudaFreeAsync(w.in2, st); return -1; }
@@ -296,7 +343,7 @@ static int full_sinkhorn_impl(const double* mu, const double* nu, const double* 
   // primal / dual at the final eps (z from the last Y-half of the final iterate)
   const double kap = std::isfinite(lam) ? eps / (1.0 + eps / lam) : eps;
   (void)kap;
-  k_sk_eval<R><<<1, 512, 0, st>>>(mu, nu, alpha, beta, w.w2, w.z2, eps, lam, n, d_eval);
+  sk_eval<R>(mu, nu, alpha, beta, w.w2, w.z2, eps, lam, n, d_eval, partials, st);
   cudaMemcpyAsync(evalh, d_eval, 6 * sizeof(double), cudaMemcpyDeviceToHost, st);
   *cerr = cudaStreamSynchronize(st);
   cudaFreeAsync(w.in2, st);

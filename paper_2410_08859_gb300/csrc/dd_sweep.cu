@@ -481,20 +481,27 @@ k_init_duals(DevState S, const double* __restrict__ alpha0, const double* __rest
 __global__ void __launch_bounds__(512) k_score(DevState S, double* out) {
   __shared__ double red[33 * 5];
   const int n = S.N * S.N;
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x, dt = gridDim.x * blockDim.x;
   double v[5] = {0, 0, 0, 0, 0};
-  for (int y = threadIdx.x; y < n; y += blockDim.x) {
-    v[1] += dd_kl_term(S.PX[y], S.mu[y]);
-    v[2] += dd_kl_term(S.PY[y], S.nu[y]);
+  for (int y = t0; y < n; y += dt) {
+    v[1] += S.lam * dd_kl_term(S.PX[y], S.mu[y]);
+    v[2] += S.lam * dd_kl_term(S.PY[y], S.nu[y]);
     v[3] += S.PY[y];
   }
-  for (int i = threadIdx.x; i < S.nbasic; i += blockDim.x) {
+  for (int i = t0; i < S.nbasic; i += dt) {
     v[0] += S.Cc[i] + S.eps * S.Hh[i];
     v[4] += (double)S.box[i].H * S.box[i].W;
   }
-  block_sum<5>(v, red);
-  if (threadIdx.x == 0) {
-    out[0] = v[0]; out[1] = S.lam * v[1]; out[2] = S.lam * v[2]; out[3] = v[3]; out[4] = v[4];
-  }
+  block_sum_to<5>(v, red, out);
+}
+
+// out[k] = sum over g of partials[g * K + k], g in order.
+__global__ void k_sum_partials(const double* partials, int G, int K, double* out) {
+  const int k = threadIdx.x;
+  if (k >= K) return;
+  double a = 0.0;
+  for (int g = 0; g < G; ++g) a += partials[g * K + k];
+  out[k] = a;
 }
 
 // Dual value and marginal errors of the certificate.
@@ -507,7 +514,7 @@ k_cert(DevState S, const double* z, double* beta_out, double* out) {
   const int n = S.N * S.N;
   const double eps = S.eps, lam = S.lam, kap = eps / (1.0 + eps / lam);
   double v[7] = {0, 0, 0, 0, 0, 0, 0};
-  for (int y = threadIdx.x; y < n; y += blockDim.x) {
+  for (int y = blockIdx.x * blockDim.x + threadIdx.x; y < n; y += gridDim.x * blockDim.x) {
     double b = -kap * z[y];
     if (beta_out) beta_out[y] = b;
     double ea = exp(-S.alpha[y] / lam), eb = exp(-b / lam);
@@ -519,8 +526,7 @@ k_cert(DevState S, const double* z, double* beta_out, double* out) {
     v[5] += fabs(S.PX[y] - ea * S.mu[y]);
     v[6] += fabs(S.PY[y] - eb * S.nu[y]);
   }
-  block_sum<7>(v, red);
-  if (threadIdx.x == 0) for (int k = 0; k < 7; ++k) out[k] = v[k];
+  block_sum_to<7>(v, red, out);
 }
 
 // ======================================================= host launch wrappers
@@ -627,11 +633,25 @@ cudaError_t launch_regrow(const DevState& S, double* new0, double* new1, long lo
   k_reset_cur<<<(S.nbasic + 255) / 256, 256, 0, st>>>(S, newoff);
   return cudaGetLastError();
 }
-cudaError_t launch_score(const DevState& S, double* out, cudaStream_t st) {
-  k_score<<<1, 512, 0, st>>>(S, out);
+// partials: kRedBlocks * 8 doubles of scratch (NULL: one block)
+cudaError_t launch_score(const DevState& S, double* out, cudaStream_t st, double* partials) {
+  const int G = red_blocks((long long)S.N * S.N, 512, partials);
+  if (G == 1) {
+    k_score<<<1, 512, 0, st>>>(S, out);
+  } else {
+    k_score<<<G, 512, 0, st>>>(S, partials);
+    k_sum_partials<<<1, 32, 0, st>>>(partials, G, 5, out);
+  }
   return cudaGetLastError();
 }
-cudaError_t launch_cert(const DevState& S, const double* z, double* beta_out, double* out, cudaStream_t st) {
-  k_cert<<<1, 512, 0, st>>>(S, z, beta_out, out);
+cudaError_t launch_cert(const DevState& S, const double* z, double* beta_out, double* out, cudaStream_t st,
+                        double* partials) {
+  const int G = red_blocks((long long)S.N * S.N, 512, partials);
+  if (G == 1) {
+    k_cert<<<1, 512, 0, st>>>(S, z, beta_out, out);
+  } else {
+    k_cert<<<G, 512, 0, st>>>(S, z, beta_out, partials);
+    k_sum_partials<<<1, 32, 0, st>>>(partials, G, 7, out);
+  }
   return cudaGetLastError();
 }
