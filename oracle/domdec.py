@@ -315,9 +315,75 @@ def mixed_quantities(st, batch, probs, sols, theta):
     return Cc, Hh, PX, PY
 
 
+LINE_ITERS = 48      # cap on steps of the GetWeights_line root search
+LINE_GTOL = 1e-12    # stop when |E'| <= LINE_GTOL * (sum of the magnitudes of its terms)
+LINE_XTOL = 1e-12    # ... or when the bracket is this narrow
+LINE_PFLOOR = 1e-300  # floor of a mixed marginal inside the logarithm
+
+
+def line_search(st, batch, probs, sols, lo):
+    """GetWeights_line (Proposition 4.3, item 4): the zeta in [lo, 1] with the
+    largest decrement of the score of sum_J (1-zeta) pi_J + zeta pi~_J.
+
+    Reading (the paper does not say how the search is done): the score is the
+    tracked E_hat (R3).  Along zeta, C and H mix linearly and so do the
+    marginals, hence
+      E'(zeta)  = L + lam <dX, log(P_X(zeta)/mu)> + lam <dY, log(P_Y(zeta)/nu)>,
+      E''(zeta) = lam <dX^2, 1/P_X(zeta)> + lam <dY^2, 1/P_Y(zeta)> >= 0,
+    with L = sum_i (C~_i - C_i) + eps (H~_i - H_i) and dX, dY the marginal
+    changes at zeta = 1.  E_hat is convex in zeta, so the minimiser on [lo, 1]
+    is 1 if E'(1) <= 0, lo if E'(lo) >= 0, and otherwise the root of E' in the
+    bracket [lo, 1]: Newton steps from zeta = 1, replaced by the bracket's
+    midpoint when a step leaves the bracket or when the bracket has not halved
+    over the last two steps (a Newton step can be tiny far from the root where
+    a mixed marginal nearly vanishes); stop when |E'| <= LINE_GTOL times the sum
+    of the magnitudes of its terms, when the bracket is narrower than
+    LINE_XTOL, or after LINE_ITERS steps.  Returns the last point evaluated."""
+    Cg, Hg, PXg, PYg = mixed_quantities(st, batch, probs, sols, 1.0)
+    L = float(np.sum(Cg - st.Cc) + st.eps * np.sum(Hg - st.Hh))
+    dX = PXg - st.PX
+    dY = PYg - st.PY
+    mx, my = dX != 0.0, dY != 0.0
+    p0x, dx, mux = st.PX[mx], dX[mx], st.mu[mx]
+    p0y, dy, nuy = st.PY[my], dY[my], st.nu[my]
+
+    def derivs(z):
+        px = np.maximum(p0x + z * dx, LINE_PFLOOR)
+        py = np.maximum(p0y + z * dy, LINE_PFLOOR)
+        tx = dx * np.log(px / mux)
+        ty = dy * np.log(py / nuy)
+        g = L + st.lam * float(np.sum(tx)) + st.lam * float(np.sum(ty))
+        h = st.lam * float(np.sum(dx * dx / px)) + st.lam * float(np.sum(dy * dy / py))
+        scale = abs(L) + st.lam * float(np.sum(np.abs(tx))) + st.lam * float(np.sum(np.abs(ty)))
+        return g, h, scale
+
+    g, h, _ = derivs(1.0)
+    if g <= 0.0:
+        return 1.0
+    if derivs(lo)[0] >= 0.0:
+        return lo
+    a, b, z = lo, 1.0, 1.0
+    widths = [np.inf, np.inf]
+    for _ in range(LINE_ITERS):
+        zn = z - g / h if h > 0.0 else a
+        if not (a < zn < b) or (b - a) > 0.5 * widths[-2]:
+            zn = 0.5 * (a + b)
+        z = zn
+        g, h, scale = derivs(z)
+        if g > 0.0:
+            b = z
+        else:
+            a = z
+        widths.append(b - a)
+        if abs(g) <= LINE_GTOL * scale or b - a <= LINE_XTOL:
+            break
+    return z
+
+
 def get_weights(st, batch, probs, sols, strategy, tau):
     """GetWeights for a batch (Eq. GWFast, Proposition 4.3; swift per
-    sub-batch for ``staggered``).  Returns (theta, E_hat, E(1), E(safe))."""
+    sub-batch for ``staggered``; ``line`` = GetWeights_line).  Returns
+    (theta, E_hat, E(1), E(safe))."""
     nb = sum(p is not None for p in probs)
     th_safe = 1.0 / max(nb, 1)
     E0 = tracked_score(st)
@@ -327,6 +393,8 @@ def get_weights(st, batch, probs, sols, strategy, tau):
         return th_safe, E0, None, None
     Eg = tracked_score(st, *mixed_quantities(st, batch, probs, sols, 1.0))
     Es = tracked_score(st, *mixed_quantities(st, batch, probs, sols, th_safe))
+    if strategy == "line":
+        return line_search(st, batch, probs, sols, th_safe), E0, Eg, Es
     if Eg <= Es + 1e-12 * abs(E0) or (tau > 0 and Eg <= (1 + tau) * E0):
         return 1.0, E0, Eg, Es
     return th_safe, E0, Eg, Es
