@@ -360,6 +360,10 @@ def main():
     ap.add_argument("--lam", type=float, default=1.0)
     ap.add_argument("--workload", default="blobs256", choices=["blobs256", "batch64", "grad512"])
     ap.add_argument("--no-extras", action="store_true", help="skip time-to-gap, e2e and CPU baseline")
+    ap.add_argument("--cell-ctas", type=int, default=0, choices=[0, 1, 2],
+                    help="CTAs per cell of the timed sweeps (domdec_params.cell_ctas)")
+    ap.add_argument("--cell-ti", type=int, default=0, choices=[0, 1],
+                    help="translation step in the cell solves of the timed sweeps (domdec_params.cell_ti)")
     ap.add_argument("--quick-warm", action="store_true",
                     help="float-only, capped warm start (profiling runs; not a bench number)")
     args = ap.parse_args()
@@ -397,7 +401,7 @@ def main():
     a0, b0, t_warm, it_warm = warm_start(dd, mu_d, nu_d, N, eps, lam, torch, quick=args.quick_warm)
 
     g = dd.DomDec(mu_d, nu_d, eps, lam, s, alpha0=a0, beta0=b0, eps_init=2 * eps, precision="fp32",
-                  tau=0.0, err=2e-5, profile=1)
+                  tau=0.0, err=2e-5, profile=1, cell_ctas=args.cell_ctas, cell_ti=args.cell_ti)
     g.iterate(args.warmup)
     g.sync()
     g.kernel_times(reset=True)
@@ -508,6 +512,7 @@ def main():
             "config": {"workload": "blobs256", "N": N, "basic_cell": s, "eps": eps, "lam": lam,
                        "eps_scaling": "1 -> 2 eps by global Sinkhorn (warm start), DomDec at eps",
                        "strategy": "staggered", "tau": 0.0, "err": 2e-5, "precision": "fp32 cell / fp64 score",
+                       "cell_ctas": args.cell_ctas, "cell_ti": args.cell_ti,
                        "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches, "cell_iters_timed": int(iters_all),

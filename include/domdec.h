@@ -50,6 +50,9 @@ extern "C" {
 #define DOMDEC_SWIFT     1   /* swift on the whole partition (Proposition 4.3, item 2) */
 #define DOMDEC_SAFE      2   /* theta = 1/|J| (Proposition 4.3, item 1) */
 #define DOMDEC_GREEDY    3   /* theta = 1 (Eq. GWFast); may diverge */
+#define DOMDEC_LINE      4   /* GetWeights_line (Proposition 4.3): one zeta in [1/|b|, 1] for all cells of the
+                                partition minimising the tracked score (convex in zeta; safeguarded Newton on
+                                its derivative, at most 48 steps, on the device); not for batches */
 
 #define DOMDEC_FP32 0        /* cell Sinkhorn arithmetic in float (state, score, decision stay double) */
 #define DOMDEC_FP64 1        /* cell Sinkhorn arithmetic in double */
@@ -65,7 +68,7 @@ typedef struct {
                           err < 0 runs exactly maxit iterations per cell */
   double trunc_thr;    /* nu_i(y) < trunc_thr is dropped (Section 5.3; paper: 1e-15) */
   double tau;          /* greedy leniency: accept theta = 1 if E(1) <= (1 + tau) E (Section 5.3: 0.005); 0 = pure swift */
-  int    strategy;     /* DOMDEC_STAGGERED | SWIFT | SAFE | GREEDY */
+  int    strategy;     /* DOMDEC_STAGGERED | SWIFT | SAFE | GREEDY | LINE */
   int    maxit;        /* cap on cell Sinkhorn iterations (status MAXIT when hit) */
   int    newton_maxit; /* cap on Newton steps per y in the Y-half */
   int    precision;    /* DOMDEC_FP32 | DOMDEC_FP64 */
@@ -77,7 +80,8 @@ typedef struct {
   int    spill_slots;  /* cells whose Y-box exceeds max_ny run from global memory slots (per sub-batch): 0 = default
                           (up to 32 slots and 4 GiB), > 0 = that many, < 0 = none (such cells fail with DOMDEC_ETOOBIG) */
   int    cell_ctas;    /* CTAs per cell: 0 = a 2-CTA cluster when all cells of a sub-batch fit as resident
-                          clusters (else 1), 1 = always one CTA per cell */
+                          clusters (else 1), 1 = always one CTA per cell, 2 = always a 2-CTA cluster (cells
+                          beyond the resident clusters wait for a free pair of SMs) */
   int    cell_ti;      /* 1: after each X-half of a cell solve, shift alpha by the t maximising the cell
                           dual along (alpha + t, beta - t) (closed form; not in the paper: it removes the
                           slow total-mass mode of the alternation when eps << lam, same fixed point);

@@ -27,6 +27,8 @@ cudaError_t launch_decide_multi(const DevState* states, int ninst, int maxn, int
 cudaError_t launch_apply_multi(const DevState* states, const CellRef* refs, int nref, int part, cudaStream_t st);
 cudaError_t launch_compact_multi(const DevState* states, int ninst, int max_nbasic, cudaStream_t st);
 cudaError_t launch_decide(const DevState& S, const CellDesc* cells, int begin, int nbatch, cudaStream_t st);
+cudaError_t launch_line_search(const DevState& S, const CellDesc* cells, int begin, int nbatch, double* partials,
+                               cudaStream_t st);
 cudaError_t launch_apply(const DevState& S, const CellDesc* cells, int begin, int nbatch, cudaStream_t st);
 cudaError_t launch_compact(const DevState& S, long long* newoff, cudaStream_t st);
 cudaError_t launch_prepare_inputs(const double* mu, const double* nu, double* logmu, double* lognu, int n,
@@ -144,8 +146,9 @@ int check_params(const domdec_params* p, int N) {
   if (!(p->lambda > 0.0) || !std::isfinite(p->lambda)) return DOMDEC_EINVAL;
   if (p->basic_cell < 1 || p->basic_cell > 16 || N % (2 * p->basic_cell)) return DOMDEC_EINVAL;
   if (p->maxit < 1 || p->newton_maxit < 1) return DOMDEC_EINVAL;
-  if (p->strategy < 0 || p->strategy > 3 || (p->precision != 0 && p->precision != 1)) return DOMDEC_EINVAL;
+  if (p->strategy < 0 || p->strategy > 4 || (p->precision != 0 && p->precision != 1)) return DOMDEC_EINVAL;
   if (!(p->trunc_thr >= 0.0) || p->box_margin < 0) return DOMDEC_EINVAL;
+  if (p->cell_ctas < 0 || p->cell_ctas > 2 || p->cell_ti < 0 || p->cell_ti > 1) return DOMDEC_EINVAL;
   return DOMDEC_OK;
 }
 
@@ -243,12 +246,16 @@ int enqueue_sweep(domdec_s* h, int part, long long slot0) {
     if (nbt <= 0) continue;
     const int slot = (int)((slot0 + k++) % LOGCAP);
     cudaEvent_t ev = prof_begin(h);
-    const int csize = (h->p.cell_ctas != 1 && nbt <= h->max_pairs) ? 2 : 1;
+    const int csize = h->max_pairs > 0 && (h->p.cell_ctas == 2 || (h->p.cell_ctas == 0 && nbt <= h->max_pairs))
+                          ? 2 : 1;
     if (launch_cell_solve(h->S, h->d_cells[part], begin, nbt, prec, csize, h->st) != cudaSuccess)
       return DOMDEC_ECUDA;
     prof_end(h, ev, 0);
     ev = prof_begin(h);
     if (launch_decide(h->S, h->d_cells[part], begin, nbt, h->st) != cudaSuccess) return DOMDEC_ECUDA;
+    if (h->p.strategy == DOMDEC_LINE &&
+        launch_line_search(h->S, h->d_cells[part], begin, nbt, h->d_partials, h->st) != cudaSuccess)
+      return DOMDEC_ECUDA;
     prof_end(h, ev, 1);
     ev = prof_begin(h);
     if (launch_apply(h->S, h->d_cells[part], begin, nbt, h->st) != cudaSuccess) return DOMDEC_ECUDA;
@@ -397,7 +404,8 @@ int domdec_init(domdec_t* out, const double* mu, const double* nu, int N, const 
   DD_ALLOC(S.slotctr, 1);
   DD_ALLOC(S.status, 1); DD_ALLOC(S.red, 2 * 152 * 5 + 8); DD_ALLOC(S.red_count, 1);
   DD_ALLOC(h->d_newoff, h->nbasic + 1); DD_ALLOC(h->d_scratch, 64);
-  DD_ALLOC(h->d_partials, kRedBlocks * 8); DD_ALLOC(h->d_numom, 8);
+  DD_ALLOC(h->d_partials, kRedBlocks * 8);
+  DD_ALLOC(h->S.line, 16); DD_ALLOC(h->d_numom, 8);
   {
     // spill slots for cell boxes beyond the shared-memory capacity: Y-side arrays
     // (4 s N + 5 N^2 values) followed by 4 N^2 doubles of new marginals
@@ -851,7 +859,7 @@ int domdec_batch_create(domdec_batch_t* out, domdec_t* handles, int n) {
     if (!handles[i]) return DOMDEC_EINVAL;
     if (handles[i]->sticky) return DOMDEC_ESTATE;
     if (handles[i]->p.precision != handles[0]->p.precision || handles[i]->p.strategy != handles[0]->p.strategy ||
-        handles[i]->sweeps != handles[0]->sweeps)
+        handles[i]->sweeps != handles[0]->sweeps || handles[i]->p.strategy == DOMDEC_LINE)
       return DOMDEC_EINVAL;
   }
   domdec_batch_s* b = new (std::nothrow) domdec_batch_s();

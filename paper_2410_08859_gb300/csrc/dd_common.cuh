@@ -44,6 +44,7 @@ struct DevState {
   double h, eps, lam, thr, err, tau;
   int maxit, newton_maxit, strategy, margin;
   int ti;                       // translation step after each cell X-half (0/1)
+  double* line;                 // GetWeights_line state (16 doubles)
   int cap_ny, cap_side;
   unsigned char* spill;         // spill slots: Y-side arrays and new marginals of cells too large
   long long spill_stride;       //   for shared memory (bytes per slot)

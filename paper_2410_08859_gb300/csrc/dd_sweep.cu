@@ -81,7 +81,14 @@ __device__ __forceinline__ void decide_body(const DevState& S, const CellDesc* _
   const unsigned long long slot = (*S.slotctr)++ % DD_LOGCAP;
   double* lg = S.declog + 4 * slot;
   lg[0] = E0; lg[1] = Eg; lg[2] = Es; lg[3] = theta;
-  atomicAdd(S.counters + (theta == 1.0 ? 3 : 4), 1ull);
+  if (S.strategy == 4) {
+    // GetWeights_line: the search kernels refine theta (and the log record)
+    S.line[5] = 0.0;        // not done
+    S.line[6] = th_s;       // lower end of the bracket
+    S.line[7] = dL;         // linear part of E'(zeta)
+  } else {
+    atomicAdd(S.counters + (theta == 1.0 ? 3 : 4), 1ull);
+  }
   *S.red_count = 0u;
   if (S.spill_count) *S.spill_count = 0u;
 }
@@ -110,6 +117,92 @@ k_decide_multi(const DevState* __restrict__ states, int part, int sub) {
   if (nblk > (int)gridDim.x) nblk = gridDim.x;
   if ((int)blockIdx.x >= nblk) return;
   decide_body(sS, sS.cells[part], begin, end - begin, blockIdx.x, nblk);
+}
+
+// ====================================================== GetWeights_line (a6)
+// E_hat(zeta) of sum_J (1-zeta) pi_J + zeta pi~_J is convex in zeta: C and H
+// mix linearly, and so do the marginals inside the two KL terms.  With the
+// marginal changes dX = P_X pi~ - P_X pi on the batch's X boxes and dY = dP_Y:
+//   E'(zeta)  = L + lam <dX, log(P_X(zeta)/mu)> + lam <dY, log(P_Y(zeta)/nu)>
+//   E''(zeta) = lam <dX^2, 1/P_X(zeta)> + lam <dY^2, 1/P_Y(zeta)>
+// The minimiser on [lo, 1] (lo = 1/|b|) is 1 if E'(1) <= 0, lo if E'(lo) >= 0,
+// else the root of E': Newton steps from zeta = 1 inside the bracket, the
+// bracket's midpoint when a step leaves it or when the bracket has not halved
+// over the last two steps; stop when |E'| <= 1e-12 x (sum of the magnitudes
+// of its terms), when the bracket is narrower than 1e-12, or after 48 steps.
+// State S.line: [0] a, [1] b, [2] zeta to evaluate, [3] g, [4] h, [5] done,
+// [6] lo, [7] L, [8] width one step ago, [9] width two steps ago,
+// [12..15] the summed terms of the last evaluation.
+constexpr int kLineIters = 48;
+constexpr double kLineGtol = 1e-12, kLineXtol = 1e-12, kLinePfloor = 1e-300;
+
+// Block partials of [<d, log(p(z)/m)>, <d^2, 1/p(z)>, <|d log(p(z)/m)|>, <d, log(p(lo)/m)>]
+// at z = 1 (first == 1, also at lo) or at z = S.line[2].
+__global__ void __launch_bounds__(512)
+k_line_eval(DevState S, const CellDesc* __restrict__ cells, int begin, int nbatch, int first, double* partials) {
+  __shared__ double red[33 * 4];
+  if (S.line[5] != 0.0) return;   // uniform: every block reads the same flag
+  const double z = first ? 1.0 : S.line[2], lo = S.line[6];
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  auto term = [&](double p0, double d, double m) {
+    const double p = fmax(p0 + z * d, kLinePfloor);
+    const double t = d * log(p / m);
+    v[0] += t;
+    v[1] += d * d / p;
+    v[2] += fabs(t);
+    if (first) v[3] += d * log(fmax(p0 + lo * d, kLinePfloor) / m);
+  };
+  const int N = S.N;
+  for (int j = blockIdx.x; j < nbatch; j += gridDim.x) {
+    const CellOut& o = S.cout[j];
+    if (o.status == CELL_EMPTY || o.status == CELL_TOOBIG) continue;
+    const CellDesc cd = cells[begin + j];
+    const int nx = cd.nx1 * cd.nx2;
+    for (int t = threadIdx.x; t < nx; t += blockDim.x) {
+      const int r = t / cd.nx2, c = t - r * cd.nx2;
+      const int x = (cd.i0 + r) * N + cd.j0 + c;
+      const double p0 = S.PX[x], d = S.PXnew[x] - p0;
+      if (d != 0.0) term(p0, d, S.mu[x]);
+    }
+  }
+  const int n = N * N;
+  for (int y = blockIdx.x * blockDim.x + threadIdx.x; y < n; y += gridDim.x * blockDim.x) {
+    const double d = S.dPY[y];
+    if (d != 0.0) term(S.PY[y], d, S.nu[y]);
+  }
+  block_sum_to<4>(v, red, partials);
+}
+
+// One step of the search from the sums of the last evaluation (one thread).
+__global__ void k_line_step(DevState S, int first, int last) {
+  if (threadIdx.x != 0 || S.line[5] != 0.0) return;
+  double* L = S.line;
+  const double lam = S.lam;
+  const double g = L[7] + lam * L[12], h = lam * L[13], scale = fabs(L[7]) + lam * L[14];
+  double a = L[0], b = L[1], z = first ? 1.0 : L[2];
+  bool done = false;
+  double zeta = z;
+  if (first) {
+    if (g <= 0.0) { done = true; zeta = 1.0; }
+    else if (L[7] + lam * L[15] >= 0.0) { done = true; zeta = L[6]; }
+    else { a = L[6]; b = 1.0; L[8] = INFINITY; L[9] = INFINITY; }
+  } else {
+    if (g > 0.0) b = z; else a = z;
+    L[9] = L[8];
+    L[8] = b - a;
+    if (fabs(g) <= kLineGtol * scale || b - a <= kLineXtol || last) { done = true; zeta = z; }
+  }
+  if (!done) {
+    double zn = h > 0.0 ? z - g / h : a;
+    if (!(a < zn && zn < b) || (b - a) > 0.5 * L[9]) zn = 0.5 * (a + b);
+    L[0] = a; L[1] = b; L[2] = zn; L[3] = g; L[4] = h;
+    return;
+  }
+  L[5] = 1.0;
+  *S.theta = zeta;
+  const unsigned long long slot = (*S.slotctr + DD_LOGCAP - 1) % DD_LOGCAP;
+  S.declog[4 * slot + 3] = zeta;
+  atomicAdd(S.counters + (zeta == 1.0 ? 3 : 4), 1ull);
 }
 
 // ================================================================= apply (a7)
@@ -536,6 +629,20 @@ cudaError_t launch_decide(const DevState& S, const CellDesc* cells, int begin, i
   if (n < nblk * 512) nblk = (n + 511) / 512;
   if (nblk < 1) nblk = 1;
   k_decide<<<nblk, 512, 0, st>>>(S, cells, begin, nbatch);
+  return cudaGetLastError();
+}
+// The search of GetWeights_line after k_decide: one evaluation at 1 and lo,
+// then up to kLineIters evaluations (no-ops once the search has stopped).
+cudaError_t launch_line_search(const DevState& S, const CellDesc* cells, int begin, int nbatch, double* partials,
+                               cudaStream_t st) {
+  int G = (S.N * S.N + 511) / 512;
+  if (G < nbatch) G = nbatch;
+  if (G > kRedBlocks) G = kRedBlocks;
+  for (int k = 0; k <= kLineIters; ++k) {
+    k_line_eval<<<G, 512, 0, st>>>(S, cells, begin, nbatch, k == 0, partials);
+    k_sum_partials<<<1, 32, 0, st>>>(partials, G, 4, S.line + 12);
+    k_line_step<<<1, 32, 0, st>>>(S, k == 0, k == kLineIters);
+  }
   return cudaGetLastError();
 }
 cudaError_t launch_decide_multi(const DevState* states, int ninst, int maxn, int part, int sub, cudaStream_t st) {

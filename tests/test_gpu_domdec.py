@@ -85,7 +85,10 @@ def run_pair(dd, N, s, mu, nu, eps, lam, sweeps, precision, strategy="staggered"
         dec = g.decisions()
         assert len(dec) == nrec + len(log)
         for rec, d in zip(log, dec[nrec:]):
-            assert d[3] == rec["theta"], (k, d, rec)
+            if strategy == "line":   # a root found by a search: equal to rounding of the search
+                assert abs(d[3] - rec["theta"]) <= 1e-9, (k, d, rec)
+            else:
+                assert d[3] == rec["theta"], (k, d, rec)
         nrec += len(log)
         if precision == "fp64" or err < 0:
             st_iters = sum(sum(r["iters"]) for r in log)
@@ -117,6 +120,17 @@ def test_fp64_ragged_partition_and_odd_cell_size(dd):
 def test_fp64_other_strategies(dd, strategy):
     mu, nu = inputs.mixture_small(N=16, seed=1003)
     g, st = run_pair(dd, 16, 2, mu, nu, (1 / 16) ** 2, 2.0, 2, "fp64", strategy=strategy)
+    g.close()
+
+
+@pytest.mark.parametrize("lam", [1.0, 5.0])
+def test_fp64_line_search_matches_oracle(dd, lam):
+    """GetWeights_line (strategy 'line'): the device search returns the
+    oracle's zeta (to the search's rounding) and the states agree."""
+    mu, nu = inputs.mixture_small(N=16, seed=1011)
+    g, st = run_pair(dd, 16, 2, mu, nu, (1 / 16) ** 2, lam, 4, "fp64", strategy="line")
+    dec = g.decisions()
+    assert any(0.07 < d[3] < 1.0 for d in dec)   # an interior zeta (lo <= 1/16) was exercised
     g.close()
 
 
