@@ -37,6 +37,7 @@ UNIT = "cell-iters/s"
 N_SM = 152
 MUFU_PER_SM_CLK = 16      # ex2/lg2 results per SM per clock (4 per SM sub-partition)
 GAP_TARGET = 1e-5
+CELL_KERNEL_DRAM_BYTES = 4.029184e6
 
 
 def peaks():
@@ -454,7 +455,10 @@ def main():
     k1_s = kms[0] / 1000.0
     achieved = (terms / k1_s) / 1e12 if k1_s > 0 else 0.0
     roofline = {"bound": "alu", "kernel": "k_cell_solve<float>", "achieved": achieved, "peak": peak_mufu,
-                "unit": "Tex2/s", "frac": achieved / peak_mufu, "traffic": None,
+                "unit": "Tex2/s", "frac": achieved / peak_mufu,
+                # dram read + write bytes of one launch, from the ncu capture summarised in
+                # profiles/cell_solve_blobs256.md (set to None when the cell kernel changes)
+                "traffic": CELL_KERNEL_DRAM_BYTES,
                 "peak_source": f"{N_SM} SMs x {MUFU_PER_SM_CLK} MUFU/clk x {sm_mhz:.0f} MHz ({pk_kind} max clock)",
                 "kernel_share": float(kms[0] / max(kms.sum(), 1e-12)),
                 "kernel_ms": {"cell_solve": kms[0], "decide": kms[1], "apply": kms[2], "compact": kms[3]},
