@@ -272,11 +272,58 @@ def cell_problem(st, cell, margin=0):
     return dict(lo=lo, hi=hi, Y=Y, rho=rho)
 
 
-def solve_cell(st, cell, prob, err=2e-5, maxit=2000, ti=False):
+def balance_factors(st, X, Y, C, beta, pi, rows):
+    """Balancing step (Section 5.3, 'Balancing', Eq. balancing) for one cell.
+
+    One more X-half from the final beta gives alpha' and the X-marginal of
+    the next plan, mu_bar = e^{-alpha'/lam} mu_J (mu_J itself for lam = inf);
+    the targets are m_i = mu_bar(X_i) |nu_J| / mu_bar(X_J) with |nu_J| the
+    mass of the new cell plan.  The paper asks for a horizontal shift of mass
+    between the basic cells (y fixed) with |nu_i| = m_i and nu_J preserved,
+    without fixing the rule.  Reading: donors (|nu_i| > m_i) give the same
+    fraction of their marginal at every y; the donated field
+    D(y) = sum_d (|nu_d| - m_d) nu_d(y) / |nu_d| is shared at every y among the
+    receivers in proportion to their deficits, and a receiver's new mass at y
+    follows its own plan row (the new cell plan is positive on X_J x B_J).
+    So the balanced plan is pi_i(x, y) rho_i(y) with
+      rho_d = m_d / |nu_d|,   rho_r(y) = 1 + D(y) (m_r - |nu_r|) / (E nu_r(y)),
+    E = sum_d (|nu_d| - m_d); nu_J is preserved at every y and |nu_i| = m_i.
+    Returns {i: rho_i (n_y,)}; all ones when nothing is to move."""
+    eps, lam = st.eps, st.lam
+    logmu = np.log(st.mu[X])
+    if np.isinf(lam):
+        mubar = st.mu[X]
+    else:
+        a2 = uot.x_half(beta, C, st.nu[Y], eps, lam)
+        mubar = np.exp(logmu - a2 / lam)
+    nut = {i: pi[r].sum(0) for i, r in rows.items()}
+    mass = {i: float(v.sum()) for i, v in nut.items()}
+    mJ = sum(mass.values())
+    m = {i: float(mubar[r].sum()) * mJ / float(mubar.sum()) for i, r in rows.items()}
+    exc = {i: mass[i] - m[i] for i in rows}
+    E = sum(e for e in exc.values() if e > 0)
+    rho = {i: np.ones(len(Y)) for i in rows}
+    if not E > 0:
+        return rho
+    D = np.zeros(len(Y))
+    for i, e in exc.items():
+        if e > 0:
+            D += (e / mass[i]) * nut[i]
+            rho[i] = np.full(len(Y), m[i] / mass[i])
+    for i, e in exc.items():
+        if e < 0:
+            with np.errstate(divide="ignore", invalid="ignore"):
+                add = np.where(nut[i] > 0, D * (-e / E) / nut[i], 0.0)
+            rho[i] = 1.0 + add
+    return rho
+
+
+def solve_cell(st, cell, prob, err=2e-5, maxit=2000, ti=False, balance=False):
     """Solve the cell subproblem and return the new cell plan's data: final
     duals, P_X of the new plan on X_J, and per member basic cell its new
     Y-marginal on B_J, C_i and H_i (H_i via log(pi/(mu nu)) =
-    (alpha+beta-c)/eps for the diagonal scaling, Eq. diagonal-scaling)."""
+    (alpha+beta-c)/eps for the diagonal scaling, Eq. diagonal-scaling).
+    With ``balance`` the plan is first balanced (balance_factors)."""
     g = st.geo
     X, Y = cell["X"], prob["Y"]
     C = uot.sq_cost(g.pix[X], g.pix[Y], g.h)
@@ -285,15 +332,24 @@ def solve_cell(st, cell, prob, err=2e-5, maxit=2000, ti=False):
     pi = uot.plan(res.alpha, res.beta, C, st.mu[X], st.nu[Y], st.eps)
     logratio = (res.alpha[:, None] + res.beta[None, :] - C) / st.eps
     shape = tuple(prob["hi"] - prob["lo"])
-    nut, Ct, Ht = {}, {}, {}
     bop = g.basic_of_pixel[X]
+    rows = {i: bop == i for i in cell["members"]}
+    px = res.px
+    if balance:
+        rho = balance_factors(st, X, Y, C, res.beta, pi, rows)
+        for i, r in rows.items():
+            pi[r] = pi[r] * rho[i][None, :]
+            with np.errstate(divide="ignore"):
+                logratio[r] = logratio[r] + np.log(rho[i])[None, :]
+        px = pi.sum(1)
+    nut, Ct, Ht = {}, {}, {}
     nu_tot = st.nu.sum()
-    for i in cell["members"]:
-        r = bop == i
+    for i, r in rows.items():
         nut[i] = pi[r].sum(0).reshape(shape)
         Ct[i] = float(np.sum(C[r] * pi[r]))
-        Ht[i] = float(np.sum(pi[r] * logratio[r] - pi[r]) + st.mu[X][r].sum() * nu_tot)
-    return dict(alpha=res.alpha, beta=res.beta, px=res.px, nut=nut, Ct=Ct, Ht=Ht,
+        pr = pi[r]
+        Ht[i] = float(np.sum(np.where(pr > 0, pr * logratio[r], 0.0) - pr) + st.mu[X][r].sum() * nu_tot)
+    return dict(alpha=res.alpha, beta=res.beta, px=px, nut=nut, Ct=Ct, Ht=Ht,
                 iters=res.iters, converged=res.converged, gap=res.gap, pi=pi)
 
 
@@ -433,14 +489,15 @@ def batches_of(st, which, strategy):
     return [cells]
 
 
-def sweep(st, which, strategy="staggered", tau=0.0, err=2e-5, maxit=2000, margin=0, ti=False):
+def sweep(st, which, strategy="staggered", tau=0.0, err=2e-5, maxit=2000, margin=0, ti=False,
+          balance=False):
     """One parallel DomDec iteration over partition ``which`` (Algorithm 4;
     for ``staggered`` once per sub-batch, in sub-batch order).  Returns one
     log record per batch."""
     log = []
     for batch in batches_of(st, which, strategy):
         probs = [cell_problem(st, c, margin) for c in batch]
-        sols = [None if p is None else solve_cell(st, c, p, err, maxit, ti)
+        sols = [None if p is None else solve_cell(st, c, p, err, maxit, ti, balance)
                 for c, p in zip(batch, probs)]
         theta, E0, Eg, Es = get_weights(st, batch, probs, sols, strategy, tau)
         apply_step(st, batch, probs, sols, theta)
@@ -450,7 +507,7 @@ def sweep(st, which, strategy="staggered", tau=0.0, err=2e-5, maxit=2000, margin
     return log
 
 
-def sequential_sweep(st, which, err=2e-5, maxit=2000, margin=0, ti=False):
+def sequential_sweep(st, which, err=2e-5, maxit=2000, margin=0, ti=False, balance=False):
     """Sequential DomDec iteration (Algorithm 3): cells in partition order,
     each solved from the current state and accepted with theta = 1."""
     iters = []
@@ -458,23 +515,23 @@ def sequential_sweep(st, which, err=2e-5, maxit=2000, margin=0, ti=False):
         prob = cell_problem(st, cell, margin)
         if prob is None:
             continue
-        sol = solve_cell(st, cell, prob, err, maxit, ti)
+        sol = solve_cell(st, cell, prob, err, maxit, ti, balance)
         apply_step(st, [cell], [prob], [sol], 1.0)
         iters.append(sol["iters"])
     return iters
 
 
 def run(st, n_sweeps, strategy="staggered", tau=0.0, err=2e-5, maxit=2000,
-        margin=0, first=0, record=None, ti=False):
+        margin=0, first=0, record=None, ti=False, balance=False):
     """Alternate A and B sweeps (Algorithm 2): sweep k uses A for even
     first+k, B otherwise.  ``record(k, st, log)`` is called after each sweep."""
     logs = []
     for k in range(n_sweeps):
         which = "A" if (first + k) % 2 == 0 else "B"
         if strategy == "sequential":
-            lg = sequential_sweep(st, which, err, maxit, margin, ti)
+            lg = sequential_sweep(st, which, err, maxit, margin, ti, balance)
         else:
-            lg = sweep(st, which, strategy, tau, err, maxit, margin, ti)
+            lg = sweep(st, which, strategy, tau, err, maxit, margin, ti, balance)
         logs.append(lg)
         if record is not None:
             record(k, st, lg)
