@@ -150,7 +150,7 @@ def domdec_to_gap(dd, mu_d, nu_d, N, s, eps, lam, a0, b0, t_warm, torch, max_swe
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     g = dd.DomDec(mu_d, nu_d, eps, lam, s, alpha0=a0, beta0=b0, eps_init=2 * eps, precision="fp32",
-                  tau=0.0, err=1e-7, maxit=5000)
+                  tau=0.0, err=1e-7, maxit=5000, profile=1)
     sweeps, rel = 0, float("inf")
     while sweeps < max_sweeps:
         g.iterate(2)
@@ -162,8 +162,9 @@ def domdec_to_gap(dd, mu_d, nu_d, N, s, eps, lam, a0, b0, t_warm, torch, max_swe
     torch.cuda.synchronize()
     t = time.perf_counter() - t0
     st = g.stats()
+    kms, _ = g.kernel_times(reset=True)
     g.close()
-    return t + t_warm, t, rel, sweeps, st["cell_iters"]
+    return t + t_warm, t, rel, sweeps, st["cell_iters"], float(kms[0]), int(st["lse_terms"])
 
 
 def oracle_sample(max_seconds=20.0, sweeps=None, maxit=None):
@@ -365,6 +366,8 @@ def main():
                     help="CTAs per cell of the timed sweeps (domdec_params.cell_ctas)")
     ap.add_argument("--cell-ti", type=int, default=0, choices=[0, 1],
                     help="translation step in the cell solves of the timed sweeps (domdec_params.cell_ti)")
+    ap.add_argument("--balance", type=int, default=0, choices=[0, 1],
+                    help="balancing step after each cell solve of the timed sweeps (domdec_params.balance)")
     ap.add_argument("--quick-warm", action="store_true",
                     help="float-only, capped warm start (profiling runs; not a bench number)")
     args = ap.parse_args()
@@ -402,7 +405,8 @@ def main():
     a0, b0, t_warm, it_warm = warm_start(dd, mu_d, nu_d, N, eps, lam, torch, quick=args.quick_warm)
 
     g = dd.DomDec(mu_d, nu_d, eps, lam, s, alpha0=a0, beta0=b0, eps_init=2 * eps, precision="fp32",
-                  tau=0.0, err=2e-5, profile=1, cell_ctas=args.cell_ctas, cell_ti=args.cell_ti)
+                  tau=0.0, err=2e-5, profile=1, cell_ctas=args.cell_ctas, cell_ti=args.cell_ti,
+                  balance=args.balance)
     g.iterate(args.warmup)
     g.sync()
     g.kernel_times(reset=True)
@@ -470,7 +474,10 @@ def main():
     e2e = None
     if not args.no_extras:
         # time to the stated gap: DomDec (warm start + sweeps) vs global Sinkhorn on the same GPU
-        tt, t_dd, rel_dd, sw, its_dd = domdec_to_gap(dd, mu_d, nu_d, N, s, eps, lam, a0, b0, t_warm, torch)
+        tt, t_dd, rel_dd, sw, its_dd, cell_ms, terms_dd = domdec_to_gap(dd, mu_d, nu_d, N, s, eps, lam, a0, b0,
+                                                                         t_warm, torch)
+        t_ti, rel_ti, it_ti = sinkhorn_to_gap(dd, mu_d, nu_d, N, eps, lam,
+                                              dd.SINKHORN_SEPARABLE | dd.SINKHORN_TI, dd.FP64, torch)
         t_sep, rel_sep, it_sep = sinkhorn_to_gap(dd, mu_d, nu_d, N, eps, lam, dd.SINKHORN_SEPARABLE, dd.FP64,
                                                  torch)
         t_dense, rel_dense, it_dense = sinkhorn_to_gap(dd, mu_d, nu_d, N, eps, lam, dd.SINKHORN_DENSE, dd.FP32,
@@ -479,6 +486,13 @@ def main():
             "target_rel_gap": GAP_TARGET,
             "domdec_s": tt, "domdec_warm_start_s": t_warm, "domdec_sweeps_s": t_dd, "domdec_gap": rel_dd,
             "domdec_sweeps": sw, "domdec_cell_iters": its_dd, "warm_start_sinkhorn_iters": it_warm,
+            # the sweeps of this run are compute-heavy (many cells iterate to maxit): throughput and
+            # MUFU roofline of the cell kernel in that regime
+            "domdec_cell_kernel_ms": cell_ms,
+            "domdec_cell_iters_per_s": its_dd / max(cell_ms / 1e3, 1e-12),
+            "domdec_cell_kernel_mufu_frac": (terms_dd / max(cell_ms / 1e3, 1e-12)) / 1e12 / peak_mufu,
+            "sinkhorn_separable_fp64_translation_s": t_ti, "sinkhorn_separable_fp64_translation_gap": rel_ti,
+            "sinkhorn_separable_fp64_translation_iters": it_ti,
             "sinkhorn_separable_fp64_s": t_sep, "sinkhorn_separable_fp64_gap": rel_sep,
             "sinkhorn_separable_fp64_iters": it_sep,
             "sinkhorn_dense_fp32_s": t_dense, "sinkhorn_dense_fp32_gap": rel_dense,
@@ -516,7 +530,7 @@ def main():
             "config": {"workload": "blobs256", "N": N, "basic_cell": s, "eps": eps, "lam": lam,
                        "eps_scaling": "1 -> 2 eps by global Sinkhorn (warm start), DomDec at eps",
                        "strategy": "staggered", "tau": 0.0, "err": 2e-5, "precision": "fp32 cell / fp64 score",
-                       "cell_ctas": args.cell_ctas, "cell_ti": args.cell_ti,
+                       "cell_ctas": args.cell_ctas, "cell_ti": args.cell_ti, "balance": args.balance,
                        "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches, "cell_iters_timed": int(iters_all),

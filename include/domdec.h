@@ -86,6 +86,11 @@ typedef struct {
                           dual along (alpha + t, beta - t) (closed form; not in the paper: it removes the
                           slow total-mass mode of the alternation when eps << lam, same fixed point);
                           0 (default): the paper's plain alternation */
+  int    balance;      /* 1: balancing step after each cell solve (Section 5.3, Eq. balancing): targets
+                          m_i = mu_bar(X_i) |nu_J| / mu_bar(X_J) from one more X-half; donors scale their
+                          plan rows by m_i/|nu_i|, receivers share the donated mass at every y in
+                          proportion to their deficits (nu_J preserved); C_i, H_i, P_X follow the
+                          balanced plan.  Cells then run on one CTA each; not for batches.  0: off */
 } domdec_params;
 
 typedef struct {

@@ -149,6 +149,7 @@ int check_params(const domdec_params* p, int N) {
   if (p->strategy < 0 || p->strategy > 4 || (p->precision != 0 && p->precision != 1)) return DOMDEC_EINVAL;
   if (!(p->trunc_thr >= 0.0) || p->box_margin < 0) return DOMDEC_EINVAL;
   if (p->cell_ctas < 0 || p->cell_ctas > 2 || p->cell_ti < 0 || p->cell_ti > 1) return DOMDEC_EINVAL;
+  if (p->balance < 0 || p->balance > 1) return DOMDEC_EINVAL;
   return DOMDEC_OK;
 }
 
@@ -246,7 +247,8 @@ int enqueue_sweep(domdec_s* h, int part, long long slot0) {
     if (nbt <= 0) continue;
     const int slot = (int)((slot0 + k++) % LOGCAP);
     cudaEvent_t ev = prof_begin(h);
-    const int csize = h->max_pairs > 0 && (h->p.cell_ctas == 2 || (h->p.cell_ctas == 0 && nbt <= h->max_pairs))
+    const int csize = h->max_pairs > 0 && !h->p.balance &&
+                              (h->p.cell_ctas == 2 || (h->p.cell_ctas == 0 && nbt <= h->max_pairs))
                           ? 2 : 1;
     if (launch_cell_solve(h->S, h->d_cells[part], begin, nbt, prec, csize, h->st) != cudaSuccess)
       return DOMDEC_ECUDA;
@@ -346,6 +348,7 @@ int domdec_init(domdec_t* out, const double* mu, const double* nu, int N, const 
   S.N = N; S.s = h->s; S.nb = h->nb; S.nbasic = h->nbasic;
   S.h = 1.0 / N; S.eps = pin->eps; S.lam = pin->lambda; S.thr = pin->trunc_thr; S.err = pin->err;
   S.ti = pin->cell_ti ? 1 : 0;
+  S.balance = pin->balance ? 1 : 0;
   S.tau = pin->tau; S.maxit = pin->maxit; S.newton_maxit = pin->newton_maxit; S.strategy = pin->strategy;
   S.margin = pin->box_margin;
   // shared-memory capacity of the cell kernel
@@ -859,7 +862,8 @@ int domdec_batch_create(domdec_batch_t* out, domdec_t* handles, int n) {
     if (!handles[i]) return DOMDEC_EINVAL;
     if (handles[i]->sticky) return DOMDEC_ESTATE;
     if (handles[i]->p.precision != handles[0]->p.precision || handles[i]->p.strategy != handles[0]->p.strategy ||
-        handles[i]->sweeps != handles[0]->sweeps || handles[i]->p.strategy == DOMDEC_LINE)
+        handles[i]->sweeps != handles[0]->sweeps || handles[i]->p.strategy == DOMDEC_LINE ||
+        handles[i]->p.balance)
       return DOMDEC_EINVAL;
   }
   domdec_batch_s* b = new (std::nothrow) domdec_batch_s();

@@ -192,6 +192,11 @@ __device__ __forceinline__ void newton_u2(const R (&lr)[2], const R (&c0)[2], co
   }
 }
 
+// v[k] for a run-time k in 0..3 without indexing a local array (keeps it in registers).
+__device__ __forceinline__ double pick4(const double (&v)[4], int k) {
+  return k == 0 ? v[0] : (k == 1 ? v[1] : (k == 2 ? v[2] : v[3]));
+}
+
 __device__ __forceinline__ double box_value(const BoxRec& b, const double* arena, int y1, int y2) {
   int a = y1 - b.k0, c = y2 - b.l0;
   if (a < 0 || c < 0 || a >= b.H || c >= b.W) return 0.0;
@@ -584,16 +589,27 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
   const bool nonfinite = !(gap == gap);
 
   // ------------------------------------------------------- epilogue (a5)
-  // alpha, P_X of the new plan and the KL_X change: first CTA only.
+  // alpha, P_X of the new plan and the KL_X change: first CTA only.  With
+  // balancing (one CTA per cell) P_X and the KL_X change follow the balancing.
+  const bool bal = S.balance && csize == 1;
+  const double th_s = 1.0 / nbatch;
   double dk[2] = {0.0, 0.0};
+  double mubar[4] = {0.0, 0.0, 0.0, 0.0};   // balancing: mu_bar(X_q), X-marginal after one more X-half
   if (crank == 0) {
-    const double th_s = 1.0 / nbatch;
     for (int t = tid; t < nx; t += nthr) {
       int r = t / nx2, c = t - r * nx2;
       int x = (cd.i0 + r) * N + cd.j0 + c;
       int xi1 = cd.i0 + r - xc1, xi2 = cd.j0 + c - xc2;
       double a = (double)av_c[t];
       S.alpha[x] = eps * (A + a + 2.0 * q * (double)(D1 * xi1 + D2 * xi2));
+      if (bal) {
+        // av_n holds the X-half of the final beta (computed before the loop stopped)
+        const int qd = 2 * (r >= s) + (c >= s);
+        const double mb = exp(((double)lm[t] + (double)gA + (double)g0[t] - sl * (double)av_n[t]));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) mubar[k] += k == qd ? mb : 0.0;   // static indices (no local memory)
+        continue;
+      }
       double p1 = (double)dd_ex2((lm[t] + av_c[t]) * L2E + Wv[t]);
       S.PXnew[x] = p1;
       double p0 = S.PX[x], m = S.mu[x];
@@ -602,7 +618,8 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
       dk[0] += dd_kl_term(p1, m) - k0v;
       dk[1] += dd_kl_term(ps, m) - k0v;
     }
-    block_sum<2>(dk, red);
+    if (bal) block_sum<4>(mubar, red);
+    else block_sum<2>(dk, red);
   }
 
   R hs[12];
@@ -673,6 +690,150 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
     }
     __threadfence();
     csync();
+  }
+  if (bal) {
+    // ---- balancing (Section 5.3, Eq. balancing): targets m_q = mu_bar(X_q) |nu_J| / mu_bar(X_J);
+    // donors scale their rows by m_q/|nu_q|, receivers by 1 + D(y) w_q / nu_q(y) with the donated
+    // field D(y) = sum_d (|nu_d| - m_d) nu_d(y)/|nu_d| and w_q = deficit_q / total excess.
+    double ms[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) ms[k] = (double)hs[8 + k];
+    block_sum<4>(ms, red);
+    double mJ = 0.0, mbJ = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) { mJ += ms[k]; mbJ += mubar[k]; }
+    double fd[4], rd[4], wr[4];   // donor factor, donor weight in D, receiver share
+    double Ex = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const double mk = mbJ > 0.0 ? mubar[k] * mJ / mbJ : 0.0;
+      const double e = ms[k] - mk;
+      fd[k] = 1.0; rd[k] = 0.0; wr[k] = 0.0;
+      if (e > 0.0 && ms[k] > 0.0) { fd[k] = mk / ms[k]; rd[k] = e / ms[k]; Ex += e; }
+      else if (e < 0.0) wr[k] = -e;
+    }
+    const bool move = Ex > 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) wr[k] = move ? wr[k] / Ex : 0.0;
+    // rho_q(u) from the unbalanced marginals in nut
+    auto rho_at = [&](int u, double (&rho)[4]) {
+      double nv[4], D = 0.0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int hr = k >> 1, hc = k & 1;
+        nv[k] = (hr < nhr && hc < nhc) ? nut[k * nst + u] : 0.0;
+        D += rd[k] * nv[k];
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        rho[k] = fd[k];
+        if (wr[k] > 0.0 && nv[k] > 0.0) rho[k] = 1.0 + D * wr[k] / nv[k];
+      }
+    };
+    // pass B: C and H of the balanced plan from the same per-y sums, weighted by rho
+    if (move) {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) hs[k] = R(0);
+      for (int hc = 0; hc < nhc; ++hc) {
+        const int cb = hc * s, ce = min(nx2, cb + s);
+        for (int t = tid; t < nx1 * W; t += nthr) {
+          int r = t / W, ll = t - r * W;
+          const R* row = xa_c + r * nx2;
+          R ctr = R(ll + offc);
+          R T2 = lse2_1d<R>([&](int m) { return row[cb + m]; }, ce - cb, ctr - R(cb), q2, R(0), false);
+          R sw = 0, sa = 0, sd = 0;
+          for (int c = cb; c < ce; ++c) {
+            R d = R(c) - ctr;
+            R w = dd_ex2(row[c] - q2 * d * d - T2);
+            sw += w;
+            sa += w * (av_c[r * nx2 + c] - qR * d * d);
+            R dt = d + R(D2);
+            sd += w * dt * dt;
+          }
+          R isw = R(1) / sw;
+          Te[t] = T2;
+          Ma[t] = sa * isw;
+          Md[t] = sd * isw;
+        }
+        __syncthreads();
+        for (int u = tid; u < ny; u += nthr) {
+          int kk = u / W, ll = u - kk * W;
+          R ctr = R(kk + offr);
+          double rho[4];
+          rho_at(u, rho);
+          for (int hr = 0; hr < nhr; ++hr) {
+            const int rb = hr * s, re = min(nx1, rb + s);
+            R P2 = lse2_1d<R>([&](int m) { return Te[(rb + m) * W + ll]; }, re - rb, ctr - R(rb), q2, R(0), false);
+            R sw = 0, sa = 0, sd = 0;
+            for (int r = rb; r < re; ++r) {
+              R d = R(r) - ctr;
+              R w = dd_ex2(Te[r * W + ll] - q2 * d * d - P2);
+              sw += w;
+              sa += w * (Ma[r * W + ll] - qR * d * d);
+              R dt = d + R(D1);
+              sd += w * (dt * dt + Md[r * W + ll]);
+            }
+            R isw = R(1) / sw;
+            const int qd = 2 * hr + hc;
+            const double nt = nut[qd * nst + u];
+            const double rh = pick4(rho, qd);
+            const double nh = rh * nt;
+            hs[qd] += R(nh * ((double)(sa * isw) + (double)bv[u] + (rh > 0.0 ? log(rh) : 0.0)));
+            hs[4 + qd] += R(nh * (double)(sd * isw));
+            hs[8 + qd] += R(nh);
+          }
+        }
+        __syncthreads();
+      }
+    }   // nothing moves: the sums of pass A stand
+    // P_X of the balanced plan: per quadrant, one more X-pass with log2 rho_q added to b + log nu
+    R* Lq = bl;
+    for (int qd = 0; qd < 4; ++qd) {
+      const int hr = qd >> 1, hc = qd & 1;
+      if (hr >= nhr || hc >= nhc) continue;
+      const int cb = hc * s, ce = min(nx2, cb + s), rb = hr * s, re = min(nx1, rb + s);
+      for (int u = tid; u < ny; u += nthr) {
+        double rho[4];
+        rho_at(u, rho);
+        const double rq = pick4(rho, qd);
+        const double lr = rq > 0.0 ? log2(rq) : -INFINITY;
+        Lq[u] = R(((double)bv[u] + (double)lnu[u]) * DD_LOG2E + lr);
+      }
+      __syncthreads();
+      for (int t = tid; t < H * (ce - cb); t += nthr) {
+        const int kk = t / (ce - cb), c = cb + (t - kk * (ce - cb));
+        U[kk * nx2 + c] = lse2_1d<R>([&](int m) { return Lq[kk * W + m]; }, W, R(c - offc), q2, R(0), false);
+      }
+      __syncthreads();
+      for (int t = tid; t < (re - rb) * (ce - cb); t += nthr) {
+        const int r = rb + t / (ce - cb), c = cb + (t - (t / (ce - cb)) * (ce - cb));
+        const int tx = r * nx2 + c;
+        R W2 = lse2_1d<R>([&](int m) { return U[m * nx2 + c]; }, H, R(r - offr), q2, R(0), false);
+        const int x = (cd.i0 + r) * N + cd.j0 + c;
+        double p1 = (double)dd_ex2((lm[tx] + av_c[tx]) * L2E + W2);
+        if (!move) p1 = (double)dd_ex2((lm[tx] + av_c[tx]) * L2E + Wv[tx]);
+        S.PXnew[x] = p1;
+        double p0 = S.PX[x], m = S.mu[x];
+        double ps = (1.0 - th_s) * p0 + th_s * p1;
+        double k0v = dd_kl_term(p0, m);
+        dk[0] += dd_kl_term(p1, m) - k0v;
+        dk[1] += dd_kl_term(ps, m) - k0v;
+      }
+      __syncthreads();
+    }
+    block_sum<2>(dk, red);
+    // the balanced marginals
+    if (move) {
+      for (int u = tid; u < ny; u += nthr) {
+        double rho[4];
+        rho_at(u, rho);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if ((k >> 1) < nhr && (k & 1) < nhc) nut[k * nst + u] *= rho[k];
+      }
+    }
+    __threadfence();
+    __syncthreads();
   }
   // change of P_Y pi for the step-size decision
   for (int u = gtid; u < ny; u += gthr) {

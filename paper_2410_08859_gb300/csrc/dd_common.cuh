@@ -45,6 +45,7 @@ struct DevState {
   int maxit, newton_maxit, strategy, margin;
   int ti;                       // translation step after each cell X-half (0/1)
   double* line;                 // GetWeights_line state (16 doubles)
+  int balance;                  // balancing step after each cell solve (0/1; one CTA per cell)
   int cap_ny, cap_side;
   unsigned char* spill;         // spill slots: Y-side arrays and new marginals of cells too large
   long long spill_stride;       //   for shared memory (bytes per slot)

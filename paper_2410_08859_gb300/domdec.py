@@ -38,7 +38,7 @@ class domdec_params(ctypes.Structure):
                 ("box_margin", ctypes.c_int), ("max_ny", ctypes.c_int),
                 ("arena_factor", ctypes.c_double), ("eps_init", ctypes.c_double),
                 ("profile", ctypes.c_int), ("spill_slots", ctypes.c_int),
-                ("cell_ctas", ctypes.c_int), ("cell_ti", ctypes.c_int)]
+                ("cell_ctas", ctypes.c_int), ("cell_ti", ctypes.c_int), ("balance", ctypes.c_int)]
 
 
 class domdec_stats(ctypes.Structure):

@@ -60,11 +60,11 @@ def compare_state(g, st, tol_score, tol_l1, tol_alpha, check_boxes=True, tol_box
 
 def run_pair(dd, N, s, mu, nu, eps, lam, sweeps, precision, strategy="staggered", err=2e-5, maxit=2000,
              tau=0.0, thr=1e-15, tols=(1e-10, 1e-10, 1e-8), tol_box=1e-8, init_duals=None, cell_ctas=0,
-             ti=0):
+             ti=0, balance=0):
     geo = odd.Geometry(N, s)
     mu, nu = mu.ravel(), nu.ravel()
     kw = dict(precision=precision, strategy=strategy, err=err, maxit=maxit, tau=tau, trunc_thr=thr,
-              cell_ctas=cell_ctas, cell_ti=ti)
+              cell_ctas=cell_ctas, cell_ti=ti, balance=balance)
     if init_duals is None:
         st = odd.init_product(geo, mu, nu, eps, lam, thr)
         g = dd.DomDec(mu, nu, eps, lam, s, **kw)
@@ -78,7 +78,7 @@ def run_pair(dd, N, s, mu, nu, eps, lam, sweeps, precision, strategy="staggered"
         which = "AB"[k % 2]
         if strategy == "sequential":
             raise ValueError
-        log = odd.sweep(st, which, strategy, tau=tau, err=err, maxit=maxit, ti=bool(ti))
+        log = odd.sweep(st, which, strategy, tau=tau, err=err, maxit=maxit, ti=bool(ti), balance=bool(balance))
         g.iterate(1)
         rc = g.sync()
         assert rc in (0, 1)
@@ -131,6 +131,37 @@ def test_fp64_line_search_matches_oracle(dd, lam):
     g, st = run_pair(dd, 16, 2, mu, nu, (1 / 16) ** 2, lam, 4, "fp64", strategy="line")
     dec = g.decisions()
     assert any(0.07 < d[3] < 1.0 for d in dec)   # an interior zeta (lo <= 1/16) was exercised
+    g.close()
+
+
+@pytest.mark.parametrize("N,s,lam", [(16, 2, 1.0), (16, 2, 5.0), (24, 3, 1.0)])
+def test_fp64_balancing_matches_oracle(dd, N, s, lam):
+    """Balancing step (Eq. balancing) after every cell solve: FP64 sweeps match
+    the oracle's balanced sweeps (decisions, iteration counts, boxes, state),
+    including border cells of the B partition with 1 or 2 basic cells."""
+    mu, nu = inputs.mixture_small(N=N, seed=1012)
+    g, st = run_pair(dd, N, s, mu, nu, (1 / N) ** 2, lam, 3, "fp64", balance=1)
+    g.close()
+
+
+def test_fp32_balancing_converges_to_oracle_optimum(dd):
+    N, s = 32, 4
+    mu, nu = inputs.mixture_small(N=N, seed=1006)
+    mu, nu = mu.ravel(), nu.ravel()
+    geo = odd.Geometry(N, s)
+    eps, lam = (1 / N) ** 2, 1.0
+    C = odd.full_cost(geo)
+    a, b, it, gap = uot.full_sinkhorn(mu, nu, C, eps, lam, err=1e-12, maxit=20000)
+    pi = uot.plan(a, b, C, mu, nu, eps)
+    Eopt = uot.primal_score(pi, C, mu, nu, eps, lam)
+    g = dd.DomDec(mu, nu, eps, lam, s, precision="fp32", err=1e-12, maxit=2000, tau=0.0, balance=1)
+    g.iterate(30)
+    g.sync()
+    E = g.score()[0]
+    PX, PY = g.marginals()
+    assert abs(E - Eopt) <= 1e-6 * Eopt, (E, Eopt)
+    assert np.abs(PX - pi.sum(1)).sum() / mu.sum() <= 1e-5
+    assert np.abs(PY - pi.sum(0)).sum() / mu.sum() <= 1e-5
     g.close()
 
 
