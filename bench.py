@@ -143,14 +143,15 @@ def sinkhorn_to_gap(dd, mu_d, nu_d, N, eps, lam, variant, precision, torch, max_
     return time.perf_counter() - t0, rel, tot
 
 
-def domdec_to_gap(dd, mu_d, nu_d, N, s, eps, lam, a0, b0, t_warm, torch, max_sweeps=40):
+def domdec_to_gap(dd, mu_d, nu_d, N, s, eps, lam, a0, b0, t_warm, torch, max_sweeps=60):
     """DomDec from the warm start until the certificate's relative gap reaches
     GAP_TARGET; cell tolerance 1e-7 (the paper's 2e-5 stalls near 1.5e-4 on this
-    workload because inexact cell solves make greedy steps lose to the safe step)."""
+    workload because inexact cell solves make greedy steps lose to the safe step),
+    at most 1000 iterations per cell solve, every cell on a 2-CTA cluster."""
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     g = dd.DomDec(mu_d, nu_d, eps, lam, s, alpha0=a0, beta0=b0, eps_init=2 * eps, precision="fp32",
-                  tau=0.0, err=1e-7, maxit=5000, profile=1)
+                  tau=0.0, err=1e-7, maxit=1000, cell_ctas=2, profile=1)
     sweeps, rel = 0, float("inf")
     while sweeps < max_sweeps:
         g.iterate(2)

@@ -29,7 +29,7 @@ def grid_positions(N, device=None, dtype=torch.float64):
     return torch.stack(torch.meshgrid(t, t, indexing="ij"), -1).reshape(N * N, 2)
 
 
-def solve(mu, nu, eps, lam, s=8, gap=1e-6, max_sweeps=200, precision="fp32", cell_err=1e-7,
+def solve(mu, nu, eps, lam, s=8, gap=1e-6, max_sweeps=200, precision="fp32", cell_err=1e-7, cell_maxit=1000,
           eps_start=1.0, warm_err=5e-6, warm_maxit=4000, alpha0=None, beta0=None, eps0=None, stream=None):
     """DomDec solve to a relative PD gap.  mu, nu: contiguous float64 CUDA
     tensors with N*N entries.  alpha0/beta0 (with their eps0) replace the
@@ -45,7 +45,7 @@ def solve(mu, nu, eps, lam, s=8, gap=1e-6, max_sweeps=200, precision="fp32", cel
                                 alpha=alpha0, beta=beta0, stream=stream)
         eps0 = 2 * eps
     g = dd.DomDec(mu, nu, eps, lam, s, alpha0=alpha0, beta0=beta0, eps_init=eps if eps0 is None else eps0,
-                  precision=precision, tau=0.0, err=cell_err, maxit=5000, stream=stream)
+                  precision=precision, tau=0.0, err=cell_err, maxit=cell_maxit, cell_ctas=2, stream=stream)
     sweeps, rel = 0, float("inf")
     try:
         while sweeps < max_sweeps:

@@ -25,16 +25,20 @@ __device__ __forceinline__ void decide_body(const DevState& S, const CellDesc* _
   double v[5] = {0, 0, 0, 0, 0};
   // The current score's marginal terms enter only the tie slack and the
   // leniency test (they cancel in E(1) - E(1/|b|)), so they are summed with
-  // float logarithms; the theta-dependent changes use double throughout.
+  // float logarithms.  The decision rests on E(1) - E(1/|b|), whose P_Y part
+  // sum_y [kl(p + d) - kl(p + d/|b|)] is summed in double (two double
+  // logarithms per pixel); E(1) - E alone (the leniency test, the decision
+  // record) takes the current term kl(p) in float.
   for (int y = bid * blockDim.x + threadIdx.x; y < n; y += nblk * blockDim.x) {
     v[0] += (double)kl_term_f(S.PX[y], S.mu[y]);
     double p = S.PY[y], m = S.nu[y];
-    v[1] += (double)kl_term_f(p, m);
+    const double k0f = (double)kl_term_f(p, m);
+    v[1] += k0f;
     double d = S.dPY[y];
     if (d != 0.0) {
-      double k0 = dd_kl_term(p, m);
-      v[2] += dd_kl_term(fmax(0.0, p + d), m) - k0;
-      v[3] += dd_kl_term(fmax(0.0, p + th_s * d), m) - k0;
+      const double k1 = dd_kl_term(fmax(0.0, p + d), m);
+      v[2] += k1 - k0f;
+      v[3] += k1 - dd_kl_term(fmax(0.0, p + th_s * d), m);
     }
   }
   for (int i = bid * blockDim.x + threadIdx.x; i < S.nbasic; i += nblk * blockDim.x)
@@ -70,13 +74,15 @@ __device__ __forceinline__ void decide_body(const DevState& S, const CellDesc* _
   if (threadIdx.x != 0) return;
   const double dL = tot[5], dKX1 = tot[6], dKXs = tot[7];
   const double E0 = tot[4] + lam * tot[0] + lam * tot[1];
-  const double dg = dL + lam * dKX1 + lam * tot[2];          // E(1) - E
-  const double ds = th_s * dL + lam * dKXs + lam * tot[3];   // E(1/|b|) - E
+  const double dg = dL + lam * dKX1 + lam * tot[2];          // E(1) - E (P_Y part against a float kl(p))
+  // E(1) - E(1/|b|) in double: the P_Y part directly, the rest as before
+  const double dgs = (1.0 - th_s) * dL + lam * (dKX1 - dKXs) + lam * tot[3];
+  const double ds = dg - dgs;                                // E(1/|b|) - E
   const double Eg = E0 + dg, Es = E0 + ds;
   double theta;
   if (S.strategy == 3) theta = 1.0;                 // greedy
   else if (S.strategy == 2) theta = th_s;           // safe
-  else theta = (dg <= ds + 1e-12 * fabs(E0) || (S.tau > 0.0 && dg <= S.tau * E0)) ? 1.0 : th_s;
+  else theta = (dgs <= 1e-12 * fabs(E0) || (S.tau > 0.0 && dg <= S.tau * E0)) ? 1.0 : th_s;
   *S.theta = theta;
   const unsigned long long slot = (*S.slotctr)++ % DD_LOGCAP;
   double* lg = S.declog + 4 * slot;
@@ -206,101 +212,96 @@ __global__ void k_line_step(DevState S, int first, int last) {
 }
 
 // ================================================================= apply (a7)
-__device__ __forceinline__ void apply_body(const DevState& S, const CellDesc cd, int pos) {
-  __shared__ BoxRec ob[4];
-  __shared__ int bb[4][4];       // per quadrant: min kk, max kk, min ll, max ll of kept entries
-  __shared__ long long noff[4];
-  __shared__ int nbox[4][4];
+// One quadrant q (member basic cell cd.mem[q]) of cell position `pos`; the four
+// quadrants of a cell run in four CTAs (the largest cell's work is split four ways).
+__device__ __forceinline__ void apply_body(const DevState& S, const CellDesc cd, int pos, int q) {
+  __shared__ BoxRec ob;
+  __shared__ int bb[4];          // min kk, max kk, min ll, max ll of kept entries
+  __shared__ long long noff;
+  __shared__ int nbox[4];
   const CellOut o = S.cout[pos];
   if (o.status == CELL_EMPTY || o.status == CELL_TOOBIG) return;
-  const double th = *S.theta, thr = S.thr;
   const int N = S.N, H = o.H, W = o.W, ny = H * W;
+  const int tid = threadIdx.x;
+  // dP_Y of the sub-batch back to zero on this cell's box (each quadrant CTA a quarter)
+  for (int u = 4 * tid + q; u < ny; u += 4 * blockDim.x) {
+    int kk = u / W, ll = u - kk * W;
+    S.dPY[(o.k0 + kk) * N + o.l0 + ll] = 0.0;
+  }
+  const int bi = cd.mem[q];
+  if (bi < 0) return;
+  const double th = *S.theta, thr = S.thr;
   double* arena = S.arena[*S.cur];
   int nst;
-  const double* nut = cell_nut(S, o, pos, &nst);
-  const int tid = threadIdx.x;
-  if (tid < 4) {
-    BoxRec b = {0, 0, 0, 0, 0};
-    if (cd.mem[tid] >= 0) b = S.box[cd.mem[tid]];
-    ob[tid] = b;
-    bb[tid][0] = 1 << 30; bb[tid][1] = -1; bb[tid][2] = 1 << 30; bb[tid][3] = -1;
+  const double* nut = cell_nut(S, o, pos, &nst) + (long long)q * nst;
+  if (tid == 0) {
+    ob = S.box[bi];
+    bb[0] = 1 << 30; bb[1] = -1; bb[2] = 1 << 30; bb[3] = -1;
   }
   __syncthreads();
-  int lb[4][4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) { lb[q][0] = 1 << 30; lb[q][1] = -1; lb[q][2] = 1 << 30; lb[q][3] = -1; }
+  int lb0 = 1 << 30, lb1 = -1, lb2 = 1 << 30, lb3 = -1;
+  const BoxRec b = ob;
   for (int u = tid; u < ny; u += blockDim.x) {
     int kk = u / W, ll = u - kk * W;
     int y1 = o.k0 + kk, y2 = o.l0 + ll;
-    double dl = 0.0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (cd.mem[q] < 0) continue;
-      const BoxRec& b = ob[q];
-      int a = y1 - b.k0, c = y2 - b.l0;
-      double old = (a >= 0 && c >= 0 && a < b.H && c < b.W) ? arena[b.off + (long long)a * b.W + c] : 0.0;
-      double v = (1.0 - th) * old + th * nut[q * nst + u];
-      if (v < thr) v = 0.0;
-      dl += v - old;
-      if (v > 0.0) {
-        lb[q][0] = min(lb[q][0], kk); lb[q][1] = max(lb[q][1], kk);
-        lb[q][2] = min(lb[q][2], ll); lb[q][3] = max(lb[q][3], ll);
-      }
+    int a = y1 - b.k0, c = y2 - b.l0;
+    double old = (a >= 0 && c >= 0 && a < b.H && c < b.W) ? arena[b.off + (long long)a * b.W + c] : 0.0;
+    double v = (1.0 - th) * old + th * nut[u];
+    if (v < thr) v = 0.0;
+    const double dl = v - old;
+    if (v > 0.0) {
+      lb0 = min(lb0, kk); lb1 = max(lb1, kk);
+      lb2 = min(lb2, ll); lb3 = max(lb3, ll);
     }
-    int y = y1 * N + y2;
-    if (dl != 0.0) atomicAdd(S.PY + y, dl);
-    S.dPY[y] = 0.0;
+    if (dl != 0.0) atomicAdd(S.PY + y1 * N + y2, dl);
   }
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    int m0 = warp_min(lb[q][0]), m1 = warp_max(lb[q][1]), m2 = warp_min(lb[q][2]), m3 = warp_max(lb[q][3]);
+  {
+    int m0 = warp_min(lb0), m1 = warp_max(lb1), m2 = warp_min(lb2), m3 = warp_max(lb3);
     if ((tid & 31) == 0) {
-      atomicMin(&bb[q][0], m0); atomicMax(&bb[q][1], m1);
-      atomicMin(&bb[q][2], m2); atomicMax(&bb[q][3], m3);
+      atomicMin(&bb[0], m0); atomicMax(&bb[1], m1);
+      atomicMin(&bb[2], m2); atomicMax(&bb[3], m3);
     }
   }
   __syncthreads();
   if (tid == 0) {
-    for (int q = 0; q < 4; ++q) {
-      int bi = cd.mem[q];
-      if (bi < 0) continue;
-      BoxRec nb = {o.k0, o.l0, 0, 0, 0};
-      if (bb[q][1] >= 0) {
-        nb.k0 = o.k0 + bb[q][0]; nb.l0 = o.l0 + bb[q][2];
-        nb.H = bb[q][1] - bb[q][0] + 1; nb.W = bb[q][3] - bb[q][2] + 1;
-      }
-      long long sz = (long long)nb.H * nb.W;
-      unsigned long long off = atomicAdd(S.head, (unsigned long long)sz);
-      if ((long long)off + sz > S.cap) {
-        atomicOr(S.status, ST_ARENA);
-        nb.H = nb.W = 0;
-        off = 0;
-      }
-      nb.off = (long long)off;
-      noff[q] = nb.off;
-      nbox[q][0] = nb.k0; nbox[q][1] = nb.l0; nbox[q][2] = nb.H; nbox[q][3] = nb.W;
-      S.box[bi] = nb;
-      S.Cc[bi] = (1.0 - th) * S.Cc[bi] + th * o.Ct[q];
-      S.Hh[bi] = (1.0 - th) * S.Hh[bi] + th * o.Ht[q];
+    BoxRec nb = {o.k0, o.l0, 0, 0, 0};
+    if (bb[1] >= 0) {
+      nb.k0 = o.k0 + bb[0]; nb.l0 = o.l0 + bb[2];
+      nb.H = bb[1] - bb[0] + 1; nb.W = bb[3] - bb[2] + 1;
     }
+    long long sz = (long long)nb.H * nb.W;
+    unsigned long long off = atomicAdd(S.head, (unsigned long long)sz);
+    if ((long long)off + sz > S.cap) {
+      atomicOr(S.status, ST_ARENA);
+      nb.H = nb.W = 0;
+      off = 0;
+    }
+    nb.off = (long long)off;
+    noff = nb.off;
+    nbox[0] = nb.k0; nbox[1] = nb.l0; nbox[2] = nb.H; nbox[3] = nb.W;
+    S.box[bi] = nb;
+    S.Cc[bi] = (1.0 - th) * S.Cc[bi] + th * o.Ct[q];
+    S.Hh[bi] = (1.0 - th) * S.Hh[bi] + th * o.Ht[q];
   }
   __syncthreads();
-  for (int q = 0; q < 4; ++q) {
-    if (cd.mem[q] < 0) continue;
-    const int nk0 = nbox[q][0], nl0 = nbox[q][1], nH = nbox[q][2], nW = nbox[q][3];
-    const BoxRec& b = ob[q];
+  {
+    const int nk0 = nbox[0], nl0 = nbox[1], nH = nbox[2], nW = nbox[3];
     for (int u = tid; u < nH * nW; u += blockDim.x) {
       int a = u / nW, c = u - a * nW;
       int y1 = nk0 + a, y2 = nl0 + c;
       int oa = y1 - b.k0, oc = y2 - b.l0;
       double old = (oa >= 0 && oc >= 0 && oa < b.H && oc < b.W) ? arena[b.off + (long long)oa * b.W + oc] : 0.0;
-      double v = (1.0 - th) * old + th * nut[q * nst + (y1 - o.k0) * W + (y2 - o.l0)];
+      double v = (1.0 - th) * old + th * nut[(y1 - o.k0) * W + (y2 - o.l0)];
       if (v < thr) v = 0.0;
-      arena[noff[q] + u] = v;
+      arena[noff + u] = v;
     }
   }
-  for (int t = tid; t < cd.nx1 * cd.nx2; t += blockDim.x) {
-    int r = t / cd.nx2, c = t - r * cd.nx2;
+  // P_X on the quadrant's pixels
+  const int s = S.s, hr = q >> 1, hc = q & 1;
+  const int rb = hr * s, re = min(cd.nx1, rb + s), cb = hc * s, ce = min(cd.nx2, cb + s);
+  const int qw = ce - cb;
+  for (int t = tid; t < (re - rb) * qw; t += blockDim.x) {
+    int r = rb + t / qw, c = cb + (t - (t / qw) * qw);
     int x = (cd.i0 + r) * N + cd.j0 + c;
     S.PX[x] = (1.0 - th) * S.PX[x] + th * S.PXnew[x];
   }
@@ -308,7 +309,7 @@ __device__ __forceinline__ void apply_body(const DevState& S, const CellDesc cd,
 
 __global__ void __launch_bounds__(1024)
 k_apply(DevState S, const CellDesc* __restrict__ cells, int begin) {
-  apply_body(S, cells[begin + blockIdx.x], blockIdx.x);
+  apply_body(S, cells[begin + blockIdx.x], blockIdx.x, blockIdx.y);
 }
 
 __global__ void __launch_bounds__(1024)
@@ -321,7 +322,7 @@ k_apply_multi(const DevState* __restrict__ states, const CellRef* __restrict__ r
     for (int w = threadIdx.x; w < (int)(sizeof(DevState) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
   }
   __syncthreads();
-  apply_body(sS, sS.cells[part][rf.cell], rf.pos);
+  apply_body(sS, sS.cells[part][rf.cell], rf.pos, blockIdx.y);
 }
 
 // ============================================================ arena compaction
@@ -653,7 +654,7 @@ cudaError_t launch_decide_multi(const DevState* states, int ninst, int maxn, int
   return cudaGetLastError();
 }
 cudaError_t launch_apply_multi(const DevState* states, const CellRef* refs, int nref, int part, cudaStream_t st) {
-  if (nref > 0) k_apply_multi<<<nref, 1024, 0, st>>>(states, refs, part);
+  if (nref > 0) k_apply_multi<<<dim3(nref, 4), 1024, 0, st>>>(states, refs, part);
   return cudaGetLastError();
 }
 cudaError_t launch_compact_multi(const DevState* states, int ninst, int max_nbasic, cudaStream_t st) {
@@ -663,7 +664,7 @@ cudaError_t launch_compact_multi(const DevState* states, int ninst, int max_nbas
   return cudaGetLastError();
 }
 cudaError_t launch_apply(const DevState& S, const CellDesc* cells, int begin, int nbatch, cudaStream_t st) {
-  k_apply<<<nbatch, 1024, 0, st>>>(S, cells, begin);
+  k_apply<<<dim3(nbatch, 4), 1024, 0, st>>>(S, cells, begin);
   return cudaGetLastError();
 }
 cudaError_t launch_compact(const DevState& S, long long* newoff, cudaStream_t st) {
