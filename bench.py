@@ -367,6 +367,9 @@ def main():
                     help="CTAs per cell of the timed sweeps (domdec_params.cell_ctas)")
     ap.add_argument("--cell-ti", type=int, default=0, choices=[0, 1],
                     help="translation step in the cell solves of the timed sweeps (domdec_params.cell_ti)")
+    ap.add_argument("--ttg-sweeps", type=int, default=0,
+                    help="only run this many sweeps of the time-to-gap configuration and report the cell "
+                         "kernel in that regime (profiling)")
     ap.add_argument("--balance", type=int, default=0, choices=[0, 1],
                     help="balancing step after each cell solve of the timed sweeps (domdec_params.balance)")
     ap.add_argument("--quick-warm", action="store_true",
@@ -404,6 +407,29 @@ def main():
     mu_d = torch.from_numpy(mu).cuda()
     nu_d = torch.from_numpy(nu).cuda()
     a0, b0, t_warm, it_warm = warm_start(dd, mu_d, nu_d, N, eps, lam, torch, quick=args.quick_warm)
+
+    if args.ttg_sweeps > 0:
+        # the compute-heavy regime of the time-to-gap run (cell tolerance 1e-7): its first sweeps
+        # only, with the cell kernel's throughput and MUFU fraction (profiling runs)
+        g = dd.DomDec(mu_d, nu_d, eps, lam, s, alpha0=a0, beta0=b0, eps_init=2 * eps, precision="fp32",
+                      tau=0.0, err=1e-7, maxit=1000, cell_ctas=args.cell_ctas, profile=1)
+        g.iterate(args.ttg_sweeps)
+        g.sync()
+        st = g.stats()
+        kms, kn = g.kernel_times(reset=True)
+        g.close()
+        pk, _ = peaks()
+        peak = N_SM * MUFU_PER_SM_CLK * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        if rank == 0:
+            print(json.dumps({"regime": "time-to-gap sweeps (cell tolerance 1e-7, maxit 1000)",
+                              "sweeps": args.ttg_sweeps, "cell_iters": st["cell_iters"],
+                              "maxit_cells": st["maxit_cells"], "cell_kernel_ms": float(kms[0]),
+                              "cell_iters_per_s": st["cell_iters"] / max(kms[0] / 1e3, 1e-12),
+                              "mufu_frac": st["lse_terms"] / max(kms[0] / 1e3, 1e-12) / 1e12 / peak}), flush=True)
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
 
     g = dd.DomDec(mu_d, nu_d, eps, lam, s, alpha0=a0, beta0=b0, eps_init=2 * eps, precision="fp32",
                   tau=0.0, err=2e-5, profile=1, cell_ctas=args.cell_ctas, cell_ti=args.cell_ti,

@@ -322,7 +322,11 @@ k_apply_multi(const DevState* __restrict__ states, const CellRef* __restrict__ r
     for (int w = threadIdx.x; w < (int)(sizeof(DevState) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
   }
   __syncthreads();
-  apply_body(sS, sS.cells[part][rf.cell], rf.pos, blockIdx.y);
+  // one CTA per cell here (a batch has thousands of cells): the four quadrants in turn
+  for (int q = 0; q < 4; ++q) {
+    apply_body(sS, sS.cells[part][rf.cell], rf.pos, q);
+    __syncthreads();
+  }
 }
 
 // ============================================================ arena compaction
@@ -654,7 +658,7 @@ cudaError_t launch_decide_multi(const DevState* states, int ninst, int maxn, int
   return cudaGetLastError();
 }
 cudaError_t launch_apply_multi(const DevState* states, const CellRef* refs, int nref, int part, cudaStream_t st) {
-  if (nref > 0) k_apply_multi<<<dim3(nref, 4), 1024, 0, st>>>(states, refs, part);
+  if (nref > 0) k_apply_multi<<<nref, 1024, 0, st>>>(states, refs, part);
   return cudaGetLastError();
 }
 cudaError_t launch_compact_multi(const DevState* states, int ninst, int max_nbasic, cudaStream_t st) {
