@@ -215,7 +215,7 @@ def run_batch(args, dd, torch):
                                 check_every=20, alpha=a, beta=b)
         for lst in (handles_b, handles_s):
             lst.append(dd.DomDec(mu_d, nu_d, p["eps"], p["lam"], 8, alpha0=a, beta0=b, eps_init=2 * p["eps"],
-                                 precision="fp32", tau=0.0, err=2e-5))
+                                 precision="fp32", tau=0.0, err=2e-5, spill_slots=32))
     torch.cuda.synchronize()
     t_warm = time.perf_counter() - t0
     B = dd.DomDecBatch(handles_b)

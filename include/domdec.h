@@ -78,7 +78,8 @@ typedef struct {
   double eps_init;     /* eps of the warm-start duals passed to domdec_init (ignored without duals) */
   int    profile;      /* 1: time every kernel of a sweep with CUDA events on the handle's stream */
   int    spill_slots;  /* cells whose Y-box exceeds max_ny run from global memory slots (per sub-batch): 0 = default
-                          (up to 32 slots and 4 GiB), > 0 = that many, < 0 = none (such cells fail with DOMDEC_ETOOBIG) */
+                          (one per cell of the largest sub-batch, at most 4 GiB), > 0 = that many, < 0 = none
+                          (such cells fail with DOMDEC_ETOOBIG) */
   int    cell_ctas;    /* CTAs per cell: 0 = a 2-CTA cluster when all cells of a sub-batch fit as resident
                           clusters (else 1), 1 = always one CTA per cell, 2 = always a 2-CTA cluster (cells
                           beyond the resident clusters wait for a free pair of SMs) */

@@ -64,8 +64,9 @@ class Geometry:
         self.pix = uot.grid_index(N, d)
         bidx = self.pix // s
         self.basic_of_pixel = np.ravel_multi_index(tuple(bidx.T), (self.nb,) * d)
-        self.basic_pixels = [np.flatnonzero(self.basic_of_pixel == i)
-                             for i in range(self.nbasic)]
+        order = np.argsort(self.basic_of_pixel, kind="stable")
+        cuts = np.searchsorted(self.basic_of_pixel[order], np.arange(self.nbasic + 1))
+        self.basic_pixels = [order[cuts[i]:cuts[i + 1]] for i in range(self.nbasic)]
         self.parts = {"A": self._partition(0), "B": self._partition(1)}
 
     def box_flat(self, lo, hi):

@@ -416,8 +416,9 @@ int domdec_init(domdec_t* out, const double* mu, const double* nu, int N, const 
     size_t ybytes = rs * (4 * (size_t)h->s * N + 5 * (size_t)n);
     ybytes = (ybytes + 255) / 256 * 256;
     const size_t stride = ybytes + 4 * (size_t)n * sizeof(double);
-    const size_t budget = (size_t)4 << 30;  // at most 4 GiB and 32 slots by default (spilled cells are rare)
-    int slots = (int)std::min<size_t>(std::min<size_t>((size_t)std::max(1, mb), 32), std::max<size_t>(1, budget / stride));
+    // default: one slot per cell of the largest sub-batch, within 4 GiB
+    const size_t budget = (size_t)4 << 30;
+    int slots = (int)std::min<size_t>((size_t)std::max(1, mb), std::max<size_t>(1, budget / stride));
     if (pin->spill_slots > 0) slots = pin->spill_slots;
     if (pin->spill_slots < 0) slots = 0;
     S.spill_stride = (long long)stride;
