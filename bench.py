@@ -48,9 +48,9 @@ def peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def workload_inputs(rank=0):
+def workload_inputs(rank=0, name="blobs256"):
     from paper_2410_08859_gb300 import inputs
-    mu, nu, spec = inputs.workload("blobs256", instance=rank)
+    mu, nu, spec = inputs.workload(name, instance=rank)
     return mu.ravel().copy(), nu.ravel().copy(), spec
 
 
@@ -223,6 +223,7 @@ def run_batch(args, dd, torch):
     B.iterate(args.warmup)
     B.sync()
     it0 = sum(h.stats()["cell_iters"] for h in handles_b)
+    lt0 = sum(h.stats()["lse_terms"] for h in handles_b)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record()
@@ -232,6 +233,9 @@ def run_batch(args, dd, torch):
     B.sync()
     t_b = e0.elapsed_time(e1)
     it_b = sum(h.stats()["cell_iters"] for h in handles_b) - it0
+    lt_b = sum(h.stats()["lse_terms"] for h in handles_b) - lt0
+    pk, _ = peaks()
+    peak = N_SM * MUFU_PER_SM_CLK * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
     # the same problems, one handle after another
     for h in handles_s:
         h.iterate(2 + args.warmup)
@@ -260,6 +264,9 @@ def run_batch(args, dd, torch):
             "sequential_single_handles": {"value": it_s / (t_s / 1000.0), "unit": UNIT,
                                           "ms_per_step": t_s / args.steps},
             "batch_speedup": (it_b / t_b) / max(it_s / t_s, 1e-30),
+            # exp terms of all cell iterations over the whole sweep time (decide, apply and
+            # compaction included): a lower bound of the cell kernel's own fraction
+            "mufu_frac_whole_sweep": (lt_b / (t_b / 1e3)) / 1e12 / peak,
             "warm_start_s": t_warm}
     print(json.dumps(line), flush=True)
 
@@ -361,7 +368,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--lam", type=float, default=1.0)
-    ap.add_argument("--workload", default="blobs256", choices=["blobs256", "batch64", "grad512"])
+    ap.add_argument("--workload", default="blobs256", choices=["blobs256", "lognormal1024", "batch64", "grad512"])
     ap.add_argument("--no-extras", action="store_true", help="skip time-to-gap, e2e and CPU baseline")
     ap.add_argument("--cell-ctas", type=int, default=0, choices=[0, 1, 2],
                     help="CTAs per cell of the timed sweeps (domdec_params.cell_ctas)")
@@ -402,7 +409,7 @@ def main():
             dist.destroy_process_group()
         return
 
-    mu, nu, spec = workload_inputs(rank)
+    mu, nu, spec = workload_inputs(rank, args.workload)
     N, s, eps, lam = spec["N"], spec["s"], spec["eps"], args.lam
     mu_d = torch.from_numpy(mu).cuda()
     nu_d = torch.from_numpy(nu).cuda()
@@ -489,7 +496,7 @@ def main():
                 "unit": "Tex2/s", "frac": achieved / peak_mufu,
                 # dram read + write bytes of one launch, from the ncu capture summarised in
                 # profiles/cell_solve_blobs256.md (set to None when the cell kernel changes)
-                "traffic": CELL_KERNEL_DRAM_BYTES,
+                "traffic": CELL_KERNEL_DRAM_BYTES if args.workload == "blobs256" else None,
                 "peak_source": f"{N_SM} SMs x {MUFU_PER_SM_CLK} MUFU/clk x {sm_mhz:.0f} MHz ({pk_kind} max clock)",
                 "kernel_share": float(kms[0] / max(kms.sum(), 1e-12)),
                 "kernel_ms": {"cell_solve": kms[0], "decide": kms[1], "apply": kms[2], "compact": kms[3]},
@@ -554,7 +561,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "blobs256", "N": N, "basic_cell": s, "eps": eps, "lam": lam,
+            "config": {"workload": args.workload, "N": N, "basic_cell": s, "eps": eps, "lam": lam,
                        "eps_scaling": "1 -> 2 eps by global Sinkhorn (warm start), DomDec at eps",
                        "strategy": "staggered", "tau": 0.0, "err": 2e-5, "precision": "fp32 cell / fp64 score",
                        "cell_ctas": args.cell_ctas, "cell_ti": args.cell_ti, "balance": args.balance,
