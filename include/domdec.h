@@ -53,6 +53,8 @@ extern "C" {
 #define DOMDEC_LINE      4   /* GetWeights_line (Proposition 4.3): one zeta in [1/|b|, 1] for all cells of the
                                 partition minimising the tracked score (convex in zeta; safeguarded Newton on
                                 its derivative, at most 48 steps, on the device); not for batches */
+#define DOMDEC_STAGGERED_LINE 5  /* the staggered sub-batches of DOMDEC_STAGGERED with GetWeights_line on each
+                                    (zeta in [1/|b|, 1] per sub-batch); not for batches */
 
 #define DOMDEC_FP32 0        /* cell Sinkhorn arithmetic in float (state, score, decision stay double) */
 #define DOMDEC_FP64 1        /* cell Sinkhorn arithmetic in double */
@@ -68,7 +70,7 @@ typedef struct {
                           err < 0 runs exactly maxit iterations per cell */
   double trunc_thr;    /* nu_i(y) < trunc_thr is dropped (Section 5.3; paper: 1e-15) */
   double tau;          /* greedy leniency: accept theta = 1 if E(1) <= (1 + tau) E (Section 5.3: 0.005); 0 = pure swift */
-  int    strategy;     /* DOMDEC_STAGGERED | SWIFT | SAFE | GREEDY | LINE */
+  int    strategy;     /* DOMDEC_STAGGERED | SWIFT | SAFE | GREEDY | LINE | STAGGERED_LINE */
   int    maxit;        /* cap on cell Sinkhorn iterations (status MAXIT when hit) */
   int    newton_maxit; /* cap on Newton steps per y in the Y-half */
   int    precision;    /* DOMDEC_FP32 | DOMDEC_FP64 */

@@ -450,7 +450,7 @@ def get_weights(st, batch, probs, sols, strategy, tau):
         return th_safe, E0, None, None
     Eg = tracked_score(st, *mixed_quantities(st, batch, probs, sols, 1.0))
     Es = tracked_score(st, *mixed_quantities(st, batch, probs, sols, th_safe))
-    if strategy == "line":
+    if strategy in ("line", "staggered_line"):
         return line_search(st, batch, probs, sols, th_safe), E0, Eg, Es
     if Eg <= Es + 1e-12 * abs(E0) or (tau > 0 and Eg <= (1 + tau) * E0):
         return 1.0, E0, Eg, Es
@@ -483,7 +483,7 @@ def apply_step(st, batch, probs, sols, theta):
 # ===================================================================== sweeps
 def batches_of(st, which, strategy):
     cells = st.geo.parts[which]
-    if strategy == "staggered":
+    if strategy in ("staggered", "staggered_line"):
         nsub = 2 ** st.geo.d
         out = [[c for c in cells if c["sub"] == b] for b in range(nsub)]
         return [b for b in out if b]

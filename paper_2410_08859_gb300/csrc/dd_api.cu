@@ -146,7 +146,7 @@ int check_params(const domdec_params* p, int N) {
   if (!(p->lambda > 0.0) || !std::isfinite(p->lambda)) return DOMDEC_EINVAL;
   if (p->basic_cell < 1 || p->basic_cell > 16 || N % (2 * p->basic_cell)) return DOMDEC_EINVAL;
   if (p->maxit < 1 || p->newton_maxit < 1) return DOMDEC_EINVAL;
-  if (p->strategy < 0 || p->strategy > 4 || (p->precision != 0 && p->precision != 1)) return DOMDEC_EINVAL;
+  if (p->strategy < 0 || p->strategy > 5 || (p->precision != 0 && p->precision != 1)) return DOMDEC_EINVAL;
   if (!(p->trunc_thr >= 0.0) || p->box_margin < 0) return DOMDEC_EINVAL;
   if (p->cell_ctas < 0 || p->cell_ctas > 2 || p->cell_ti < 0 || p->cell_ti > 1) return DOMDEC_EINVAL;
   if (p->balance < 0 || p->balance > 1) return DOMDEC_EINVAL;
@@ -236,7 +236,7 @@ void prof_collect(domdec_s* h) {
 int enqueue_sweep(domdec_s* h, int part, long long slot0) {
   const int prec = h->p.precision;
   std::vector<std::pair<int, int>> batches;
-  if (h->p.strategy == DOMDEC_STAGGERED) {
+  if (h->p.strategy == DOMDEC_STAGGERED || h->p.strategy == DOMDEC_STAGGERED_LINE) {
     for (int b = 0; b < 4; ++b) batches.push_back({h->sub_start[part][b], h->sub_start[part][b + 1]});
   } else {
     batches.push_back({0, h->ncell[part]});
@@ -255,7 +255,7 @@ int enqueue_sweep(domdec_s* h, int part, long long slot0) {
     prof_end(h, ev, 0);
     ev = prof_begin(h);
     if (launch_decide(h->S, h->d_cells[part], begin, nbt, h->st) != cudaSuccess) return DOMDEC_ECUDA;
-    if (h->p.strategy == DOMDEC_LINE &&
+    if ((h->p.strategy == DOMDEC_LINE || h->p.strategy == DOMDEC_STAGGERED_LINE) &&
         launch_line_search(h->S, h->d_cells[part], begin, nbt, h->d_partials, h->st) != cudaSuccess)
       return DOMDEC_ECUDA;
     prof_end(h, ev, 1);
@@ -271,7 +271,8 @@ int enqueue_sweep(domdec_s* h, int part, long long slot0) {
 }
 
 int batches_per_sweep(domdec_s* h, int part) {
-  if (h->p.strategy != DOMDEC_STAGGERED) return h->ncell[part] > 0 ? 1 : 0;
+  if (h->p.strategy != DOMDEC_STAGGERED && h->p.strategy != DOMDEC_STAGGERED_LINE)
+    return h->ncell[part] > 0 ? 1 : 0;
   int c = 0;
   for (int b = 0; b < 4; ++b) c += h->sub_start[part][b + 1] > h->sub_start[part][b];
   return c;
@@ -378,7 +379,7 @@ int domdec_init(domdec_t* out, const double* mu, const double* nu, int N, const 
   }
   int mb = 0;
   for (int w = 0; w < 2; ++w) {
-    if (pin->strategy == DOMDEC_STAGGERED) {
+    if (pin->strategy == DOMDEC_STAGGERED || pin->strategy == DOMDEC_STAGGERED_LINE) {
       for (int b = 0; b < 4; ++b) mb = std::max(mb, h->sub_start[w][b + 1] - h->sub_start[w][b]);
     } else {
       mb = std::max(mb, h->ncell[w]);
@@ -450,7 +451,7 @@ int domdec_init(domdec_t* out, const double* mu, const double* nu, int N, const 
     S.cells[w] = h->d_cells[w];
     for (int b = 0; b < 5; ++b) S.sub_start[w][b] = h->sub_start[w][b];
   }
-  S.staggered = pin->strategy == DOMDEC_STAGGERED;
+  S.staggered = pin->strategy == DOMDEC_STAGGERED || pin->strategy == DOMDEC_STAGGERED_LINE;
   S.newoff = h->d_newoff;
   cudaMemsetAsync(S.slotctr, 0, sizeof(unsigned long long), st);
   if (e == cudaSuccess) e = launch_prepare_inputs(dmu, dnu, dlogmu, dlognu, n, S.status, st);
@@ -864,6 +865,7 @@ int domdec_batch_create(domdec_batch_t* out, domdec_t* handles, int n) {
     if (handles[i]->sticky) return DOMDEC_ESTATE;
     if (handles[i]->p.precision != handles[0]->p.precision || handles[i]->p.strategy != handles[0]->p.strategy ||
         handles[i]->sweeps != handles[0]->sweeps || handles[i]->p.strategy == DOMDEC_LINE ||
+        handles[i]->p.strategy == DOMDEC_STAGGERED_LINE ||
         handles[i]->p.balance)
       return DOMDEC_EINVAL;
   }

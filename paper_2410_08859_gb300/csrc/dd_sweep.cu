@@ -87,7 +87,7 @@ __device__ __forceinline__ void decide_body(const DevState& S, const CellDesc* _
   const unsigned long long slot = (*S.slotctr)++ % DD_LOGCAP;
   double* lg = S.declog + 4 * slot;
   lg[0] = E0; lg[1] = Eg; lg[2] = Es; lg[3] = theta;
-  if (S.strategy == 4) {
+  if (S.strategy == 4 || S.strategy == 5) {
     // GetWeights_line: the search kernels refine theta (and the log record)
     S.line[5] = 0.0;        // not done
     S.line[6] = th_s;       // lower end of the bracket

@@ -17,8 +17,9 @@ from . import build as _build
 DOMDEC_OK, DOMDEC_WNOTCONV = 0, 1
 DOMDEC_EINVAL, DOMDEC_ENOMEM, DOMDEC_ECUDA = -1, -2, -3
 DOMDEC_ETOOBIG, DOMDEC_EARENA, DOMDEC_ESTATE, DOMDEC_ENOLIB = -4, -5, -6, -7
-STAGGERED, SWIFT, SAFE, GREEDY, LINE = 0, 1, 2, 3, 4
-STRATEGIES = {"staggered": STAGGERED, "swift": SWIFT, "safe": SAFE, "greedy": GREEDY, "line": LINE}
+STAGGERED, SWIFT, SAFE, GREEDY, LINE, STAGGERED_LINE = 0, 1, 2, 3, 4, 5
+STRATEGIES = {"staggered": STAGGERED, "swift": SWIFT, "safe": SAFE, "greedy": GREEDY, "line": LINE,
+              "staggered_line": STAGGERED_LINE}
 FP32, FP64, MIXED = 0, 1, 2
 SINKHORN_DENSE, SINKHORN_SEPARABLE, SINKHORN_TI = 0, 1, 4
 

@@ -85,7 +85,7 @@ def run_pair(dd, N, s, mu, nu, eps, lam, sweeps, precision, strategy="staggered"
         dec = g.decisions()
         assert len(dec) == nrec + len(log)
         for rec, d in zip(log, dec[nrec:]):
-            if strategy == "line":   # a root found by a search: equal to rounding of the search
+            if strategy in ("line", "staggered_line"):   # a search's root: equal to its rounding
                 assert abs(d[3] - rec["theta"]) <= 1e-9, (k, d, rec)
             else:
                 assert d[3] == rec["theta"], (k, d, rec)
@@ -162,6 +162,13 @@ def test_fp32_balancing_converges_to_oracle_optimum(dd):
     assert abs(E - Eopt) <= 1e-6 * Eopt, (E, Eopt)
     assert np.abs(PX - pi.sum(1)).sum() / mu.sum() <= 1e-5
     assert np.abs(PY - pi.sum(0)).sum() / mu.sum() <= 1e-5
+    g.close()
+
+
+def test_fp64_staggered_line_search_matches_oracle(dd):
+    """Staggered sub-batches with GetWeights_line on each (strategy 'staggered_line')."""
+    mu, nu = inputs.mixture_small(N=32, seed=1013)
+    g, st = run_pair(dd, 32, 4, mu, nu, (1 / 32) ** 2, 1.0, 3, "fp64", strategy="staggered_line")
     g.close()
 
 
