@@ -1,6 +1,6 @@
 // Host side of the C ABI declared in include/domdec.h: handle lifetime, the
 // partitions and staggered sub-batches (Section 5.3), the sweep driver
-// (Algorithm 2 over Algorithm 4 per sub-batch), CUDA-graph replay of sweeps,
+// (Algorithm 2 over Algorithm 4 per sub-batch),
 // and the read-back entry points.
 #include <cuda_runtime.h>
 
@@ -82,9 +82,6 @@ struct domdec_s {
   int sticky = 0;
   int last_batch = 0;
   int max_pairs = 0;  // co-resident 2-CTA clusters of the cell kernel
-  // graphs: one sweep per partition
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
-  bool graph_ok = true;
   // profiling: pending event pairs per kernel class
   struct EvPair { cudaEvent_t a, b; int cls; };
   std::vector<EvPair> pend;
@@ -187,8 +184,6 @@ int ensure_arena(domdec_s* h) {
   h->S.arena[0] = a0;
   h->S.arena[1] = a1;
   h->S.cap = ncap;
-  for (int k = 0; k < 2; ++k)
-    if (h->graph[k]) { cudaGraphExecDestroy(h->graph[k]); h->graph[k] = nullptr; }
   return DOMDEC_OK;
 }
 
@@ -321,8 +316,6 @@ void domdec_free(domdec_t h) {
   cudaStreamSynchronize(h->st);
   prof_collect(h);
   for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
-  for (int k = 0; k < 2; ++k)
-    if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
   for (void* q : h->allocs)
     if (q) cudaFree(q);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
@@ -516,8 +509,6 @@ int domdec_set_eps(domdec_t h, double eps) {
   if (!(eps > 0.0) || !std::isfinite(eps)) return DOMDEC_EINVAL;
   h->S.eps = eps;
   h->p.eps = eps;
-  for (int k = 0; k < 2; ++k)
-    if (h->graph[k]) { cudaGraphExecDestroy(h->graph[k]); h->graph[k] = nullptr; }
   return DOMDEC_OK;
 }
 
@@ -527,8 +518,6 @@ int domdec_set_tolerance(domdec_t h, double err) {
   if (!(err == err) || std::isinf(err)) return DOMDEC_EINVAL;
   h->S.err = err;
   h->p.err = err;
-  for (int k = 0; k < 2; ++k)
-    if (h->graph[k]) { cudaGraphExecDestroy(h->graph[k]); h->graph[k] = nullptr; }
   return DOMDEC_OK;
 }
 
