@@ -8,13 +8,14 @@
  * on X = Y = the N x N pixel grid {h (i, j)}, h = 1/N, c(x,y) = |x - y|^2.
  *
  * One call of domdec_iterate performs parallel DomDec iterations (Algorithm 4)
- * over partition A, then B, ... (Algorithm 2).  Each iteration is split into
- * the 2^2 staggered sub-batches of Section 5.3 and, for each sub-batch:
+ * over partition A, then B, ... (Algorithm 2).  With the staggered strategies
+ * each iteration is split into the 2^2 staggered sub-batches of Section 5.3
+ * (otherwise one batch per partition) and, for each sub-batch:
  *   a1 nu_{-J}/nu on the cell's Y-box B_J            (Section 5.1, "Computing and handling nu_{-J}")
  *   a2-a4 the cell Sinkhorn with Newton Y-half and PD stopping
  *                                                     (Eqs. sinkhorn-X/Y-iteration, proxdiv-problem, PD-gap-KL)
  *   a5 the new basic-cell Y-marginals, C_i, H_i      (Eq. sinkhorn-primal, Definition 2.4)
- *   a6 GetWeights = swift on the sub-batch           (Proposition 4.3, Section 4.4 "staggered")
+ *   a6 GetWeights per domdec_params.strategy         (Proposition 4.3, Section 4.4 "staggered")
  *   a7 the convex combination, truncation, box refresh (Algorithm 4 last line; Section 5.3 truncation)
  * all on the GPU, enqueued on the stream given at domdec_init.
  *
