@@ -59,7 +59,9 @@ extern "C" {
 
 #define DOMDEC_FP32 0        /* cell Sinkhorn arithmetic in float (state, score, decision stay double) */
 #define DOMDEC_FP64 1        /* cell Sinkhorn arithmetic in double */
-#define DOMDEC_MIXED 2       /* domdec_full_sinkhorn only: float for coarse eps stages, double for fine */
+#define DOMDEC_MIXED 2       /* domdec_full_sinkhorn only: float for coarse eps stages (eps >= 64 h^2); for the
+                                fine ones double potentials and exponents with float exponentials of the kept
+                                terms (relative error ~1e-7 per log-sum-exp, i.e. ~1e-7 eps in the potentials) */
 
 typedef struct domdec_s* domdec_t;
 

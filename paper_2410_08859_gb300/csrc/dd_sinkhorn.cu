@@ -34,7 +34,11 @@ struct SepBufs {
 // One 1-D log-sum-exp per target with P lanes: the maximum and the window
 // test run in float on the shadow values; only terms within `cut` of the
 // maximum are evaluated (in R) and summed.
-template <typename R, typename FS, typename FF>
+// FAST (double only): each kept term's exponent is formed in double and only its
+// exponential (at most `cut` below the maximum) is taken in float (ex2.approx);
+// the sums stay double.  The sum's relative error is ~1e-7, i.e. ~1e-7 absolute
+// in log2 units, whatever the magnitude of the exponents.
+template <typename R, bool FAST = false, typename FS, typename FF>
 __device__ __forceinline__ R lse_window(FS src, FF srcf, int M, int ctr, double q2, int part, int P) {
   const float q2f = (float)q2;
   float mxf = -INFINITY;
@@ -51,7 +55,8 @@ __device__ __forceinline__ R lse_window(FS src, FF srcf, int M, int ctr, double 
     float d = (float)(ctr - m);
     if (srcf(m) - q2f * d * d - mxf > -cutf) {
       R dr = R(ctr - m);
-      acc += dd_ex2(src(m) - q2r * dr * dr - mx);
+      if (FAST) acc += R(dd_ex2(float(src(m) - q2r * dr * dr - mx)));
+      else acc += dd_ex2(src(m) - q2r * dr * dr - mx);
     }
   }
   for (int o = 1; o < P; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -61,7 +66,7 @@ __device__ __forceinline__ R lse_window(FS src, FF srcf, int M, int ctr, double 
 constexpr int kSepLanes = 4;   // lanes per target in the separable passes
 
 // tmp[k*N + j] = log2 sum_l 2^{in[k*N + l] - q2 (j - l)^2}   (block = row k)
-template <typename R>
+template <typename R, bool FAST>
 __global__ void __launch_bounds__(1024) k_sep_rows(SepBufs<R> B, int N, double q2) {
   extern __shared__ __align__(16) unsigned char sm[];
   R* row = reinterpret_cast<R*>(sm);
@@ -75,7 +80,7 @@ __global__ void __launch_bounds__(1024) k_sep_rows(SepBufs<R> B, int N, double q
   const int P = kSepLanes, nt = (N * P + 31) & ~31;
   for (int i = threadIdx.x; i < nt; i += blockDim.x) {
     const int j0 = i / P, part = i % P, j = min(j0, N - 1);
-    R v = lse_window<R>([&](int m) { return row[m]; }, [&](int m) { return rowf[m]; }, N, j, q2, part, P);
+    R v = lse_window<R, FAST>([&](int m) { return row[m]; }, [&](int m) { return rowf[m]; }, N, j, q2, part, P);
     if (part == 0 && j0 < N) {
       B.tmp[(long long)k * N + j] = v;
       if (sizeof(R) == 8) B.tmpf[(long long)k * N + j] = (float)v;
@@ -84,7 +89,7 @@ __global__ void __launch_bounds__(1024) k_sep_rows(SepBufs<R> B, int N, double q
 }
 
 // out[i*N + j] = log2 sum_k 2^{tmp[k*N + j] - q2 (i - k)^2}   (block = (j tile, i))
-template <typename R>
+template <typename R, bool FAST>
 __global__ void __launch_bounds__(256) k_sep_cols(SepBufs<R> B, int N, double q2) {
   const int P = kSepLanes;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -92,7 +97,7 @@ __global__ void __launch_bounds__(256) k_sep_cols(SepBufs<R> B, int N, double q2
   const int i = blockIdx.y;
   const R* col = B.tmp + j;
   const float* colf = B.tmpf + j;
-  R v = lse_window<R>([&](int m) { return col[(long long)m * N]; }, [&](int m) { return colf[(long long)m * N]; },
+  R v = lse_window<R, FAST>([&](int m) { return col[(long long)m * N]; }, [&](int m) { return colf[(long long)m * N]; },
                       N, i, q2, part, P);
   if (part == 0 && j0 < N) B.out[(long long)i * N + j] = v;
 }
@@ -242,7 +247,7 @@ struct Work {
 // in2f / tmpf: float shadows (required for R = double; ignored for float).
 template <typename R>
 cudaError_t lse_all(const R* in2, R* tmp, R* out2, int N, double q, int variant, int use_shift, cudaStream_t st,
-                    const float* in2f = nullptr, float* tmpf = nullptr) {
+                    const float* in2f = nullptr, float* tmpf = nullptr, bool fast = false) {
   if (variant == 1) {
     SepBufs<R> B;
     B.in = in2;
@@ -252,8 +257,13 @@ cudaError_t lse_all(const R* in2, R* tmp, R* out2, int N, double q, int variant,
     B.out = out2;
     const double q2 = q * DD_LOG2E;
     const int thr_rows = min(1024, ((N * kSepLanes + 31) / 32) * 32);
-    k_sep_rows<R><<<N, thr_rows, N * (sizeof(R) + sizeof(float)), st>>>(B, N, q2);
-    k_sep_cols<R><<<dim3((N * kSepLanes + 255) / 256, N), 256, 0, st>>>(B, N, q2);
+    if (fast && sizeof(R) == 8) {
+      k_sep_rows<R, true><<<N, thr_rows, N * (sizeof(R) + sizeof(float)), st>>>(B, N, q2);
+      k_sep_cols<R, true><<<dim3((N * kSepLanes + 255) / 256, N), 256, 0, st>>>(B, N, q2);
+    } else {
+      k_sep_rows<R, false><<<N, thr_rows, N * (sizeof(R) + sizeof(float)), st>>>(B, N, q2);
+      k_sep_cols<R, false><<<dim3((N * kSepLanes + 255) / 256, N), 256, 0, st>>>(B, N, q2);
+    }
   } else {
     R q2 = R(q * DD_LOG2E);
     int n = N * N;
@@ -284,7 +294,7 @@ template <typename R>
 static int full_sinkhorn_impl(const double* mu, const double* nu, const double* logmu, const double* lognu,
                               int N, double eps_start, double eps, double lam, int variant, int maxit,
                               double err, int check_every, double* alpha, double* beta, double* out,
-                              double* d_eval, cudaStream_t st, cudaError_t* cerr) {
+                              double* d_eval, cudaStream_t st, cudaError_t* cerr, bool fast = false) {
   const int n = N * N;
   const double h = 1.0 / N;
   const bool ti = (variant & DOMDEC_SINKHORN_TI) && std::isfinite(lam);
@@ -310,7 +320,7 @@ static int full_sinkhorn_impl(const double* mu, const double* nu, const double* 
     const double q = h * h / e;
     // w = LSE_y[beta/e + log nu]
     k_to_log2<R><<<grid, 256, 0, st>>>(beta, lognu, 1.0 / e, w.in2, n, w.in2f);
-    lse_all<R>(w.in2, w.tmp, w.w2, N, q, variant, 0, st, w.in2f, w.tmpf);
+    lse_all<R>(w.in2, w.tmp, w.w2, N, q, variant, 0, st, w.in2f, w.tmpf, fast);
     int it = 0;
     bool conv = false;
     int shift_ok = 0;
@@ -318,10 +328,10 @@ static int full_sinkhorn_impl(const double* mu, const double* nu, const double* 
       k_half<R><<<grid, 256, 0, st>>>(w.w2, kap, alpha, n);
       if (ti) ti_step(mu, nu, alpha, beta, lam, n, d_eval + 6, partials, st);
       k_to_log2<R><<<grid, 256, 0, st>>>(alpha, logmu, 1.0 / e, w.in2, n, w.in2f);
-      lse_all<R>(w.in2, w.tmp, w.z2, N, q, variant, shift_ok, st, w.in2f, w.tmpf);
+      lse_all<R>(w.in2, w.tmp, w.z2, N, q, variant, shift_ok, st, w.in2f, w.tmpf, fast);
       k_half<R><<<grid, 256, 0, st>>>(w.z2, kap, beta, n);
       k_to_log2<R><<<grid, 256, 0, st>>>(beta, lognu, 1.0 / e, w.in2, n, w.in2f);
-      lse_all<R>(w.in2, w.tmp, w.w2, N, q, variant, 1, st, w.in2f, w.tmpf);
+      lse_all<R>(w.in2, w.tmp, w.w2, N, q, variant, 1, st, w.in2f, w.tmpf, fast);
       shift_ok = 1;
       ++it;
       if (it % check_every == 0 || it == maxit) {
@@ -377,11 +387,14 @@ int full_sinkhorn_dev(const double* mu, const double* nu, const double* logmu, c
       if (r < 0) return r;
       its += (long long)o1[0];
       int r2 = full_sinkhorn_impl<double>(mu, nu, logmu, lognu, N, 0.5 * e_end, eps, lam, variant, maxit, err,
-                                          check_every, alpha, beta, out, d_eval, st, cerr);
+                                          check_every, alpha, beta, out, d_eval, st, cerr, true);
       out[0] += (double)its;
       return r2;
     }
     precision = eps < e_sw ? 1 : 0;
+    if (precision)   // mixed: the double stages take float exponentials of double exponents
+      return full_sinkhorn_impl<double>(mu, nu, logmu, lognu, N, eps_start, eps, lam, variant, maxit, err,
+                                        check_every, alpha, beta, out, d_eval, st, cerr, true);
   }
   if (precision)
     return full_sinkhorn_impl<double>(mu, nu, logmu, lognu, N, eps_start, eps, lam, variant, maxit, err,
