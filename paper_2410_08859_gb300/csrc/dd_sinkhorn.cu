@@ -421,7 +421,7 @@ constexpr int kNoAllocMaxN2 = 256 * 256;  // largest grid: N*N <= 65536 (N <= 25
 // (double-sized slots, also used for float), one N*N double slot holding two
 // float shadow arrays, 8 doubles of reductions and the input-status word.
 constexpr long long kNoAllocDoubles = 7LL * kNoAllocMaxN2 + 16;
-__device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
 
 constexpr int kMaxDevices = 64;
 double* g_noalloc_ptr[kMaxDevices] = {nullptr};
