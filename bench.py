@@ -27,7 +27,11 @@ import subprocess
 import sys
 import time
 
-import numpy as np
+# the CPU baseline (the FP64 oracle) is reported on one thread: keep BLAS to one
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
