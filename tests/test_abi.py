@@ -37,12 +37,17 @@ def test_default_params_and_error_strings():
     p = dd.domdec_default_params()
     assert p.err == 2e-5 and p.trunc_thr == 1e-15 and p.strategy == dd.STAGGERED
     assert p.basic_cell == 4 and p.precision == dd.FP32
+    # the paper's plain iteration by default: no translation step, no balancing
+    assert p.cell_ti == 0 and p.balance == 0 and p.cell_ctas == 0
+    assert dd.domdec_default_params(strategy="staggered_line").strategy == dd.STAGGERED_LINE == 5
     assert dd.error_string(dd.DOMDEC_EINVAL) == "invalid argument"
     assert "arena" in dd.error_string(dd.DOMDEC_EARENA)
 
 
 @pytest.mark.parametrize("bad", [dict(N=30, s=4), dict(N=32, s=0), dict(N=32, s=4, eps=-1.0),
-                                 dict(N=32, s=4, lam=float("inf")), dict(N=32, s=4, strategy=7)])
+                                 dict(N=32, s=4, lam=float("inf")), dict(N=32, s=4, strategy=7),
+                                 dict(N=32, s=4, strategy=6), dict(N=32, s=4, cell_ctas=3),
+                                 dict(N=32, s=4, cell_ti=2), dict(N=32, s=4, balance=-1)])
 def test_init_rejects_bad_parameters_before_touching_the_device(bad):
     import numpy as np
 
