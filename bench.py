@@ -52,6 +52,20 @@ def peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def aggregate_ranks(units, ms, world, device):
+    """Whole-job figures of N replicas: units summed over ranks, time = the
+    slowest rank's (max).  world == 1: the local values."""
+    if world <= 1:
+        return float(units), float(ms)
+    import torch
+    import torch.distributed as dist
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u[0]), float(t[0])
+
+
 def workload_inputs(rank=0, name="blobs256"):
     from paper_2410_08859_gb300 import inputs
     mu, nu, spec = inputs.workload(name, instance=rank)
@@ -479,14 +493,7 @@ def main():
     cert = g.pd_gap()
     g.close()
 
-    tot = torch.tensor([float(iters), t_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        it_t = torch.tensor([float(iters)], dtype=torch.float64, device="cuda")
-        t_t = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(it_t, op=dist.ReduceOp.SUM)
-        dist.all_reduce(t_t, op=dist.ReduceOp.MAX)
-        tot = torch.stack([it_t[0], t_t[0]])
-    iters_all, t_max = float(tot[0]), float(tot[1])
+    iters_all, t_max = aggregate_ranks(float(iters), t_ms, world, "cuda")
     value = iters_all / (t_max / 1000.0)
 
     if rank != 0:
