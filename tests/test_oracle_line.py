@@ -78,3 +78,23 @@ def test_line_run_monotone_and_converges():
     # grid; the distance to the optimum shrinks by over 100x in 30 sweeps
     assert scores[-1] >= Eopt - 1e-12 * abs(Eopt)
     assert scores[-1] - Eopt <= 1e-2 * (scores[0] - Eopt)
+
+
+def test_staggered_line_never_worse_than_staggered_swift_step():
+    """On each staggered sub-batch the line search's step decreases the
+    tracked score at least as much as the swift choice would (both evaluated
+    on the same cell solutions)."""
+    N, s = 16, 2
+    mu, nu = inputs.mixture_small(N=N, seed=1206)
+    geo = odd.Geometry(N, s)
+    st = odd.init_product(geo, mu.ravel(), nu.ravel(), (1.0 / N) ** 2, 1.0)
+    odd.run(st, 1, strategy="safe")
+    for batch in odd.batches_of(st, "B", "staggered_line"):
+        probs = [odd.cell_problem(st, c) for c in batch]
+        sols = [None if p is None else odd.solve_cell(st, c, p) for c, p in zip(batch, probs)]
+        th_line, E0, Eg, Es = odd.get_weights(st, batch, probs, sols, "staggered_line", 0.0)
+        th_swift = odd.get_weights(st, batch, probs, sols, "staggered", 0.0)[0]
+        E_line = score_at(st, batch, probs, sols, th_line)
+        E_swift = score_at(st, batch, probs, sols, th_swift)
+        assert E_line <= E_swift + 1e-13 * abs(E_swift)
+        odd.apply_step(st, batch, probs, sols, th_line)
