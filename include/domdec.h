@@ -46,6 +46,10 @@ extern "C" {
 #define DOMDEC_EARENA   -5   /* the box arena overflowed (raise arena_factor) */
 #define DOMDEC_ESTATE   -6   /* the handle is in an error state */
 #define DOMDEC_ENOLIB   -7   /* reserved for bindings: library not loaded */
+#define DOMDEC_EEMPTY   -8   /* a composite cell has no Y-support left: every member basic-cell marginal
+                                fell below trunc_thr (Section 5.3 truncation); raise the masses or lower trunc_thr */
+#define DOMDEC_ENONFINITE -9 /* a cell solve produced a non-finite value (NaN/Inf in the potentials or the
+                                stopping gap) */
 
 #define DOMDEC_STAGGERED 0   /* swift on each of the 4 staggered sub-batches (Section 4.4) */
 #define DOMDEC_SWIFT     1   /* swift on the whole partition (Proposition 4.3, item 2) */
@@ -147,7 +151,10 @@ int domdec_set_eps(domdec_t h, double eps);
  * iterations per cell. */
 int domdec_set_tolerance(domdec_t h, double err);
 
-/* Wait for the stream and report device-side errors / warnings.  Synchronises. */
+/* Wait for the stream and report device-side errors / warnings: DOMDEC_WNOTCONV
+ * if a cell solve stopped at maxit since the previous domdec_sync of this
+ * handle (or since domdec_init), DOMDEC_EEMPTY / DOMDEC_ENONFINITE / ... for
+ * errors (sticky).  Synchronises. */
 int domdec_sync(domdec_t h);
 
 /* out[0] tracked score E_hat = sum_i (C_i + eps H_i) + lam KL(P_X|mu) + lam KL(P_Y|nu)
@@ -296,15 +303,19 @@ void domdec_batch_free(domdec_batch_t b);
  * Same arguments and results as domdec_full_sinkhorn, except:
  *  - mu, nu (N*N, > 0), alpha and beta (N*N outputs, also the iteration state)
  *    must be DEVICE pointers of the current device; beta_in may be NULL
- *    (start from 0), equal to beta, or another device pointer;
+ *    (start from 0), equal to beta, or another device pointer.  Each pointer
+ *    is checked with cudaPointerGetAttributes before any work is enqueued:
+ *    host memory (pinned or pageable) or memory of another device returns
+ *    DOMDEC_EINVAL;
  *  - precision must be DOMDEC_FP32 or DOMDEC_FP64;
  *  - N*N must not exceed 65536 (N <= 256): larger grids return DOMDEC_ETOOBIG.
  * It calls no cudaMalloc, cudaFree or allocating library routine: all working
  * arrays live in one static device array of about 3.7 MB that every GPU which
- * loads the library keeps until the process exits.  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress) and
- * caches it; make that first call before any stream capture on the device.
- * All calls share the one array, which keeps the last call's contents (the
+ * loads the library keeps until the process exits.  Every call looks up that
+ * array's address in the current context (cudaGetSymbolAddress, which
+ * allocates nothing), so a cudaDeviceReset or another context of the same
+ * device between calls is handled; the first call in a context loads the
+ * module, so make it before any stream capture.  All calls share the one array, which keeps the last call's contents (the
  * status word it needs cleared is reset at the start of each call): calls that
  * overlap on the GPU -- from several streams or host threads -- race and
  * must be serialised by the caller.  Synchronises. */
@@ -313,6 +324,19 @@ int domdec_full_sinkhorn_noalloc(const double* mu, const double* nu, int N, doub
                                  int maxit, double err, int check_every,
                                  const double* beta_in, double* alpha, double* beta,
                                  double out[4], void* stream);
+
+/* Measurement helper (the paper has no counterpart): throughput probes that
+ * give the roofline denominators of the cell kernel on the current device.
+ * Runs, on all SMs, one kernel of independent ex2.approx.ftz.f32 (the
+ * exponential of every log-sum-exp term) and one of independent FP32 FFMA
+ * chains, `iters` loop passes of 16 operations per thread, each launched
+ * twice with the second launch timed by CUDA events on `stream`.
+ * out[0] ex2/s, out[1] ex2 per SM per clock, out[2] SM clock (MHz, from
+ * clock64 against the global timer inside the ex2 kernel), out[3] FFMA/s,
+ * out[4] FFMA per SM per clock, out[5] SM clock of the FFMA kernel,
+ * out[6] SM count, out[7] blocks launched.  Allocates a few KB with
+ * cudaMallocAsync; synchronises. */
+int domdec_probe_peaks(int iters, double out[8], void* stream);
 
 #ifdef __cplusplus
 }

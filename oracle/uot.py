@@ -156,26 +156,3 @@ def full_sinkhorn(mu, nu, C, eps, lam, err=2e-5, maxit=10000, beta0=None,
         if it >= min_iters and gap <= tol:
             break
     return alpha, beta, it, gap
-
-
-def eps_schedule(eps_start, eps_end):
-    """Geometric halving eps_start, eps_start/2, ... down to eps_end (the last
-    stage is exactly eps_end); the paper's eps-scaling halves eps between
-    stages (Section 5.3, 'Multi-scale and eps-scaling')."""
-    out = []
-    e = float(eps_start)
-    while e > eps_end * (1 + 1e-12):
-        out.append(e)
-        e *= 0.5
-    out.append(float(eps_end))
-    return out
-
-
-def sinkhorn_eps_scaling(mu, nu, C, eps_list, lam, err=2e-5, maxit=10000):
-    """Run full_sinkhorn over a list of eps values, warm-starting beta."""
-    beta = None
-    total = 0
-    for e in eps_list:
-        alpha, beta, it, gap = full_sinkhorn(mu, nu, C, e, lam, err, maxit, beta)
-        total += it
-    return alpha, beta, total, gap

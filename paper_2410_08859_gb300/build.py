@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libdomdec.so")
-SOURCES = ["dd_cell.cu", "dd_sweep.cu", "dd_sinkhorn.cu", "dd_grad.cu", "dd_api.cu"]
+SOURCES = ["dd_cell.cu", "dd_sweep.cu", "dd_sinkhorn.cu", "dd_grad.cu", "dd_api.cu", "dd_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

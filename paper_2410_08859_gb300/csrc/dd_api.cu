@@ -79,6 +79,7 @@ struct domdec_s {
   double* h_pinned = nullptr;   // 64 doubles
   long long sweeps = 0;
   long long slot = 0;
+  unsigned long long maxit_seen = 0;  // maxit-cell counter at the previous domdec_sync
   int sticky = 0;
   int last_batch = 0;
   int max_pairs = 0;  // co-resident 2-CTA clusters of the cell kernel
@@ -160,7 +161,8 @@ int read_status(domdec_s* h) {
   if (st & ST_BADINPUT) return fail(h, DOMDEC_EINVAL);
   if (st & ST_TOOBIG) return fail(h, DOMDEC_ETOOBIG);
   if (st & ST_ARENA) return fail(h, DOMDEC_EARENA);
-  if (st & (ST_EMPTY | ST_NONFINITE)) return fail(h, DOMDEC_ECUDA);
+  if (st & ST_EMPTY) return fail(h, DOMDEC_EEMPTY);
+  if (st & ST_NONFINITE) return fail(h, DOMDEC_ENONFINITE);
   return DOMDEC_OK;
 }
 
@@ -302,11 +304,13 @@ const char* domdec_error_string(int code) {
     case DOMDEC_WNOTCONV: return "warning: some cell solves stopped at maxit";
     case DOMDEC_EINVAL: return "invalid argument";
     case DOMDEC_ENOMEM: return "device allocation failed";
-    case DOMDEC_ECUDA: return "CUDA runtime error or non-finite values on the device";
+    case DOMDEC_ECUDA: return "CUDA runtime error";
     case DOMDEC_ETOOBIG: return "a cell Y-box exceeds the kernel's shared-memory capacity (max_ny)";
     case DOMDEC_EARENA: return "box arena overflow";
     case DOMDEC_ESTATE: return "handle is in an error state";
     case DOMDEC_ENOLIB: return "library not loaded";
+    case DOMDEC_EEMPTY: return "a composite cell has no Y-support left after truncation";
+    case DOMDEC_ENONFINITE: return "a cell solve produced a non-finite value";
     default: return "unknown error";
   }
 }
@@ -531,7 +535,10 @@ int domdec_sync(domdec_t h) {
   if (rc) return rc;
   unsigned long long c[NCOUNT];
   if (cudaMemcpy(c, h->S.counters, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess) return fail(h, DOMDEC_ECUDA);
-  return c[2] ? DOMDEC_WNOTCONV : DOMDEC_OK;
+  // the warning covers the cell solves since the previous domdec_sync only
+  const bool notconv = c[2] > h->maxit_seen;
+  h->maxit_seen = c[2];
+  return notconv ? DOMDEC_WNOTCONV : DOMDEC_OK;
 }
 
 int domdec_score(domdec_t h, double out[6]) {

@@ -897,6 +897,8 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbat
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int crank = csize > 1 ? (int)cg::this_cluster().block_rank() : 0;
   const int cidx = blockIdx.x / csize;
+  // the partner CTA must have started before its shared memory is written
+  if (csize > 1) cg::this_cluster().sync();
   cell_solve_body<R>(S, cells[begin + cidx], cidx, nbatch, csize, crank, smem_raw);
 }
 
@@ -915,6 +917,8 @@ k_cell_solve_multi(const DevState* __restrict__ states, const CellRef* __restric
     if (csize > 1) cg::this_cluster().sync();
     else __syncthreads();
   };
+  // the partner CTA must have started before its shared memory is written
+  if (csize > 1) cg::this_cluster().sync();
   for (;;) {
     if (crank == 0 && threadIdx.x == 0) {
       int j = (int)atomicAdd(queue, 1u);

@@ -413,8 +413,6 @@ int full_sinkhorn_dev(const double* mu, const double* nu, const double* logmu, c
 // cudaMalloc/cudaFree.  For them the working arrays live in one file-scope
 // device array of fixed size, reserved on every GPU that loads the library
 // for the life of the process.
-#include <mutex>
-
 namespace {
 constexpr int kNoAllocMaxN2 = 256 * 256;  // largest grid: N*N <= 65536 (N <= 256)
 // log mu, log nu (N*N doubles each), four N*N work arrays of the log-sum-exp
@@ -423,26 +421,30 @@ constexpr int kNoAllocMaxN2 = 256 * 256;  // largest grid: N*N <= 65536 (N <= 25
 constexpr long long kNoAllocDoubles = 7LL * kNoAllocMaxN2 + 16;
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
 
-constexpr int kMaxDevices = 64;
-double* g_noalloc_ptr[kMaxDevices] = {nullptr};
-std::mutex g_noalloc_mu;
-
-// Device address of the scratch array for the current device (host code must
-// not use the symbol itself: it is only a host-side stand-in).
+// Device address of the scratch array in the current device's context (host
+// code must not use the symbol itself: it is only a host-side stand-in).  It
+// is looked up on every call (no allocation, no cache), so it stays right
+// after a cudaDeviceReset or under another context of the same device.
 cudaError_t noalloc_scratch(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_noalloc_ptr[dev] = static_cast<double*>(p);
-  }
-  *out = g_noalloc_ptr[dev];
+  *out = static_cast<double*>(p);
   return cudaSuccess;
+}
+
+// True if p is device (or managed) memory that the current device can use
+// directly; host memory, pinned or pageable, is rejected.
+bool is_current_device_ptr(const void* p) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 template <typename R>
@@ -520,6 +522,12 @@ int domdec_full_sinkhorn_noalloc(const double* mu, const double* nu, int N, doub
       maxit < 1)
     return DOMDEC_EINVAL;
   if ((long long)N * N > kNoAllocMaxN2) return DOMDEC_ETOOBIG;
+  // the kernels read mu, nu, beta_in and write alpha, beta directly: each must be
+  // memory of the current device (a host array would fault or, where the GPU can
+  // reach host memory, be used silently)
+  if (!is_current_device_ptr(mu) || !is_current_device_ptr(nu) || !is_current_device_ptr(alpha) ||
+      !is_current_device_ptr(beta) || (beta_in && !is_current_device_ptr(beta_in)))
+    return DOMDEC_EINVAL;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   double* base = nullptr;
   if (noalloc_scratch(&base) != cudaSuccess) return DOMDEC_ECUDA;

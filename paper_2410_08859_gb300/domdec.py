@@ -17,6 +17,7 @@ from . import build as _build
 DOMDEC_OK, DOMDEC_WNOTCONV = 0, 1
 DOMDEC_EINVAL, DOMDEC_ENOMEM, DOMDEC_ECUDA = -1, -2, -3
 DOMDEC_ETOOBIG, DOMDEC_EARENA, DOMDEC_ESTATE, DOMDEC_ENOLIB = -4, -5, -6, -7
+DOMDEC_EEMPTY, DOMDEC_ENONFINITE = -8, -9
 STAGGERED, SWIFT, SAFE, GREEDY, LINE, STAGGERED_LINE = 0, 1, 2, 3, 4, 5
 STRATEGIES = {"staggered": STAGGERED, "swift": SWIFT, "safe": SAFE, "greedy": GREEDY, "line": LINE,
               "staggered_line": STAGGERED_LINE}
@@ -87,6 +88,7 @@ _SIGS = {
     "domdec_batch_sync": (_I, [_P]),
     "domdec_batch_autotune": (_I, [_P, ctypes.POINTER(ctypes.c_int)]),
     "domdec_batch_free": (None, [_P]),
+    "domdec_probe_peaks": (_I, [_I, _DP, _P]),
 }
 
 
@@ -275,7 +277,16 @@ def domdec_full_sinkhorn_noalloc(mu, nu, N, eps, lam, alpha, beta, eps_start=Non
                                  variant=SINKHORN_SEPARABLE, precision=FP64, maxit=10000, err=2e-5,
                                  check_every=10, beta_in=None, stream=None):
     """Allocation-free global Sinkhorn: device tensors only, N <= 256 (see
-    include/domdec.h).  Returns (iterations, PD/lam, primal, dual, rc)."""
+    include/domdec.h).  Returns (iterations, PD/lam, primal, dual, rc).
+    NumPy arrays and tensors that do not live on the current CUDA device are
+    rejected here, before the library is called (the C entry point rejects
+    them too)."""
+    import torch
+    for name, a in (("mu", mu), ("nu", nu), ("alpha", alpha), ("beta", beta), ("beta_in", beta_in)):
+        if a is None and name == "beta_in":
+            continue
+        if not (isinstance(a, torch.Tensor) and a.is_cuda and a.device.index == torch.cuda.current_device()):
+            raise TypeError(f"domdec_full_sinkhorn_noalloc: {name} must be a tensor on the current CUDA device")
     out = (ctypes.c_double * 4)()
     n = N * N
     rc = lib().domdec_full_sinkhorn_noalloc(_ptr(mu, n), _ptr(nu, n), int(N),
@@ -308,6 +319,16 @@ def domdec_gradients(h, N, precision=FP64, grad_mu=None, grad_nu=None, grad_x=No
     _check(lib().domdec_gradients(h, int(precision), _ptr(grad_mu, n, True), _ptr(grad_nu, n, True),
                                   _ptr(grad_x, 2 * n, True), out, _ptr(beta, n, True)), "domdec_gradients")
     return list(out)
+
+
+def domdec_probe_peaks(iters=20000, stream=None):
+    """MUFU ex2 and FFMA throughput of the current device: dict with ex2/s,
+    ex2 per SM per clock, FFMA/s, FFMA per SM per clock, SM clocks, SM count."""
+    out = (ctypes.c_double * 8)()
+    _check(lib().domdec_probe_peaks(int(iters), out, _stream_ptr(stream)), "domdec_probe_peaks")
+    return {"ex2_per_s": out[0], "ex2_per_sm_clk": out[1], "ex2_sm_mhz": out[2],
+            "ffma_per_s": out[3], "ffma_per_sm_clk": out[4], "ffma_sm_mhz": out[5],
+            "sms": int(out[6]), "blocks": int(out[7])}
 
 
 class DomDecBatch:

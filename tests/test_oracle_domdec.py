@@ -148,6 +148,47 @@ def test_converges_to_global_optimum(strategy):
     assert 0 <= gap < 1e-7
 
 
+def test_marginal_errors_closed_forms_on_the_product_plan():
+    """Section 5.3 ('Solution quality') measures |P_X - e^{-alpha/lam} mu|_1 and
+    |P_Y - e^{-beta/lam} nu|_1.  On the product plan pi = mu x nu the marginals
+    are P_X = |nu| mu and P_Y = |mu| nu, so for constant potentials alpha = a,
+    beta = b both errors have closed forms: |mu| ||nu| - e^{-a/lam}| and
+    |nu| ||mu| - e^{-b/lam}|; b = -lam log|mu| makes the Y error vanish."""
+    N, s = 8, 2
+    geo = domdec.Geometry(N, s)
+    mu, nu = inputs.mixture_small(N=N, seed=1013, masses=(0.8, 1.3))
+    mu, nu = mu.ravel(), nu.ravel()
+    lam = 0.5
+    st = domdec.init_product(geo, mu, nu, (1.0 / N) ** 2, lam, thr=0.0)
+    M, Nn = mu.sum(), nu.sum()
+    for a, b in ((0.0, 0.0), (0.3, 0.7), (-0.2, -lam * np.log(M))):
+        st.alpha = np.full(geo.n, a)
+        ex, ey = domdec.marginal_errors(st, np.full(geo.n, b))
+        assert abs(ex - M * abs(Nn - np.exp(-a / lam))) <= 1e-13
+        assert abs(ey - Nn * abs(M - np.exp(-b / lam))) <= 1e-13
+    assert ey <= 1e-13
+
+
+def test_marginal_errors_vanish_at_the_optimum():
+    """First-order optimality (Section 4, the marginal conditions of the
+    primal-dual pair): at the minimiser P_X = e^{-alpha/lam} mu and
+    P_Y = e^{-beta/lam} nu, so both errors fall from O(1) at the product plan
+    towards 0 as DomDec converges (beta = beta* of one global Y-half)."""
+    N, s = 8, 2
+    geo = domdec.Geometry(N, s)
+    mu, nu = small_problem(N, seed=1014)
+    eps, lam = (2.0 / N) ** 2, 1.0
+    st = domdec.init_product(geo, mu, nu, eps, lam, thr=1e-30)
+    e0 = domdec.marginal_errors(st, domdec.y_half_global(st, st.alpha))
+    assert min(e0) > 1e-2 * mu.sum()
+    errs = []
+    for n_sweeps, err in ((4, 1e-6), (12, 1e-13)):
+        domdec.run(st, n_sweeps, "staggered", tau=0.0, err=err, maxit=6000)
+        errs.append(domdec.marginal_errors(st, domdec.pd_certificate(st)[3]))
+    assert errs[1][0] < errs[0][0] and errs[1][1] < errs[0][1]
+    assert max(errs[1]) < 1e-6 * mu.sum()
+
+
 def test_certificate_weak_duality_along_iterations():
     geo = domdec.Geometry(16, 2)
     mu, nu = small_problem(16, seed=1007)

@@ -57,3 +57,35 @@ def test_noalloc_rejects_grids_beyond_its_capacity(env):
     with pytest.raises(dd.DomDecError) as e:
         dd.domdec_full_sinkhorn_noalloc(mu, mu, N, 1e-3, 1.0, a, b, maxit=1)
     assert e.value.code == dd.DOMDEC_ETOOBIG
+
+
+def test_noalloc_rejects_host_memory_before_any_launch(env):
+    """Host arrays never reach the kernels: the binding raises on NumPy input
+    and on CPU tensors, and the C entry point itself returns DOMDEC_EINVAL for
+    host pointers (pageable and pinned) before it enqueues anything."""
+    import ctypes
+    torch, dd = env
+    N = 16
+    mu, nu = inputs.mixture_small(N=N, seed=1012)
+    mu, nu = mu.ravel().copy(), nu.ravel().copy()
+    a = torch.empty(N * N, dtype=torch.float64, device="cuda")
+    b = torch.empty_like(a)
+    with pytest.raises(TypeError):
+        dd.domdec_full_sinkhorn_noalloc(mu, nu, N, 1e-2, 1.0, a, b, maxit=1)
+    with pytest.raises(TypeError):
+        dd.domdec_full_sinkhorn_noalloc(torch.from_numpy(mu), torch.from_numpy(nu), N, 1e-2, 1.0, a, b, maxit=1)
+    mu_d = torch.from_numpy(mu).cuda()
+    nu_d = torch.from_numpy(nu).cuda()
+    pinned = torch.from_numpy(mu).pin_memory()
+    out = (ctypes.c_double * 4)()
+    L = dd.lib()
+    stream = torch.cuda.current_stream().cuda_stream
+    for m_ptr, n_ptr, a_ptr in ((mu.ctypes.data, nu_d.data_ptr(), a.data_ptr()),
+                                (mu_d.data_ptr(), nu_d.data_ptr(), mu.ctypes.data),
+                                (pinned.data_ptr(), nu_d.data_ptr(), a.data_ptr())):
+        a.fill_(7.0)
+        rc = L.domdec_full_sinkhorn_noalloc(m_ptr, n_ptr, N, 1e-2, 1e-2, 1.0, 1, 1, 1, 1e-6, 1, None,
+                                            a_ptr, b.data_ptr(), out, stream)
+        torch.cuda.synchronize()
+        assert rc == dd.DOMDEC_EINVAL
+        assert bool((a == 7.0).all())   # nothing was written
