@@ -1,22 +1,30 @@
 #!/usr/bin/env python
 """Benchmark of the DomDec hot path on one GB300 (or N independent replicas).
 
-Workload (``blobs256``): 256 x 256 grids, mu and nu seeded mixtures of 5..20
-Gaussian blobs with mass ratio in [0.7, 1.5], squared-Euclidean cost, lam = 1,
-eps-scaling from 1 to (1/256)^2 (global Sinkhorn warm start down to
-2 (1/256)^2, then DomDec at (1/256)^2), basic cells 8 x 8, FP32 cell Sinkhorn,
-FP64 score and step size, staggered strategy (swift on each sub-batch, no leniency), cell tolerance 2e-5.
+Headline workload (``lognormal1024``): 1024 x 1024 grids, mu and nu seeded
+log-normal random fields (correlation length 0.05) of masses 1.0 / 1.2,
+squared-Euclidean cost, lam = 1, eps-scaling to (2/1024)^2 (global Sinkhorn
+warm start from eps = 1 down to 2 (2/1024)^2, then DomDec at (2/1024)^2),
+basic cells 16 x 16, FP32 cell Sinkhorn, FP64 score and step size, staggered
+strategy (swift on each sub-batch, no leniency), cell tolerance 2e-5.
 
-One step = one DomDec sweep over one partition (all staggered sub-batches:
-nu_{-J} gather, cell Sinkhorn, GetWeights, mixing and box refresh, arena
-compaction).  Metric: cell-iterations per second (one X-half + one Y-half on one
-composite cell).  Inputs are smaller than L2, so L2 is flushed (256 MB write)
-between timed steps, outside the timed events.
+One step = one DomDec sweep over one partition (all four staggered
+sub-batches: nu_{-J} gather, cell Sinkhorn, GetWeights, mixing and box
+refresh, arena compaction).  Metric: cell-iterations per second (one X-half
+plus one Y-half on one composite cell).  L2 is flushed (256 MB write) between
+timed steps, outside the timed events.
 
-Also reported: the roofline of the cell kernel (exp terms of its log-sum-exp
-passes against the MUFU ex2 rate), the time to a relative primal-dual gap of
-1e-5 against global Sinkhorn on the same GPU, an end-to-end number through the
-C ABI with host buffers, and the FP64 CPU oracle on a bounded sample.
+The same JSON line also carries: the roofline of the cell kernel (exp terms
+of its log-sum-exp passes against the MUFU ex2 rate measured on this GPU by
+domdec_probe_peaks), the GB/s of the decision / mixing / compaction kernels,
+an end-to-end number through the C ABI with host buffers (domdec_reset from
+pinned host memory + sweeps + score and marginals back), the FP64 CPU oracle
+on a bounded sample, and every other configuration of the benchmark plan:
+blobs256 at lam = 0.1, 1, 10, mix32 (FP64, DomDec against global Sinkhorn to a
+relative primal-dual gap of 1e-6), the time to a relative gap of 1e-5 on
+blobs256 (the paper's pipeline first), batch64 (64 problems in one
+persistent launch), grad512 (the backward pass) and the FP32-vs-FP64 error of
+each result.
 """
 from __future__ import annotations
 
@@ -38,13 +46,14 @@ sys.path.insert(0, ROOT)
 
 METRIC = "time to stated primal-dual gap and cell-iters/s vs full Sinkhorn on one GB300"
 UNIT = "cell-iters/s"
-N_SM = 152
-MUFU_PER_SM_CLK = 16      # ex2/lg2 results per SM per clock (4 per SM sub-partition)
 GAP_TARGET = 1e-5
-CELL_KERNEL_DRAM_BYTES = None   # capture of 4.03e6 bytes (profiles/) predates the balancing epilogue
+# dram read + write bytes of one cell-kernel launch from an ncu capture of the
+# current kernel in this configuration (profiles/); None: not captured since
+# the kernel last changed
+CELL_KERNEL_DRAM_BYTES = {}
 
 
-def peaks():
+def peaks_file():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return json.load(f), "measured"
@@ -66,25 +75,18 @@ def aggregate_ranks(units, ms, world, device):
     return float(u[0]), float(t[0])
 
 
-def workload_inputs(rank=0, name="blobs256"):
-    from paper_2410_08859_gb300 import inputs
-    mu, nu, spec = inputs.workload(name, instance=rank)
-    return mu.ravel().copy(), nu.ravel().copy(), spec
-
-
 class ClockSampler:
     """nvidia-smi clock / throttle samples during the timed region."""
 
-    def __init__(self, out_path=None):
+    def __init__(self):
         self.proc = None
-        self.path = out_path
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             dev = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0"
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={dev}", f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -116,40 +118,160 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def warm_start(dd, mu_d, nu_d, N, eps, lam, torch, quick=False, err=2e-5 / 4):
-    """Global Sinkhorn (separable; float for coarse eps, double for fine) from
-    eps = 1 down to 2 eps, at a quarter of the DomDec tolerance (Section 5.3
-    warm start).  quick: float only, at most 200 iterations per stage (profiling
-    runs, where only the shape of the DomDec state matters)."""
+def to_dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).ravel().copy()).cuda()
+
+
+def warm_start(dd, torch, mu_d, nu_d, N, eps, lam, precision=None, err=2e-5 / 4, maxit=4000):
+    """Global separable Sinkhorn from eps = 1 down to 2 eps at a quarter of the
+    cell tolerance (Section 5.3 warm start).  Returns (alpha, beta, seconds, iterations)."""
     a = torch.empty(N * N, dtype=torch.float64, device="cuda")
     b = torch.empty_like(a)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     it, gap, P, D, rc = dd.domdec_full_sinkhorn(mu_d, nu_d, N, 2 * eps, lam, eps_start=1.0,
                                                 variant=dd.SINKHORN_SEPARABLE,
-                                                precision=dd.FP32 if quick else dd.MIXED,
-                                                maxit=200 if quick else 4000, err=err, check_every=10,
-                                                alpha=a, beta=b)
+                                                precision=dd.MIXED if precision is None else precision,
+                                                maxit=maxit, err=err, check_every=10, alpha=a, beta=b)
     torch.cuda.synchronize()
     return a, b, time.perf_counter() - t0, it
 
 
-def sinkhorn_to_gap(dd, mu_d, nu_d, N, eps, lam, variant, precision, torch, max_rounds=6, maxit=3000):
-    """Global Sinkhorn with eps-scaling from 1 to eps, tightening the PD tolerance
-    until the relative gap (E - D)/|D| <= GAP_TARGET.  Returns (seconds, gap, iterations)."""
-    b = torch.zeros(N * N, dtype=torch.float64, device="cuda")
-    a = torch.empty_like(b)
-    err = 2e-5
+def timed_sweeps(dd, torch, g, steps, warmup, flush, sample_clocks=False):
+    """warmup untimed sweeps, then `steps` sweeps timed one by one with CUDA events
+    on the current stream (L2 flushed before each, outside the events).
+    Returns a dict of the timed region's figures."""
+    g.iterate(warmup)
+    g.sync()
+    g.kernel_times(reset=True)
+    st0 = g.stats()
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    sampler = ClockSampler() if sample_clocks else None
+    torch.cuda.synchronize()
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        g.iterate(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    rc = g.sync()
+    t_ms = sum(a.elapsed_time(b) for a, b in ev)
+    st1 = g.stats()
+    kms, kn = g.kernel_times(reset=True)
+    d = {k: st1[k] - st0[k] for k in ("cell_iters", "cell_solves", "lse_terms", "box_points", "maxit_cells",
+                                      "greedy_steps", "safe_steps")}
+    d.update(ms=t_ms, kms=kms, kn=kn, clocks=clocks, box_entries=st1["box_entries"], rc=rc,
+             max_ny=st1["max_ny"])
+    return d
+
+
+def roofline_of(d, pk, N, peaks_meas):
+    """Cell kernel against the measured MUFU ex2 rate; the other sweep kernels
+    against the measured HBM copy bandwidth (algorithmic bytes per launch)."""
+    k1_s = d["kms"][0] / 1e3
+    achieved = d["lse_terms"] / k1_s / 1e12 if k1_s > 0 else 0.0
+    peak = peaks_meas["ex2_per_s"] / 1e12
+    hbm = float(pk.get("hbm_gbs", 6800.0))
+    n = N * N
+    nsub = max(int(d["kn"][1]), 1)
+    # decide: P_X, mu, P_Y, nu, dP_Y read per pixel (8 B each), log nu where dP_Y != 0
+    dec_bytes = 5 * 8 * n
+    # apply: per Y-box point of the solved cells, per quadrant: old value, new value read,
+    # mixed value written (8 B each), plus dP_Y zeroed; P_X / P_Xnew mixed on the cells' pixels
+    pts = d["box_points"] / nsub
+    app_bytes = 4 * 3 * 8 * pts + 8 * pts + 3 * 8 * n / 4
+    # compaction: every live box entry read and written once per sweep
+    nsw = max(int(d["kn"][3]), 1)
+    cmp_bytes = 16 * d["box_entries"]
+
+    def gbs(b, ms, k):
+        return b / (ms / k / 1e3) / 1e9 if ms > 0 else 0.0
+
+    return {"bound": "alu", "kernel": "k_cell_solve<float>", "achieved": achieved, "peak": peak,
+            "unit": "Tex2/s", "frac": achieved / peak if peak > 0 else 0.0,
+            "traffic": CELL_KERNEL_DRAM_BYTES.get(N),
+            "peak_source": ("measured on this GPU (domdec_probe_peaks: ex2.approx.ftz.f32 chains on all "
+                            f"{peaks_meas['sms']} SMs): {peaks_meas['ex2_per_sm_clk']:.1f} ex2/SM/clk at "
+                            f"{peaks_meas['ex2_sm_mhz']:.0f} MHz"),
+            "kernel_share": float(d["kms"][0] / max(d["kms"].sum(), 1e-12)),
+            "kernel_ms": {"cell_solve": float(d["kms"][0]), "decide": float(d["kms"][1]),
+                          "apply": float(d["kms"][2]), "compact": float(d["kms"][3])},
+            "launches": {"cell_solve": int(d["kn"][0]), "decide": int(d["kn"][1]), "apply": int(d["kn"][2]),
+                         "compact": int(d["kn"][3])},
+            "hbm_kernels": {"peak_gb_s": hbm,
+                            "decide": {"bytes_per_launch": dec_bytes, "gb_s": gbs(dec_bytes, d["kms"][1], nsub)},
+                            "apply": {"bytes_per_launch": app_bytes, "gb_s": gbs(app_bytes, d["kms"][2], nsub)},
+                            "compact": {"bytes_per_launch": cmp_bytes,
+                                        "gb_s": gbs(cmp_bytes, d["kms"][3], nsw)}}}
+
+
+def sweep_config(dd, torch, name, lam, steps, warmup, flush, peaks_meas, pk, precision="fp32", cell_ctas=0):
+    """Warm start + timed sweeps of one workload at one lam (the throughput
+    figures of one configuration)."""
+    from paper_2410_08859_gb300 import inputs
+    mu, nu, spec = inputs.workload(name)
+    N, s, eps = spec["N"], spec["s"], spec["eps"]
+    mu_d, nu_d = to_dev(torch, mu), to_dev(torch, nu)
+    a0, b0, t_w, it_w = warm_start(dd, torch, mu_d, nu_d, N, eps, lam)
+    g = dd.DomDec(mu_d, nu_d, eps, lam, s, alpha0=a0, beta0=b0, eps_init=2 * eps, precision=precision,
+                  tau=0.0, err=2e-5, profile=1, cell_ctas=cell_ctas)
+    d = timed_sweeps(dd, torch, g, steps, warmup, flush)
+    cert = g.pd_gap()
+    g.close()
+    rl = roofline_of(d, pk, N, peaks_meas)
+    return {"value": d["cell_iters"] / (d["ms"] / 1e3), "unit": UNIT, "ms_per_sweep": d["ms"] / steps,
+            "mufu_frac": rl["frac"], "cell_kernel_share": rl["kernel_share"],
+            "mean_iters_per_solve": d["cell_iters"] / max(d["cell_solves"], 1), "max_ny": d["max_ny"],
+            "warm_start_s": t_w, "warm_start_iters": it_w, "rel_gap_after": float(cert[2])}
+
+
+def domdec_to_gap(dd, torch, mu_d, nu_d, N, s, eps, lam, a0, b0, t_warm, target, max_sweeps=60, fast=False,
+                  precision="fp32", err=1e-7, maxit=1000):
+    """DomDec from a warm start until the certificate's relative gap reaches
+    `target`.  fast = False: the paper's pipeline (plain cells, staggered swift);
+    fast = True: the extension of this library (translation step in the cells,
+    GetWeights_line on each staggered sub-batch; not in the paper)."""
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    tot = 0
+    g = dd.DomDec(mu_d, nu_d, eps, lam, s, alpha0=a0, beta0=b0, eps_init=2 * eps, precision=precision,
+                  tau=0.0, err=err, maxit=300 if fast else maxit, profile=1,
+                  cell_ti=1 if fast else 0, strategy="staggered_line" if fast else "staggered")
+    sweeps, rel = 0, float("inf")
+    while sweeps < max_sweeps:
+        g.iterate(2)
+        sweeps += 2
+        rel = g.pd_gap()[2]
+        if rel <= target:
+            break
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    st = g.stats()
+    kms, _ = g.kernel_times(reset=True)
+    g.close()
+    return {"s": t + t_warm, "warm_start_s": t_warm, "sweeps_s": t, "gap": rel, "sweeps": sweeps,
+            "cell_iters": st["cell_iters"], "cell_kernel_ms": float(kms[0]),
+            "cell_iters_per_s": st["cell_iters"] / max(kms[0] / 1e3, 1e-12), "lse_terms": int(st["lse_terms"])}
+
+
+def sinkhorn_to_gap(dd, torch, mu_d, nu_d, N, eps, lam, variant, precision, target, max_rounds=6, maxit=3000,
+                    err0=2e-5):
+    """Global Sinkhorn with eps-scaling from 1 to eps, tightening the PD
+    tolerance until the relative gap (E - D)/|D| <= target.
+    Returns (seconds, gap, iterations)."""
+    b = torch.zeros(N * N, dtype=torch.float64, device="cuda")
+    a = torch.empty_like(b)
+    err = err0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     it, gap, P, D, rc = dd.domdec_full_sinkhorn(mu_d, nu_d, N, eps, lam, eps_start=1.0, variant=variant,
                                                 precision=precision, maxit=maxit, err=err, check_every=10,
                                                 beta_in=b, alpha=a, beta=b)
-    tot += it
+    tot = it
     rel = (P - D) / abs(D)
     rounds = 0
-    while not rel <= GAP_TARGET and rounds < max_rounds:
+    while not rel <= target and rounds < max_rounds:
         err /= 4
         it, gap, P, D, rc = dd.domdec_full_sinkhorn(mu_d, nu_d, N, eps, lam, variant=variant,
                                                     precision=precision, maxit=maxit, err=err,
@@ -161,80 +283,109 @@ def sinkhorn_to_gap(dd, mu_d, nu_d, N, eps, lam, variant, precision, torch, max_
     return time.perf_counter() - t0, rel, tot
 
 
-def domdec_to_gap(dd, mu_d, nu_d, N, s, eps, lam, a0, b0, t_warm, torch, max_sweeps=60, fast=True):
-    """DomDec from the warm start until the certificate's relative gap reaches
-    GAP_TARGET; cell tolerance 1e-7 (the paper's 2e-5 stalls near 1.5e-4 on this
-    workload because inexact cell solves make greedy steps lose to the safe step),
-    every cell on a 2-CTA cluster.  fast: translation step in the cells,
-    GetWeights_line on each staggered sub-batch, at most 300 iterations per
-    cell solve; otherwise the paper's staggered swift with plain cells, at most
-    1000 iterations per cell solve."""
+def time_to_gap_blobs256(dd, torch, mu, nu, spec, lam):
+    """Time to a relative primal-dual gap of 1e-5 on blobs256, all from eps = 1
+    on the same GPU: DomDec as in the paper (headline), the library's extension
+    (labelled), global separable FP64 Sinkhorn (with and without the
+    translation step) and the dense FP32 Sinkhorn of the plain method."""
+    N, s, eps = spec["N"], spec["s"], spec["eps"]
+    mu_d, nu_d = to_dev(torch, mu), to_dev(torch, nu)
+    a0, b0, t_w, it_w = warm_start(dd, torch, mu_d, nu_d, N, eps, lam)
+    paper = domdec_to_gap(dd, torch, mu_d, nu_d, N, s, eps, lam, a0, b0, t_w, GAP_TARGET)
+    paper.update(what="warm start (global separable Sinkhorn, eps 1 -> 2 eps, PD/lam <= 5e-6 |mu|); "
+                      "plain cell Sinkhorn (tolerance 1e-7, at most 1000 iterations); staggered swift "
+                      "(Section 5.3)", warm_start_iters=it_w)
+    a_f, b_f, t_wf, it_wf = warm_start(dd, torch, mu_d, nu_d, N, eps, lam, err=2e-5)
+    ext = domdec_to_gap(dd, torch, mu_d, nu_d, N, s, eps, lam, a_f, b_f, t_wf, GAP_TARGET, fast=True)
+    ext.update(what="not in the paper: looser warm start (2e-5); cells with the translation step (at most 300 "
+                    "iterations); GetWeights_line per staggered sub-batch", warm_start_iters=it_wf)
+    t_sep, g_sep, i_sep = sinkhorn_to_gap(dd, torch, mu_d, nu_d, N, eps, lam, dd.SINKHORN_SEPARABLE, dd.FP64,
+                                          GAP_TARGET)
+    t_ti, g_ti, i_ti = sinkhorn_to_gap(dd, torch, mu_d, nu_d, N, eps, lam,
+                                       dd.SINKHORN_SEPARABLE | dd.SINKHORN_TI, dd.FP64, GAP_TARGET)
+    t_den, g_den, i_den = sinkhorn_to_gap(dd, torch, mu_d, nu_d, N, eps, lam, dd.SINKHORN_DENSE, dd.FP32,
+                                          GAP_TARGET, max_rounds=0, maxit=100)
+    return {"target_rel_gap": GAP_TARGET, "workload": "blobs256", "lam": lam,
+            "domdec_paper_pipeline": paper, "domdec_extension_pipeline": ext,
+            "sinkhorn_separable_fp64": {"s": t_sep, "gap": g_sep, "iters": i_sep},
+            "sinkhorn_separable_fp64_translation": {"s": t_ti, "gap": g_ti, "iters": i_ti,
+                                                    "what": "not in the paper (translation step)"},
+            "sinkhorn_dense_fp32": {"s": t_den, "gap": g_den, "iters": i_den,
+                                    "what": "plain method, eps-scaling stages capped at 100 iterations"}}
+
+
+def mix32_fp64(dd, torch):
+    """Config 1: 32 x 32 Gaussian mixtures, FP64, pi0 = mu x nu; DomDec and the
+    global separable Sinkhorn to a relative primal-dual gap of 1e-6."""
+    from paper_2410_08859_gb300 import inputs
+    mu, nu, spec = inputs.workload("mix32")
+    N, s, eps, lam = spec["N"], spec["s"], spec["eps"], spec["lam"]
+    mu_d, nu_d = to_dev(torch, mu), to_dev(torch, nu)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    g = dd.DomDec(mu_d, nu_d, eps, lam, s, alpha0=a0, beta0=b0, eps_init=2 * eps, precision="fp32",
-                  tau=0.0, err=1e-7, maxit=300 if fast else 1000, cell_ctas=2, profile=1,
-                  cell_ti=1 if fast else 0, strategy="staggered_line" if fast else "staggered")
+    g = dd.DomDec(mu_d, nu_d, eps, lam, s, precision="fp64", tau=0.0, err=1e-10, maxit=20000)
     sweeps, rel = 0, float("inf")
-    while sweeps < max_sweeps:
+    while sweeps < 200:
         g.iterate(2)
         sweeps += 2
-        cert = g.pd_gap()
-        rel = cert[2]
-        if rel <= GAP_TARGET:
+        rel = g.pd_gap()[2]
+        if rel <= 1e-6:
             break
     torch.cuda.synchronize()
-    t = time.perf_counter() - t0
-    st = g.stats()
-    kms, _ = g.kernel_times(reset=True)
+    t_dd = time.perf_counter() - t0
+    its = g.stats()["cell_iters"]
     g.close()
-    return t + t_warm, t, rel, sweeps, st["cell_iters"], float(kms[0]), int(st["lse_terms"])
+    t_sk, g_sk, i_sk = sinkhorn_to_gap(dd, torch, mu_d, nu_d, N, eps, lam, dd.SINKHORN_SEPARABLE, dd.FP64, 1e-6,
+                                       max_rounds=8, maxit=20000, err0=1e-6)
+    return {"N": N, "s": s, "eps": eps, "lam": lam, "precision": "fp64", "target_rel_gap": 1e-6,
+            "domdec": {"s": t_dd, "gap": rel, "sweeps": sweeps, "cell_iters": its},
+            "sinkhorn_separable_fp64": {"s": t_sk, "gap": g_sk, "iters": i_sk}}
 
 
-def oracle_sample(max_seconds=20.0, sweeps=None, maxit=None):
-    """The FP64 oracle on a bounded sample of the workload: the same blob
-    distribution and cell geometry (s = 8, composite cells of 16 x 16 pixels,
-    eps = h^2) on a 32 x 32 grid from the product plan; whole sweeps are timed
-    until max_seconds.  Returns (cell-iters/s, description, cell-iters, seconds)."""
-    from oracle import domdec as odd
+def fp32_vs_fp64(dd, torch, name, lam, sweeps=4):
+    """The same sweeps from the same warm start with FP32 and with FP64 cell
+    arithmetic: relative difference of the tracked score, L1 differences of
+    P_X and P_Y relative to the mass, max difference of alpha relative to its
+    magnitude, and whether the step-size decisions agree."""
     from paper_2410_08859_gb300 import inputs
-    N, s = 32, 8
-    mu, nu = inputs.mixture_blobs(N=N, seed=2000)
-    mu, nu = mu.ravel(), nu.ravel()
-    geo = odd.Geometry(N, s)
-    st = odd.init_product(geo, mu, nu, (1.0 / N) ** 2, 1.0)
-    t0 = time.perf_counter()
-    its, k = 0, 0
-    while True:
-        lg = odd.sweep(st, "AB"[k % 2], "staggered", tau=0.005, err=2e-5, maxit=maxit or 2000)
-        its += sum(sum(r["iters"]) for r in lg)
-        k += 1
-        el = time.perf_counter() - t0
-        if (sweeps is not None and k >= sweeps) or (sweeps is None and el >= max_seconds):
-            break
-    desc = (f"oracle (NumPy FP64, 1 thread) DomDec sweeps on blobs 32x32, s=8 "
-            f"(composite cells 16x16 = the workload's cell size), eps=h^2, lam=1, pi0=mu x nu; "
-            f"{k} sweeps, {its} cell-iterations in {el:.1f} s")
-    return its / el, desc, its, el
+    mu, nu, spec = inputs.workload(name)
+    N, s, eps = spec["N"], spec["s"], spec["eps"]
+    mu_d, nu_d = to_dev(torch, mu), to_dev(torch, nu)
+    a0, b0, _, _ = warm_start(dd, torch, mu_d, nu_d, N, eps, lam)
+    res = {}
+    for prec in ("fp32", "fp64"):
+        g = dd.DomDec(mu_d, nu_d, eps, lam, s, alpha0=a0, beta0=b0, eps_init=2 * eps, precision=prec, tau=0.0,
+                      err=2e-5)
+        g.iterate(sweeps)
+        g.sync()
+        res[prec] = (g.score()[0], *g.marginals(), g.duals(), g.decisions()[:, 3], g.pd_gap()[2])
+        g.close()
+    s32, s64 = res["fp32"], res["fp64"]
+    mass = float(mu.sum())
+    return {"workload": name, "lam": lam, "sweeps": sweeps,
+            "score_rel": abs(s32[0] - s64[0]) / abs(s64[0]),
+            "PX_l1_rel": float(np.abs(s32[1] - s64[1]).sum() / mass),
+            "PY_l1_rel": float(np.abs(s32[2] - s64[2]).sum() / mass),
+            "alpha_max_rel": float(np.abs(s32[3] - s64[3]).max() / (1 + np.abs(s64[3]).max())),
+            "decisions_equal": bool(np.array_equal(s32[4], s64[4])),
+            "rel_gap_fp32": float(s32[5]), "rel_gap_fp64": float(s64[5])}
 
 
-def run_batch(args, dd, torch):
-    """Many-instance batching: 64 independent problems (sides from {64, 128,
-    256, 512}, eps = (2/n)^2, lam in {0.5, 1, 5}) swept together, each warm-
-    started by global Sinkhorn down to 2 eps; against the same problems swept
-    one after another with single handles."""
+def run_batch(dd, torch, steps, warmup, peaks_meas):
+    """Many-instance batching (config 4): 64 independent problems (sides from
+    {64, 128, 256, 512}, eps = (2/n)^2, lam in {0.5, 1, 5}) swept together in
+    one persistent launch per staggered sub-batch, each warm-started by
+    global Sinkhorn (float, 2e-5) down to 2 eps; against the same problems
+    swept one after another with single handles."""
     from paper_2410_08859_gb300 import inputs
     probs = inputs.batch_instances(64)
     t0 = time.perf_counter()
     handles_b, handles_s = [], []
     for p in probs:
         N = p["N"]
-        mu_d = torch.from_numpy(p["mu"].ravel().copy()).cuda()
-        nu_d = torch.from_numpy(p["nu"].ravel().copy()).cuda()
-        a = torch.empty(N * N, dtype=torch.float64, device="cuda")
-        b = torch.empty_like(a)
-        dd.domdec_full_sinkhorn(mu_d, nu_d, N, 2 * p["eps"], p["lam"], eps_start=1.0,
-                                variant=dd.SINKHORN_SEPARABLE, precision=dd.MIXED, maxit=1000, err=2e-5,
-                                check_every=20, alpha=a, beta=b)
+        mu_d, nu_d = to_dev(torch, p["mu"]), to_dev(torch, p["nu"])
+        a, b, _, _ = warm_start(dd, torch, mu_d, nu_d, N, p["eps"], p["lam"], precision=dd.FP32, err=2e-5,
+                                maxit=1000)
         for lst in (handles_b, handles_s):
             lst.append(dd.DomDec(mu_d, nu_d, p["eps"], p["lam"], 8, alpha0=a, beta0=b, eps_init=2 * p["eps"],
                                  precision="fp32", tau=0.0, err=2e-5, spill_slots=32))
@@ -242,31 +393,28 @@ def run_batch(args, dd, torch):
     t_warm = time.perf_counter() - t0
     B = dd.DomDecBatch(handles_b)
     chosen = B.autotune()
-    B.iterate(args.warmup)
+    B.iterate(warmup)
     B.sync()
     it0 = sum(h.stats()["cell_iters"] for h in handles_b)
     lt0 = sum(h.stats()["lse_terms"] for h in handles_b)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record()
-    B.iterate(args.steps)
+    B.iterate(steps)
     e1.record()
     torch.cuda.synchronize()
     B.sync()
     t_b = e0.elapsed_time(e1)
     it_b = sum(h.stats()["cell_iters"] for h in handles_b) - it0
     lt_b = sum(h.stats()["lse_terms"] for h in handles_b) - lt0
-    pk, _ = peaks()
-    peak = N_SM * MUFU_PER_SM_CLK * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
-    # the same problems, one handle after another
     for h in handles_s:
-        h.iterate(2 + args.warmup)
+        h.iterate(2 + warmup)
         h.sync()
     it0 = sum(h.stats()["cell_iters"] for h in handles_s)
     torch.cuda.synchronize()
     e0.record()
     for h in handles_s:
-        h.iterate(args.steps)
+        h.iterate(steps)
     e1.record()
     torch.cuda.synchronize()
     for h in handles_s:
@@ -276,25 +424,18 @@ def run_batch(args, dd, torch):
     B.close()
     for h in handles_b + handles_s:
         h.close()
-    sides = sorted(set(p["N"] for p in probs))
-    line = {"metric": METRIC, "value": it_b / (t_b / 1000.0), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t_b / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "batch64", "instances": len(probs), "sides": sides, "basic_cell": 8,
-                       "eps": "(2/n)^2", "lam": "{0.5, 1, 5}", "cell_ctas_autotuned": chosen,
-                       "l2": "state of 64 instances exceeds L2 (no flush)"},
-            "sequential_single_handles": {"value": it_s / (t_s / 1000.0), "unit": UNIT,
-                                          "ms_per_step": t_s / args.steps},
+    peak = peaks_meas["ex2_per_s"] / 1e12
+    return {"value": it_b / (t_b / 1000.0), "unit": UNIT, "ms_per_sweep": t_b / steps, "instances": len(probs),
+            "sides": sorted(set(p["N"] for p in probs)), "autotuned": chosen,
+            "sequential_single_handles": {"value": it_s / (t_s / 1000.0), "ms_per_sweep": t_s / steps},
             "batch_speedup": (it_b / t_b) / max(it_s / t_s, 1e-30),
             # exp terms of all cell iterations over the whole sweep time (decide, apply and
             # compaction included): a lower bound of the cell kernel's own fraction
-            "mufu_frac_whole_sweep": (lt_b / (t_b / 1e3)) / 1e12 / peak,
-            "warm_start_s": t_warm}
-    print(json.dumps(line), flush=True)
+            "mufu_frac_whole_sweep": (lt_b / (t_b / 1e3)) / 1e12 / peak, "warm_start_s": t_warm}
 
 
-def run_grad(args, dd, torch):
-    """Differentiation workload: 512 x 512, eps = (2/512)^2, lam = 1, blob
+def run_grad(dd, torch, steps, warmup):
+    """Differentiation (config 5): 512 x 512, eps = (2/512)^2, lam = 1, blob
     mixtures of masses 1.0 / 1.1; DomDec (FP32 cells) to a relative PD gap of
     1e-6, then the backward pass (beta_star by one global Y-half, adjoint
     kernels for d/dmu, d/dnu, d/dx) timed per call, FP32 and FP64 summation."""
@@ -303,8 +444,7 @@ def run_grad(args, dd, torch):
     N, s = 512, 8
     mu, nu = inputs.mixture_blobs(N=N, seed=5000, mass_ratio=1.1)
     eps, lam = (2.0 / N) ** 2, 1.0
-    mu_d = torch.from_numpy(mu.ravel().copy()).cuda()
-    nu_d = torch.from_numpy(nu.ravel().copy()).cuda()
+    mu_d, nu_d = to_dev(torch, mu), to_dev(torch, nu)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     g, info = ag.solve(mu_d, nu_d, eps, lam, s=s, gap=1e-6, precision="fp32")
@@ -315,16 +455,15 @@ def run_grad(args, dd, torch):
                 torch.empty(2 * n, dtype=torch.float64, device="cuda")) for p in (dd.FP32, dd.FP64)}
     times = {}
     for p in (dd.FP32, dd.FP64):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             g.gradients(p, *bufs[p])
         ts = []
-        for _ in range(args.steps):
+        for _ in range(steps):
             torch.cuda.synchronize()
             t1 = time.perf_counter()
             g.gradients(p, *bufs[p])
             ts.append(time.perf_counter() - t1)
         times[p] = 1000 * float(np.median(ts))
-    # the adjoint alone (potentials given), CUDA events on the current stream
     a = torch.empty(n, dtype=torch.float64, device="cuda")
     b = torch.empty_like(a)
     dd.domdec_duals(g.h, a)
@@ -332,53 +471,105 @@ def run_grad(args, dd, torch):
     adj = {}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for p in (dd.FP32, dd.FP64):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             dd.domdec_uot_gradients(mu_d, nu_d, a, b, N, eps, lam, p, *bufs[p])
         torch.cuda.synchronize()
         e0.record()
-        for _ in range(args.steps):
+        for _ in range(steps):
             dd.domdec_uot_gradients(mu_d, nu_d, a, b, N, eps, lam, p, *bufs[p])
         e1.record()
         torch.cuda.synchronize()
-        adj[p] = e0.elapsed_time(e1) / args.steps
+        adj[p] = e0.elapsed_time(e1) / steps
     errs = {}
     for k, name in enumerate(("mu", "nu", "x")):
         ref = bufs[dd.FP64][k]
         errs[name] = float((bufs[dd.FP32][k] - ref).abs().max() / ref.abs().max())
-    sc = g.score()
     g.close()
-    line = {"metric": "backward (adjoint) time, 512x512 UOT score gradient", "value": times[dd.FP32],
-            "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": times[dd.FP32],
-            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "grad512", "N": N, "eps": eps, "lam": lam, "masses": [1.0, 1.1], "basic_cell": s},
-            "backward_fp64_ms": times[dd.FP64],
-            "adjoint_only_ms": {"fp32": adj[dd.FP32], "fp64": adj[dd.FP64]},
-            "fp32_vs_fp64_rel_err": errs,
-            "solve": {"seconds": t_solve, "sweeps": info["sweeps"], "rel_gap": info["rel_gap"], "score": sc[0]}}
-    print(json.dumps(line), flush=True)
+    return {"backward_ms": times[dd.FP32], "backward_fp64_ms": times[dd.FP64],
+            "adjoint_only_ms": {"fp32": adj[dd.FP32], "fp64": adj[dd.FP64]}, "fp32_vs_fp64_rel_err": errs,
+            "solve": {"seconds": t_solve, "sweeps": info["sweeps"], "rel_gap": info["rel_gap"]},
+            "N": N, "eps": eps, "lam": lam, "masses": [1.0, 1.1]}
+
+
+def e2e_reset(dd, torch, mu, nu, a0, b0, spec, lam, steps=3, sweeps=4):
+    """End to end through the C ABI with host buffers: every step loads the
+    problem from pinned host memory into one reused handle (domdec_reset: mu,
+    nu and the warm-start duals), runs `sweeps` sweeps and reads the tracked
+    score and both plan marginals back to pinned host memory."""
+    N, s, eps = spec["N"], spec["s"], spec["eps"]
+    pin = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64).ravel().copy()).pin_memory()
+    mu_h, nu_h, a_h, b_h = pin(mu), pin(nu), a0.cpu().pin_memory(), b0.cpu().pin_memory()
+    PX = torch.empty(N * N, dtype=torch.float64).pin_memory()
+    PY = torch.empty_like(PX)
+    g = dd.DomDec(mu_h, nu_h, eps, lam, s, alpha0=a_h, beta0=b_h, eps_init=2 * eps, precision="fp32", tau=0.0,
+                  err=2e-5)
+    g.iterate(1)
+    g.sync()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    its = 0
+    for _ in range(steps):
+        g.reset(mu_h, nu_h, alpha0=a_h, beta0=b_h, eps_init=2 * eps)
+        g.iterate(sweeps)
+        g.score()
+        dd.domdec_plan_marginals(g.h, PX, PY)
+        its += g.stats()["cell_iters"]
+    te = time.perf_counter() - t0
+    g.close()
+    return {"value": its / te, "unit": UNIT, "h2d_bytes_per_step": 4 * N * N * 8,
+            "d2h_bytes_per_step": 2 * N * N * 8 + 6 * 8,
+            "step": f"domdec_reset from pinned host mu, nu, alpha0, beta0 + {sweeps} sweeps + score + "
+                    "P_X, P_Y to pinned host memory, one reused handle"}
+
+
+def oracle_sample(max_seconds=20.0, sweeps=None, maxit=None):
+    """The FP64 oracle on a bounded sample of the headline workload: a
+    log-normal field (correlation length 0.05, masses 1.0 / 1.2) on a 32 x 32
+    grid, eps = (2/32)^2 (4 pixels^2, as the workload's (2/1024)^2), lam = 1,
+    s = 8, pi0 = mu x nu, staggered, cell tolerance 2e-5; whole sweeps are timed
+    until max_seconds.  Returns (cell-iters/s, description, cell-iters, seconds)."""
+    from oracle import domdec as odd
+    from paper_2410_08859_gb300 import inputs
+    N, s = 32, 8
+    mu, nu = inputs.lognormal_field(N=N, seed=3100)
+    mu, nu = mu.ravel(), nu.ravel()
+    geo = odd.Geometry(N, s)
+    st = odd.init_product(geo, mu, nu, (2.0 / N) ** 2, 1.0)
+    t0 = time.perf_counter()
+    its, k = 0, 0
+    while True:
+        lg = odd.sweep(st, "AB"[k % 2], "staggered", tau=0.0, err=2e-5, maxit=maxit or 2000)
+        its += sum(sum(r["iters"]) for r in lg)
+        k += 1
+        el = time.perf_counter() - t0
+        if (sweeps is not None and k >= sweeps) or (sweeps is None and el >= max_seconds):
+            break
+    desc = (f"oracle (NumPy FP64, 1 thread) DomDec sweeps on a log-normal 32x32 sample of the workload "
+            f"(eps = 4 pixels^2 as the workload, lam=1, s=8: composite cells 16x16, pi0=mu x nu); "
+            f"{k} sweeps, {its} cell-iterations in {el:.1f} s")
+    return its / el, desc, its, el
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    vals = []
-    for w in range(args.warmup):
+    for _ in range(args.warmup):
         oracle_sample(sweeps=1, maxit=200)
     t_all, its_all = 0.0, 0
-    for k in range(args.steps):
+    for _ in range(args.steps):
         v, desc, its, el = oracle_sample(sweeps=1, maxit=200)
         t_all += el
         its_all += its
-        vals.append(v)
     value = its_all / t_all
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * t_all / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": "blobs256 (oracle sample: 32x32 grid, same cell geometry)",
-                       "lam": 1.0, "s": 8},
+            "config": {"workload": "lognormal1024 (oracle sample: log-normal 32x32 grid, eps = 4 pixels^2, "
+                                   "s = 8)", "lam": 1.0},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "one oracle sweep per step (cell maxit 200) on blobs 32x32, s=8"},
+                             "sample": "one oracle sweep per step (cell maxit 200) on a log-normal 32x32 sample, "
+                                       "s=8"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -390,19 +581,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--lam", type=float, default=1.0)
-    ap.add_argument("--workload", default="blobs256", choices=["blobs256", "lognormal1024", "batch64", "grad512"])
-    ap.add_argument("--no-extras", action="store_true", help="skip time-to-gap, e2e and CPU baseline")
-    ap.add_argument("--cell-ctas", type=int, default=0, choices=[0, 1, 2],
+    ap.add_argument("--workload", default="lognormal1024", choices=["blobs256", "lognormal1024"])
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline line only: no other configurations, e2e or CPU baseline")
+    ap.add_argument("--extras", default="all",
+                    help="comma list of extras: configs,ttg,mix32,batch64,grad512,fp32fp64,e2e,cpu (default all)")
+    ap.add_argument("--cell-ctas", type=int, default=0, choices=[0, 1, 2, 4, 8],
                     help="CTAs per cell of the timed sweeps (domdec_params.cell_ctas)")
-    ap.add_argument("--cell-ti", type=int, default=0, choices=[0, 1],
-                    help="translation step in the cell solves of the timed sweeps (domdec_params.cell_ti)")
-    ap.add_argument("--ttg-sweeps", type=int, default=0,
-                    help="only run this many sweeps of the time-to-gap configuration and report the cell "
-                         "kernel in that regime (profiling)")
-    ap.add_argument("--balance", type=int, default=0, choices=[0, 1],
-                    help="balancing step after each cell solve of the timed sweeps (domdec_params.balance)")
-    ap.add_argument("--quick-warm", action="store_true",
-                    help="float-only, capped warm start (profiling runs; not a bench number)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -421,169 +606,64 @@ def main():
     if world > 1:
         dist.barrier()
     from paper_2410_08859_gb300 import domdec as dd
+    from paper_2410_08859_gb300 import inputs
     dd.lib()
+    t_start = time.perf_counter()
 
-    if args.workload in ("batch64", "grad512"):
-        if rank == 0:
-            (run_batch if args.workload == "batch64" else run_grad)(args, dd, torch)
-        if world > 1:
-            dist.barrier()
-            dist.destroy_process_group()
-        return
-
-    mu, nu, spec = workload_inputs(rank, args.workload)
-    N, s, eps, lam = spec["N"], spec["s"], spec["eps"], args.lam
-    mu_d = torch.from_numpy(mu).cuda()
-    nu_d = torch.from_numpy(nu).cuda()
-    a0, b0, t_warm, it_warm = warm_start(dd, mu_d, nu_d, N, eps, lam, torch, quick=args.quick_warm)
-
-    if args.ttg_sweeps > 0:
-        # the compute-heavy regime of the time-to-gap run (cell tolerance 1e-7): its first sweeps
-        # only, with the cell kernel's throughput and MUFU fraction (profiling runs)
-        g = dd.DomDec(mu_d, nu_d, eps, lam, s, alpha0=a0, beta0=b0, eps_init=2 * eps, precision="fp32",
-                      tau=0.0, err=1e-7, maxit=1000, cell_ctas=args.cell_ctas, profile=1)
-        g.iterate(args.ttg_sweeps)
-        g.sync()
-        st = g.stats()
-        kms, kn = g.kernel_times(reset=True)
-        g.close()
-        pk, _ = peaks()
-        peak = N_SM * MUFU_PER_SM_CLK * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
-        if rank == 0:
-            print(json.dumps({"regime": "time-to-gap sweeps (cell tolerance 1e-7, maxit 1000)",
-                              "sweeps": args.ttg_sweeps, "cell_iters": st["cell_iters"],
-                              "maxit_cells": st["maxit_cells"], "cell_kernel_ms": float(kms[0]),
-                              "cell_iters_per_s": st["cell_iters"] / max(kms[0] / 1e3, 1e-12),
-                              "mufu_frac": st["lse_terms"] / max(kms[0] / 1e3, 1e-12) / 1e12 / peak}), flush=True)
-        if world > 1:
-            dist.barrier()
-            dist.destroy_process_group()
-        return
-
-    g = dd.DomDec(mu_d, nu_d, eps, lam, s, alpha0=a0, beta0=b0, eps_init=2 * eps, precision="fp32",
-                  tau=0.0, err=2e-5, profile=1, cell_ctas=args.cell_ctas, cell_ti=args.cell_ti,
-                  balance=args.balance)
-    g.iterate(args.warmup)
-    g.sync()
-    g.kernel_times(reset=True)
-    st0 = g.stats()
+    pk, pk_kind = peaks_file()
+    peaks_meas = dd.domdec_probe_peaks(20000)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    stream = torch.cuda.current_stream()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    sampler = ClockSampler() if rank == 0 else None
+
+    # ---- headline: the contract's largest single-GPU configuration
+    mu, nu, spec = inputs.workload(args.workload, instance=rank)
+    N, s, eps, lam = spec["N"], spec["s"], spec["eps"], args.lam
+    mu_d, nu_d = to_dev(torch, mu), to_dev(torch, nu)
+    a0, b0, t_warm, it_warm = warm_start(dd, torch, mu_d, nu_d, N, eps, lam)
+    g = dd.DomDec(mu_d, nu_d, eps, lam, s, alpha0=a0, beta0=b0, eps_init=2 * eps, precision="fp32",
+                  tau=0.0, err=2e-5, profile=1, cell_ctas=args.cell_ctas)
     if world > 1:
         dist.barrier()
-    torch.cuda.synchronize()
-    for k in range(args.steps):
-        flush.zero_()
-        ev[k][0].record(stream)
-        g.iterate(1)
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
+    d = timed_sweeps(dd, torch, g, args.steps, args.warmup, flush, sample_clocks=(rank == 0))
     if world > 1:
         dist.barrier()
-    clocks = sampler.stop() if sampler else None
-    g.sync()
-    t_ms = sum(a.elapsed_time(b) for a, b in ev)
-    st1 = g.stats()
-    kms, kn = g.kernel_times(reset=True)
-    iters = st1["cell_iters"] - st0["cell_iters"]
-    terms = st1["lse_terms"] - st0["lse_terms"]
-    launches = int(kn.sum())
     cert = g.pd_gap()
     g.close()
-
-    iters_all, t_max = aggregate_ranks(float(iters), t_ms, world, "cuda")
+    iters_all, t_max = aggregate_ranks(float(d["cell_iters"]), d["ms"], world, "cuda")
     value = iters_all / (t_max / 1000.0)
-
+    # kernels of the timed region: per sweep one ordering kernel, per sub-batch the cell solve,
+    # decision and mixing kernels, three compaction kernels (one timed class)
+    launches = int(d["kn"][0] + d["kn"][1] + d["kn"][2] + 4 * d["kn"][3])
     if rank != 0:
         if world > 1:
             dist.barrier()
             dist.destroy_process_group()
         return
+    roofline = roofline_of(d, pk, N, peaks_meas)
 
-    pk, pk_kind = peaks()
-    sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
-    peak_mufu = N_SM * MUFU_PER_SM_CLK * sm_mhz * 1e6 / 1e12   # T ex2/s
-    k1_s = kms[0] / 1000.0
-    achieved = (terms / k1_s) / 1e12 if k1_s > 0 else 0.0
-    roofline = {"bound": "alu", "kernel": "k_cell_solve<float>", "achieved": achieved, "peak": peak_mufu,
-                "unit": "Tex2/s", "frac": achieved / peak_mufu,
-                # dram read + write bytes of one launch from an ncu capture of the current cell
-                # kernel in this configuration; None: the last capture predates kernel changes
-                "traffic": CELL_KERNEL_DRAM_BYTES if args.workload == "blobs256" else None,
-                "peak_source": f"{N_SM} SMs x {MUFU_PER_SM_CLK} MUFU/clk x {sm_mhz:.0f} MHz ({pk_kind} max clock)",
-                "kernel_share": float(kms[0] / max(kms.sum(), 1e-12)),
-                "kernel_ms": {"cell_solve": kms[0], "decide": kms[1], "apply": kms[2], "compact": kms[3]},
-                "launches": {"cell_solve": int(kn[0]), "decide": int(kn[1]), "apply": int(kn[2]),
-                             "compact": int(kn[3])}}
-
-    extras = {}
-    cpu = None
-    e2e = None
-    if not args.no_extras:
-        # time to the stated gap: DomDec (warm start + sweeps) vs global Sinkhorn on the same GPU
-        # the fast pipeline starts from a looser warm start (PD/lam <= 2e-5 |mu|): its line-searched
-        # steps make up for the rest in fewer seconds than the extra global Sinkhorn iterations
-        a_f, b_f, t_warm_f, it_warm_f = warm_start(dd, mu_d, nu_d, N, eps, lam, torch, err=2e-5)
-        tt, t_dd, rel_dd, sw, its_dd, cell_ms, terms_dd = domdec_to_gap(dd, mu_d, nu_d, N, s, eps, lam, a_f, b_f,
-                                                                         t_warm_f, torch)
-        tt_p, t_dd_p, rel_dd_p, sw_p, its_dd_p, cell_ms_p, terms_dd_p = domdec_to_gap(
-            dd, mu_d, nu_d, N, s, eps, lam, a0, b0, t_warm, torch, fast=False)
-        t_ti, rel_ti, it_ti = sinkhorn_to_gap(dd, mu_d, nu_d, N, eps, lam,
-                                              dd.SINKHORN_SEPARABLE | dd.SINKHORN_TI, dd.FP64, torch)
-        t_sep, rel_sep, it_sep = sinkhorn_to_gap(dd, mu_d, nu_d, N, eps, lam, dd.SINKHORN_SEPARABLE, dd.FP64,
-                                                 torch)
-        t_dense, rel_dense, it_dense = sinkhorn_to_gap(dd, mu_d, nu_d, N, eps, lam, dd.SINKHORN_DENSE, dd.FP32,
-                                                       torch, max_rounds=1, maxit=400)
-        extras["time_to_gap"] = {
-            "target_rel_gap": GAP_TARGET,
-            "domdec_pipeline": "warm start; cells with the translation step (maxit 300); GetWeights_line per "
-                               "staggered sub-batch",
-            "domdec_s": tt, "domdec_warm_start_s": t_warm_f, "domdec_sweeps_s": t_dd, "domdec_gap": rel_dd,
-            "domdec_sweeps": sw, "domdec_cell_iters": its_dd, "warm_start_sinkhorn_iters": it_warm_f,
-            # the sweeps of this run are compute-heavy (many cells iterate to maxit): throughput and
-            # MUFU roofline of the cell kernel in that regime
-            "domdec_cell_kernel_ms": cell_ms,
-            "domdec_cell_iters_per_s": its_dd / max(cell_ms / 1e3, 1e-12),
-            "domdec_cell_kernel_mufu_frac": (terms_dd / max(cell_ms / 1e3, 1e-12)) / 1e12 / peak_mufu,
-            "domdec_paper_pipeline": {"what": "warm start; plain cells; staggered swift (the paper's)",
-                                      "s": tt_p, "warm_start_s": t_warm, "warm_start_sinkhorn_iters": it_warm,
-                                      "sweeps_s": t_dd_p, "gap": rel_dd_p, "sweeps": sw_p,
-                                      "cell_iters": its_dd_p,
-                                      "cell_iters_per_s": its_dd_p / max(cell_ms_p / 1e3, 1e-12),
-                                      "cell_kernel_mufu_frac":
-                                          (terms_dd_p / max(cell_ms_p / 1e3, 1e-12)) / 1e12 / peak_mufu},
-            "sinkhorn_separable_fp64_translation_s": t_ti, "sinkhorn_separable_fp64_translation_gap": rel_ti,
-            "sinkhorn_separable_fp64_translation_iters": it_ti,
-            "sinkhorn_separable_fp64_s": t_sep, "sinkhorn_separable_fp64_gap": rel_sep,
-            "sinkhorn_separable_fp64_iters": it_sep,
-            "sinkhorn_dense_fp32_s": t_dense, "sinkhorn_dense_fp32_gap": rel_dense,
-            "sinkhorn_dense_fp32_iters": it_dense}
-        # end to end through the C ABI with host buffers: init (H2D of mu, nu and the
-        # warm-start duals), one A and one B sweep, score and marginals back to the host
-        mu_h = torch.from_numpy(mu).pin_memory()
-        nu_h = torch.from_numpy(nu).pin_memory()
-        a_h = a0.cpu().pin_memory()
-        b_h = b0.cpu().pin_memory()
-        PX = torch.empty(N * N, dtype=torch.float64).pin_memory()
-        PY = torch.empty_like(PX)
-        n_e2e = 3
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        its_e = 0
-        for _ in range(n_e2e):
-            ge = dd.DomDec(mu_h, nu_h, eps, lam, s, alpha0=a_h, beta0=b_h, eps_init=2 * eps, precision="fp32",
-                           tau=0.0)
-            ge.iterate(2)
-            ge.score()
-            dd.domdec_plan_marginals(ge.h, PX, PY)
-            its_e += ge.stats()["cell_iters"]
-            ge.close()
-        te = time.perf_counter() - t0
-        e2e = {"value": its_e / te, "unit": UNIT, "h2d_bytes_per_step": 4 * N * N * 8,
-               "d2h_bytes_per_step": 2 * N * N * 8 + 6 * 8,
-               "step": "domdec_init from host mu, nu, alpha0, beta0 + 2 sweeps + score + P_X, P_Y to host"}
+    extras, cpu, e2e = {}, None, None
+    want = set() if args.no_extras else set(args.extras.split(",")) if args.extras != "all" else \
+        {"configs", "ttg", "mix32", "batch64", "grad512", "fp32fp64", "e2e", "cpu"}
+    if "e2e" in want:
+        e2e = e2e_reset(dd, torch, mu, nu, a0, b0, spec, lam)
+    configs = {}
+    if "configs" in want:
+        configs["blobs256"] = {f"lam={lm:g}": sweep_config(dd, torch, "blobs256", lm, args.steps, args.warmup,
+                                                             flush, peaks_meas, pk)
+                               for lm in (0.1, 1.0, 10.0)}
+    if "mix32" in want:
+        configs["mix32"] = mix32_fp64(dd, torch)
+    if "batch64" in want:
+        configs["batch64"] = run_batch(dd, torch, max(4, args.steps // 2), args.warmup, peaks_meas)
+    if "grad512" in want:
+        configs["grad512"] = run_grad(dd, torch, 10, 3)
+    if configs:
+        extras["configs"] = configs
+    if "ttg" in want:
+        bm, bn, bspec = inputs.workload("blobs256")
+        extras["time_to_gap"] = time_to_gap_blobs256(dd, torch, bm, bn, bspec, 1.0)
+    if "fp32fp64" in want:
+        extras["fp32_vs_fp64"] = [fp32_vs_fp64(dd, torch, "blobs256", 1.0), fp32_vs_fp64(dd, torch, "mix32", 1.0)]
+    if "cpu" in want:
         v, desc, its, el = oracle_sample(max_seconds=15.0)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
 
@@ -593,12 +673,16 @@ def main():
             "config": {"workload": args.workload, "N": N, "basic_cell": s, "eps": eps, "lam": lam,
                        "eps_scaling": "1 -> 2 eps by global Sinkhorn (warm start), DomDec at eps",
                        "strategy": "staggered", "tau": 0.0, "err": 2e-5, "precision": "fp32 cell / fp64 score",
-                       "cell_ctas": args.cell_ctas, "cell_ti": args.cell_ti, "balance": args.balance,
-                       "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas x{world}"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                       "cell_ctas": args.cell_ctas, "l2": "flushed (256 MB write) between timed steps",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": d["clocks"],
             "gpu_launches": launches, "cell_iters_timed": int(iters_all),
-            "final_rel_gap_after_timed_sweeps": float(cert[2])}
+            "mean_iters_per_solve": d["cell_iters"] / max(d["cell_solves"], 1), "max_ny": d["max_ny"],
+            "warm_start": {"s": t_warm, "iters": it_warm},
+            "final_rel_gap_after_timed_sweeps": float(cert[2]),
+            "peaks_measured": peaks_meas, "peaks_file": pk_kind, "bench_wall_s": None}
     line.update(extras)
+    line["bench_wall_s"] = time.perf_counter() - t_start
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

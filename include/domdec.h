@@ -87,11 +87,18 @@ typedef struct {
   double eps_init;     /* eps of the warm-start duals passed to domdec_init (ignored without duals) */
   int    profile;      /* 1: time every kernel of a sweep with CUDA events on the handle's stream */
   int    spill_slots;  /* cells whose Y-box exceeds max_ny run from global memory slots (per sub-batch): 0 = default
-                          (one per cell of the largest sub-batch, at most 4 GiB), > 0 = that many, < 0 = none
+                          (one per cell of the largest sub-batch, at most 1 GiB), > 0 = that many, < 0 = none
                           (such cells fail with DOMDEC_ETOOBIG) */
-  int    cell_ctas;    /* CTAs per cell: 0 = a 2-CTA cluster when all cells of a sub-batch fit as resident
-                          clusters (else 1), 1 = always one CTA per cell, 2 = always a 2-CTA cluster (cells
-                          beyond the resident clusters wait for a free pair of SMs) */
+  int    cell_ctas;    /* CTAs per cell.  The cell kernel is a persistent grid over the resident CTAs that
+                          takes the cells of a sub-batch in order of decreasing estimated work (the exp
+                          terms of one iteration, from the box sizes).  A cell may be solved by a whole
+                          thread-block cluster, its Y box split by rows over the CTAs (each CTA holds its
+                          rows' Y-side arrays; the X-half log-sum-exp is combined from per-CTA parts).
+                          0 = automatic: clusters of 4 CTAs (s <= 8) or 8 (s > 8) for the cells whose
+                          work exceeds twice the mean work per CTA or whose box exceeds one CTA's
+                          shared memory, one CTA for the others; 1 = one CTA per cell; 2, 4, 8 = every
+                          cell whose box fits the cluster layout on a cluster of that many CTAs.  With
+                          balance or cell_ti every cell runs on one CTA. */
   int    cell_ti;      /* 1: after each X-half of a cell solve, shift alpha by the t maximising the cell
                           dual along (alpha + t, beta - t) (closed form; not in the paper: it removes the
                           slow total-mass mode of the alternation when eps << lam, same fixed point);
@@ -112,6 +119,8 @@ typedef struct {
   long long safe_steps;      /* sub-batches that fell back to theta = 1/|b| */
   long long box_entries;     /* stored entries of all nu_i (memory diagnostic, Section 5.3 "Sparsity") */
   long long lse_terms;       /* exp terms of the cell log-sum-exp passes (algorithmic work of the cell kernel) */
+  long long box_points;      /* sum over the cell solves of the Y-box size |B_J| (the points that the mixing
+                                and box refresh of a7 read and write) */
   int       max_cell_iters;  /* largest iteration count of one cell solve */
   int       max_ny;          /* largest cell Y-box seen */
 } domdec_stats;
@@ -135,6 +144,19 @@ void domdec_default_params(domdec_params* p);
 int domdec_init(domdec_t* out, const double* mu, const double* nu, int N,
                 const domdec_params* p, const double* alpha0, const double* beta0,
                 void* stream);
+
+/* Start a new problem of the same size in an existing handle: copy mu, nu
+ * (N*N, finite, > 0, host or device) and, if given, the warm-start duals
+ * alpha0, beta0 at eps_init (as domdec_init), rebuild the initial plan, and
+ * reset eps and err to the values given at domdec_init, the sweep count, the
+ * counters, the decision log and the kernel timers.  The handle's device
+ * allocations are reused (the box arenas are reallocated only if the new
+ * initial plan does not fit them; the dual buffers are allocated on the first
+ * call with duals), so a sequence of problems pays domdec_init's allocation
+ * and set-up once.  A handle in an error state returns DOMDEC_ESTATE.
+ * Synchronises. */
+int domdec_reset(domdec_t h, const double* mu, const double* nu, const double* alpha0,
+                 const double* beta0, double eps_init);
 
 /* Run n_sweeps partition sweeps (A, B, A, ... continuing the alternation of
  * earlier calls).  Enqueues only; errors found on the device are reported by
@@ -170,6 +192,13 @@ int domdec_plan_marginals(domdec_t h, double* PX, double* PY);
 /* The stitched X-potential alpha (proof of Proposition 4.2) into alpha (N*N
  * doubles, host or device).  Synchronises. */
 int domdec_duals(domdec_t h, double* alpha);
+
+/* The tracked per-basic-cell terms of the score (reading R3 of the tracked
+ * score, Section 4.4): C[i] = <c, pi_i> and H[i] = KL(pi_i | mu_i x nu) of the
+ * plan part of basic cell i, mixed linearly by the step sizes, (N/s)^2 doubles
+ * each in basic-cell order (row-major over the basic cells), host or device;
+ * either may be NULL.  Synchronises. */
+int domdec_basic_costs(domdec_t h, double* C, double* H);
 
 /* Primal-dual certificate: out[0] = E_hat, out[1] = D(alpha, beta_star) with beta_star
  * from one global closed-form Y-half (Eq. sinkhorn-iters-ot), out[2] =
@@ -310,7 +339,7 @@ void domdec_batch_free(domdec_batch_t b);
  *  - precision must be DOMDEC_FP32 or DOMDEC_FP64;
  *  - N*N must not exceed 65536 (N <= 256): larger grids return DOMDEC_ETOOBIG.
  * It calls no cudaMalloc, cudaFree or allocating library routine: all working
- * arrays live in one static device array of about 3.7 MB that every GPU which
+ * arrays live in one static device array of about 4.2 MB that every GPU which
  * loads the library keeps until the process exits.  Every call looks up that
  * array's address in the current context (cudaGetSymbolAddress, which
  * allocates nothing), so a cudaDeviceReset or another context of the same
@@ -327,9 +356,9 @@ int domdec_full_sinkhorn_noalloc(const double* mu, const double* nu, int N, doub
 
 /* Measurement helper (the paper has no counterpart): throughput probes that
  * give the roofline denominators of the cell kernel on the current device.
- * Runs, on all SMs, one kernel of independent ex2.approx.ftz.f32 (the
- * exponential of every log-sum-exp term) and one of independent FP32 FFMA
- * chains, `iters` loop passes of 16 operations per thread, each launched
+ * Runs, on all SMs, one kernel of 16 independent ex2.approx.ftz.f32 chains
+ * per thread (x <- 2^{-x}: the exponential of every log-sum-exp term) and one
+ * of 16 independent FP32 FFMA chains, `iters` loop passes of 16 operations per thread, each launched
  * twice with the second launch timed by CUDA events on `stream`.
  * out[0] ex2/s, out[1] ex2 per SM per clock, out[2] SM clock (MHz, from
  * clock64 against the global timer inside the ex2 kernel), out[3] FFMA/s,

@@ -17,9 +17,13 @@
 
 // ---- kernels' launch wrappers (dd_cell.cu, dd_sweep.cu, dd_sinkhorn.cu)
 size_t cell_smem_bytes(int s, int cap_side, int cap_ny, int precision);
-cudaError_t launch_cell_solve(const DevState& S, const CellDesc* cells, int begin, int nbatch, int precision,
-                              int csize, cudaStream_t st);
+cudaError_t launch_cell_solve(const DevState& S, const CellDesc* cells, const int* order, const int* nbig_p,
+                              int begin, int nbatch, int precision, size_t smem, int nctas, cudaStream_t st);
+cudaError_t launch_cell_order(const DevState& S, int part, int mode, int slots, cudaStream_t st);
 int cell_max_pair_clusters(int s, int cap_side, int cap_ny, int precision);
+size_t dist_smem_bytes(int s, int C, int cap_w, int cap_hl, int cap_nyl, int precision);
+int cell_static_smem(int precision);
+int cell_resident_ctas(size_t smem, int C, int precision);
 cudaError_t launch_cell_solve_multi(const DevState* states, const CellRef* refs, int nref, int part,
                                     unsigned int* queue, int s, int cap_side, int cap_ny, int precision, int csize,
                                     int nctas, cudaStream_t st);
@@ -58,7 +62,7 @@ cudaError_t adjoint_dev(const double* mu, const double* nu, const double* alpha,
 
 namespace {
 constexpr int LOGCAP = 4096;
-constexpr int NCOUNT = 8;
+constexpr int NCOUNT = 9;
 }  // namespace
 
 struct domdec_s {
@@ -82,7 +86,11 @@ struct domdec_s {
   unsigned long long maxit_seen = 0;  // maxit-cell counter at the previous domdec_sync
   int sticky = 0;
   int last_batch = 0;
-  int max_pairs = 0;  // co-resident 2-CTA clusters of the cell kernel
+  double eps0 = 0.0, err0 = 0.0;           // eps and err given at domdec_init (restored by domdec_reset)
+  double *d_a0 = nullptr, *d_b0 = nullptr, *d_w4 = nullptr;  // warm-start duals and 4 N*N scratch
+  int cell_nctas = 0;      // persistent CTAs of the cell kernel (whole clusters of S.dist_c)
+  size_t cell_smem = 0;    // its dynamic shared memory
+  int order_mode = 0;      // k_cell_order: 0 automatic, 1 every fitting cell on a cluster, 2 none
   // profiling: pending event pairs per kernel class
   struct EvPair { cudaEvent_t a, b; int cls; };
   std::vector<EvPair> pend;
@@ -146,7 +154,9 @@ int check_params(const domdec_params* p, int N) {
   if (p->maxit < 1 || p->newton_maxit < 1) return DOMDEC_EINVAL;
   if (p->strategy < 0 || p->strategy > 5 || (p->precision != 0 && p->precision != 1)) return DOMDEC_EINVAL;
   if (!(p->trunc_thr >= 0.0) || p->box_margin < 0) return DOMDEC_EINVAL;
-  if (p->cell_ctas < 0 || p->cell_ctas > 2 || p->cell_ti < 0 || p->cell_ti > 1) return DOMDEC_EINVAL;
+  if ((p->cell_ctas != 0 && p->cell_ctas != 1 && p->cell_ctas != 2 && p->cell_ctas != 4 && p->cell_ctas != 8) ||
+      p->cell_ti < 0 || p->cell_ti > 1)
+    return DOMDEC_EINVAL;
   if (p->balance < 0 || p->balance > 1) return DOMDEC_EINVAL;
   return DOMDEC_OK;
 }
@@ -239,15 +249,19 @@ int enqueue_sweep(domdec_s* h, int part, long long slot0) {
     batches.push_back({0, h->ncell[part]});
   }
   int k = 0;
+  // largest-first order of the cells of every sub-batch of this sweep (the
+  // member boxes of a sub-batch do not change before its own cell solve)
+  if (launch_cell_order(h->S, part, h->order_mode, h->cell_nctas, h->st) != cudaSuccess) return DOMDEC_ECUDA;
   for (auto& bt : batches) {
     const int begin = bt.first, nbt = bt.second - bt.first;
     if (nbt <= 0) continue;
     const int slot = (int)((slot0 + k++) % LOGCAP);
+    (void)slot;
     cudaEvent_t ev = prof_begin(h);
-    const int csize = h->max_pairs > 0 && !h->p.balance &&
-                              (h->p.cell_ctas == 2 || (h->p.cell_ctas == 0 && nbt <= h->max_pairs))
-                          ? 2 : 1;
-    if (launch_cell_solve(h->S, h->d_cells[part], begin, nbt, prec, csize, h->st) != cudaSuccess)
+    const int sub = (int)(&bt - batches.data());
+    const int* nbig_p = h->S.nbig + part * 4 + (batches.size() == 4 ? sub : 0);
+    if (launch_cell_solve(h->S, h->d_cells[part], h->S.order[part], nbig_p, begin, nbt, prec, h->cell_smem,
+                          h->cell_nctas, h->st) != cudaSuccess)
       return DOMDEC_ECUDA;
     prof_end(h, ev, 0);
     ev = prof_begin(h);
@@ -264,6 +278,84 @@ int enqueue_sweep(domdec_s* h, int part, long long slot0) {
   cudaEvent_t ev = prof_begin(h);
   if (launch_compact(h->S, h->d_newoff, h->st) != cudaSuccess) return DOMDEC_ECUDA;
   prof_end(h, ev, 3);
+  return DOMDEC_OK;
+}
+
+// Copy mu, nu (and the warm-start duals) into the handle's buffers, clear the
+// sweep state and build the initial plan (Algorithm 2, pi_init): the product
+// plan, or exp((alpha0 + beta0 - c)/eps0) mu x nu.  Allocates only what does
+// not exist yet (the arenas on the first call or when the new plan does not
+// fit them, the dual buffers on the first call with duals).  Synchronises.
+int load_problem(domdec_s* h, const double* mu, const double* nu, const double* alpha0, const double* beta0,
+                 double eps0) {
+  DevState& S = h->S;
+  const int n = h->n, N = h->N;
+  cudaStream_t st = h->st;
+  cudaError_t e = cudaMemcpyAsync(const_cast<double*>(S.mu), mu, n * sizeof(double), cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(const_cast<double*>(S.nu), nu, n * sizeof(double), cudaMemcpyDefault, st);
+  cudaMemsetAsync(S.status, 0, sizeof(int), st);
+  cudaMemsetAsync(S.cur, 0, sizeof(int), st);
+  cudaMemsetAsync(S.head, 0, sizeof(unsigned long long), st);
+  cudaMemsetAsync(S.counters, 0, NCOUNT * sizeof(unsigned long long), st);
+  cudaMemsetAsync(S.red_count, 0, sizeof(unsigned int), st);
+  cudaMemsetAsync(S.queue, 0, 2 * sizeof(unsigned int), st);
+  cudaMemsetAsync(S.nbig, 0, 8 * sizeof(int), st);
+  cudaMemsetAsync(S.spill_count, 0, sizeof(unsigned int), st);
+  cudaMemsetAsync(S.dPY, 0, n * sizeof(double), st);
+  cudaMemsetAsync(S.PY, 0, n * sizeof(double), st);
+  cudaMemsetAsync(S.theta, 0, sizeof(double), st);
+  cudaMemsetAsync(S.declog, 0, 4 * LOGCAP * sizeof(double), st);
+  cudaMemsetAsync(S.slotctr, 0, sizeof(unsigned long long), st);
+  if (e == cudaSuccess)
+    e = launch_prepare_inputs(S.mu, S.nu, const_cast<double*>(S.logmu), const_cast<double*>(S.lognu), n, S.status,
+                              st);
+  if (e != cudaSuccess) return DOMDEC_ECUDA;
+  if (alpha0 && !h->d_a0) {
+    if (dalloc(h, &h->d_a0, n) != cudaSuccess || dalloc(h, &h->d_b0, n) != cudaSuccess ||
+        dalloc(h, &h->d_w4, 4 * (size_t)n) != cudaSuccess)
+      return DOMDEC_ENOMEM;
+  }
+  double *ad = h->d_a0, *bd = h->d_b0, *wtmp = h->d_w4;
+  if (alpha0) {
+    e = cudaMemcpyAsync(ad, alpha0, n * sizeof(double), cudaMemcpyDefault, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bd, beta0, n * sizeof(double), cudaMemcpyDefault, st);
+    if (e == cudaSuccess) e = launch_init_duals_boxes(S, ad, bd, eps0, h->d_numom, h->d_mumass, h->d_newoff, st);
+  } else {
+    e = launch_init_product_boxes(S, h->d_numom, h->d_mumass, h->d_newoff, st);
+  }
+  long long total = 0;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&total, h->d_newoff + h->nbasic, sizeof(long long), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return DOMDEC_ECUDA;
+  int rc = read_status(h);
+  if (rc) return rc;
+  const double fac = h->p.arena_factor > 0 ? h->p.arena_factor : 48.0;
+  const long long need = std::max((long long)(fac * n), 8 * total + 1024);
+  if (!S.arena[0] || S.cap < 8 * total + 1024) {
+    for (auto& q : h->allocs)
+      if (q && (q == S.arena[0] || q == S.arena[1])) { cudaFree(q); q = nullptr; }
+    S.arena[0] = S.arena[1] = nullptr;
+    if (dalloc(h, &S.arena[0], need) != cudaSuccess || dalloc(h, &S.arena[1], need) != cudaSuccess)
+      return DOMDEC_ENOMEM;
+    S.cap = need;
+  }
+  if (alpha0) {
+    // w(x) = log sum_y exp(beta0/eps0 + log nu - c/eps0): P_X of the initial plan
+    e = global_lse64(bd, S.lognu, eps0, 1.0 / N, N, wtmp, wtmp + n, wtmp + 2 * (size_t)n, wtmp + 3 * (size_t)n, st);
+    if (e == cudaSuccess) e = launch_init_duals_fill(S, ad, bd, eps0, wtmp, h->d_newoff, st);
+  } else {
+    e = launch_init_product_fill(S, h->d_numom, h->d_mumass, h->d_newoff, st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return DOMDEC_ECUDA;
+  rc = read_status(h);
+  if (rc) return rc;
+  h->sweeps = 0;
+  h->slot = 0;
+  h->maxit_seen = 0;
+  h->last_batch = 0;
+  for (int k = 0; k < 4; ++k) { h->kt[k] = 0.0; h->kn[k] = 0; }
   return DOMDEC_OK;
 }
 
@@ -353,21 +445,59 @@ int domdec_init(domdec_t* out, const double* mu, const double* nu, int N, const 
   int dev = 0, smem_optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  // dynamic shared memory left beside the kernels' static shared memory
+  const int smem_budget = smem_optin - cell_static_smem(pin->precision) - 64;
   int cap_ny = pin->max_ny > 0 ? pin->max_ny : (pin->precision ? 3072 : 8192);
   int cap_side = std::min(N, 128);
   for (;;) {
     cap_side = std::min(cap_side, cap_ny);
     // epilogue scratch (3 nx1 W) must fit in the T/U/bl/lrho/Zv region
     while (2 * h->s * cap_side > 3 * cap_ny && cap_side > 1) --cap_side;
-    if (cell_smem_bytes(h->s, cap_side, cap_ny, pin->precision) <= (size_t)smem_optin || cap_ny <= 64) break;
+    if (cell_smem_bytes(h->s, cap_side, cap_ny, pin->precision) <= (size_t)smem_budget || cap_ny <= 64) break;
     cap_ny -= 256;
   }
   S.cap_ny = cap_ny;
   S.cap_side = cap_side;
-  h->max_pairs = pin->cell_ctas == 1 ? 0 : cell_max_pair_clusters(h->s, cap_side, cap_ny, pin->precision);
-  if (cell_smem_bytes(h->s, cap_side, cap_ny, pin->precision) > (size_t)smem_optin) {
+  if (cell_smem_bytes(h->s, cap_side, cap_ny, pin->precision) > (size_t)smem_budget) {
     delete h;
     return DOMDEC_EINVAL;
+  }
+  // clusters for the largest cells: automatic 4 CTAs (s <= 8) or 8 (larger cells);
+  // one CTA per cell with balancing or the translation step
+  {
+    int C = pin->cell_ctas == 0 ? (h->s <= 8 ? 4 : 8) : pin->cell_ctas;
+    if (pin->balance || pin->cell_ti) C = 1;
+    h->order_mode = pin->cell_ctas == 0 ? 0 : 1;
+    const size_t rs = pin->precision ? sizeof(double) : sizeof(float);
+    size_t smem = cell_smem_bytes(h->s, cap_side, cap_ny, pin->precision);
+    int nctas = 0;
+    for (; C > 1; C /= 2) {
+      int cw = std::min(N, 256), ch = std::min(N, 128), nyl = 0;
+      for (; cw >= 16; cw /= 2, ch = std::max(16, ch / 2)) {
+        const size_t fixed = dist_smem_bytes(h->s, C, cw, ch, 0, pin->precision);
+        if (fixed >= (size_t)smem_budget) continue;
+        nyl = (int)(((size_t)smem_budget - fixed) / (5 * rs)) / 32 * 32;
+        // epilogue scratch (3 nx1 W) must fit in the T/U/bl/lrho/Zv region
+        if (nyl >= 512 && 4 * h->s * cw <= 2 * h->s * ch + 3 * nyl) break;
+        nyl = 0;
+      }
+      if (nyl < 512) continue;
+      const size_t sm = std::max(smem, dist_smem_bytes(h->s, C, cw, ch, nyl, pin->precision));
+      const int n = cell_resident_ctas(sm, C, pin->precision);
+      if (n >= C) {
+        S.dist_c = C; S.dist_cap_w = cw; S.dist_cap_hl = ch; S.dist_cap_nyl = nyl;
+        smem = sm;
+        nctas = n;
+        break;
+      }
+    }
+    if (C <= 1) {
+      S.dist_c = 1; S.dist_cap_w = S.dist_cap_hl = S.dist_cap_nyl = 0;
+      h->order_mode = 2;
+      nctas = cell_resident_ctas(smem, 1, pin->precision);
+    }
+    h->cell_smem = smem;
+    h->cell_nctas = std::max(1, nctas);
   }
   std::vector<CellDesc> cells[2];
   for (int w = 0; w < 2; ++w) {
@@ -400,13 +530,17 @@ int domdec_init(domdec_t* out, const double* mu, const double* nu, int N, const 
   DD_ALLOC(S.cur, 1); DD_ALLOC(S.head, 1);
   DD_ALLOC(h->d_cells[0], std::max(1, h->ncell[0])); DD_ALLOC(h->d_cells[1], std::max(1, h->ncell[1]));
   DD_ALLOC(S.cout, std::max(1, mb));
-  DD_ALLOC(S.nut, (size_t)std::max(1, mb) * 4 * cap_ny);
+  S.cap_nut = std::max(cap_ny, S.dist_c > 1 ? S.dist_c * S.dist_cap_nyl : 0);
+  DD_ALLOC(S.nut, (size_t)std::max(1, mb) * 4 * S.cap_nut);
   DD_ALLOC(S.theta, 1); DD_ALLOC(S.declog, 4 * LOGCAP); DD_ALLOC(S.counters, NCOUNT);
   DD_ALLOC(S.slotctr, 1);
   DD_ALLOC(S.status, 1); DD_ALLOC(S.red, 2 * 152 * 5 + 8); DD_ALLOC(S.red_count, 1);
   DD_ALLOC(h->d_newoff, h->nbasic + 1); DD_ALLOC(h->d_scratch, 64);
   DD_ALLOC(h->d_partials, kRedBlocks * 8);
   DD_ALLOC(h->S.line, 16); DD_ALLOC(h->d_numom, 8);
+  DD_ALLOC(S.queue, 2);
+  DD_ALLOC(S.nbig, 8);
+  DD_ALLOC(S.order[0], std::max(1, h->ncell[0])); DD_ALLOC(S.order[1], std::max(1, h->ncell[1]));
   {
     // spill slots for cell boxes beyond the shared-memory capacity: Y-side arrays
     // (4 s N + 5 N^2 values) followed by 4 N^2 doubles of new marginals
@@ -414,8 +548,8 @@ int domdec_init(domdec_t* out, const double* mu, const double* nu, int N, const 
     size_t ybytes = rs * (4 * (size_t)h->s * N + 5 * (size_t)n);
     ybytes = (ybytes + 255) / 256 * 256;
     const size_t stride = ybytes + 4 * (size_t)n * sizeof(double);
-    // default: one slot per cell of the largest sub-batch, within 4 GiB
-    const size_t budget = (size_t)4 << 30;
+    // default: one slot per cell of the largest sub-batch, within 1 GiB
+    const size_t budget = (size_t)1 << 30;
     int slots = (int)std::min<size_t>((size_t)std::max(1, mb), std::max<size_t>(1, budget / stride));
     if (pin->spill_slots > 0) slots = pin->spill_slots;
     if (pin->spill_slots < 0) slots = 0;
@@ -428,66 +562,26 @@ int domdec_init(domdec_t* out, const double* mu, const double* nu, int N, const 
   S.mu = dmu; S.nu = dnu; S.logmu = dlogmu; S.lognu = dlognu; S.muinu = dmuinu;
   if (cudaMallocHost(&h->h_pinned, 64 * sizeof(double)) != cudaSuccess) { domdec_free(h); return DOMDEC_ENOMEM; }
   cudaStream_t st = h->st;
-  e = cudaMemcpyAsync(dmu, mu, n * sizeof(double), cudaMemcpyDefault, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dnu, nu, n * sizeof(double), cudaMemcpyDefault, st);
-  cudaMemsetAsync(S.status, 0, sizeof(int), st);
-  cudaMemsetAsync(S.cur, 0, sizeof(int), st);
-  cudaMemsetAsync(S.head, 0, sizeof(unsigned long long), st);
-  cudaMemsetAsync(S.counters, 0, NCOUNT * sizeof(unsigned long long), st);
-  cudaMemsetAsync(S.red_count, 0, sizeof(unsigned int), st);
-  cudaMemsetAsync(S.spill_count, 0, sizeof(unsigned int), st);
-  cudaMemsetAsync(S.dPY, 0, n * sizeof(double), st);
-  cudaMemsetAsync(S.PY, 0, n * sizeof(double), st);
-  cudaMemsetAsync(S.theta, 0, sizeof(double), st);
-  cudaMemsetAsync(S.declog, 0, 4 * LOGCAP * sizeof(double), st);
   for (int w = 0; w < 2; ++w)
-    if (h->ncell[w])
-      cudaMemcpyAsync(h->d_cells[w], cells[w].data(), cells[w].size() * sizeof(CellDesc),
-                      cudaMemcpyHostToDevice, st);
+    if (h->ncell[w] &&
+        cudaMemcpyAsync(h->d_cells[w], cells[w].data(), cells[w].size() * sizeof(CellDesc),
+                        cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      domdec_free(h);
+      return DOMDEC_ECUDA;
+    }
   for (int w = 0; w < 2; ++w) {
     S.cells[w] = h->d_cells[w];
     for (int b = 0; b < 5; ++b) S.sub_start[w][b] = h->sub_start[w][b];
   }
   S.staggered = pin->strategy == DOMDEC_STAGGERED || pin->strategy == DOMDEC_STAGGERED_LINE;
   S.newoff = h->d_newoff;
-  cudaMemsetAsync(S.slotctr, 0, sizeof(unsigned long long), st);
-  if (e == cudaSuccess) e = launch_prepare_inputs(dmu, dnu, dlogmu, dlognu, n, S.status, st);
-  if (e != cudaSuccess) { domdec_free(h); return DOMDEC_ECUDA; }
-  // temporary arena pointers for the box pass (no values written yet)
-  double* ad = nullptr;
-  double* bd = nullptr;
-  double* wtmp = nullptr;
-  if (alpha0) {
-    DD_ALLOC(ad, n); DD_ALLOC(bd, n); DD_ALLOC(wtmp, 4 * (size_t)n);
-    cudaMemcpyAsync(ad, alpha0, n * sizeof(double), cudaMemcpyDefault, st);
-    cudaMemcpyAsync(bd, beta0, n * sizeof(double), cudaMemcpyDefault, st);
-    e = launch_init_duals_boxes(S, ad, bd, pin->eps_init, h->d_numom, h->d_mumass, h->d_newoff, st);
-  } else {
-    e = launch_init_product_boxes(S, h->d_numom, h->d_mumass, h->d_newoff, st);
+  h->eps0 = pin->eps;
+  h->err0 = pin->err;
+  rc = load_problem(h, mu, nu, alpha0, beta0, pin->eps_init);
+  if (rc) {
+    domdec_free(h);
+    return rc;
   }
-  long long total = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&total, h->d_newoff + h->nbasic, sizeof(long long),
-                                            cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) { domdec_free(h); return DOMDEC_ECUDA; }
-  rc = read_status(h);
-  if (rc) { domdec_free(h); return rc; }
-  const double fac = pin->arena_factor > 0 ? pin->arena_factor : 48.0;
-  S.cap = std::max((long long)(fac * n), 8 * total + 1024);
-  DD_ALLOC(S.arena[0], S.cap);
-  DD_ALLOC(S.arena[1], S.cap);
-  if (alpha0) {
-    // w(x) = log sum_y exp(beta0/eps0 + log nu - c/eps0): P_X of the initial plan
-    global_lse64(bd, dlognu, pin->eps_init, 1.0 / N, N, wtmp, wtmp + n, wtmp + 2 * (size_t)n,
-                 wtmp + 3 * (size_t)n, st);
-    e = launch_init_duals_fill(S, ad, bd, pin->eps_init, wtmp, h->d_newoff, st);
-  } else {
-    e = launch_init_product_fill(S, h->d_numom, h->d_mumass, h->d_newoff, st);
-  }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) { domdec_free(h); return DOMDEC_ECUDA; }
-  rc = read_status(h);
-  if (rc) { domdec_free(h); return rc; }
   *out = h;
   return DOMDEC_OK;
 #undef DD_ALLOC
@@ -505,6 +599,20 @@ int domdec_iterate(domdec_t h, int n_sweeps) {
     ++h->sweeps;
   }
   return DOMDEC_OK;
+}
+
+int domdec_reset(domdec_t h, const double* mu, const double* nu, const double* alpha0, const double* beta0,
+                 double eps_init) {
+  if (!h || !mu || !nu) return DOMDEC_EINVAL;
+  if (h->sticky) return DOMDEC_ESTATE;
+  if ((alpha0 == nullptr) != (beta0 == nullptr)) return DOMDEC_EINVAL;
+  if (alpha0 && !(eps_init > 0.0 && std::isfinite(eps_init))) return DOMDEC_EINVAL;
+  if (cudaStreamSynchronize(h->st) != cudaSuccess) return fail(h, DOMDEC_ECUDA);
+  prof_collect(h);
+  h->S.eps = h->p.eps = h->eps0;
+  h->S.err = h->p.err = h->err0;
+  const int rc = load_problem(h, mu, nu, alpha0, beta0, eps_init);
+  return rc ? fail(h, rc) : DOMDEC_OK;
 }
 
 int domdec_set_eps(domdec_t h, double eps) {
@@ -575,6 +683,17 @@ int domdec_duals(domdec_t h, double* alpha) {
   if (!h || !alpha) return DOMDEC_EINVAL;
   if (h->sticky) return DOMDEC_ESTATE;
   cudaError_t e = cudaMemcpyAsync(alpha, h->S.alpha, h->n * sizeof(double), cudaMemcpyDefault, h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return fail(h, DOMDEC_ECUDA);
+  return read_status(h);
+}
+
+int domdec_basic_costs(domdec_t h, double* C, double* H) {
+  if (!h) return DOMDEC_EINVAL;
+  if (h->sticky) return DOMDEC_ESTATE;
+  cudaError_t e = cudaSuccess;
+  if (C) e = cudaMemcpyAsync(C, h->S.Cc, h->nbasic * sizeof(double), cudaMemcpyDefault, h->st);
+  if (H && e == cudaSuccess) e = cudaMemcpyAsync(H, h->S.Hh, h->nbasic * sizeof(double), cudaMemcpyDefault, h->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
   if (e != cudaSuccess) return fail(h, DOMDEC_ECUDA);
   return read_status(h);
@@ -698,6 +817,7 @@ int domdec_get_stats(domdec_t h, domdec_stats* s) {
   s->greedy_steps = (long long)c[3];
   s->safe_steps = (long long)c[4];
   s->lse_terms = (long long)c[7];
+  s->box_points = (long long)c[8];
   s->max_cell_iters = (int)c[5];
   s->max_ny = (int)c[6];
   s->box_entries = (long long)h->h_pinned[4];

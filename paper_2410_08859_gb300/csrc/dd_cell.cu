@@ -21,6 +21,8 @@
 //    previous iteration's value (one pass), with an exact max-shifted fallback.
 #include <cooperative_groups.h>
 
+#include <algorithm>
+
 #include "dd_common.cuh"
 
 namespace {
@@ -190,6 +192,25 @@ __device__ __forceinline__ void newton_u2(const R (&lr)[2], const R (&c0)[2], co
       }
     }
   }
+}
+
+// mu phi((p0 + d)/mu) - mu phi(p0/mu) with phi(s) = s log s - s + 1, written as
+//   d (log(p0/mu) - 1) + (p0 + d) log1p(d/p0),
+// an identity whose float evaluation errs by ~1e-7 |d| (both logarithms enter
+// multiplied by the change), unlike the difference of the two terms (~1e-7 p0).
+// log_mu: natural log of mu.  The result is returned in double for summation.
+__device__ __forceinline__ double kl_change_f(double p0, double d, float log_mu) {
+  const double p1 = p0 + d;
+  if (p0 <= 0.0) {   // mu phi(0) = mu
+    if (p1 <= 0.0) return 0.0;
+    const float p1f = (float)p1;
+    return (double)(p1f * (dd_lg2(p1f) * (float)DD_LN2 - log_mu - 1.0f));
+  }
+  const float p0f = (float)p0, df = (float)d;
+  const float l0 = dd_lg2(p0f) * (float)DD_LN2 - log_mu;
+  const float l1p = log1pf(df / p0f);
+  if (p1 <= 0.0) return (double)(df * (l0 - 1.0f));   // limit p1 log(p1/p0) -> 0
+  return (double)(df * (l0 - 1.0f)) + p1 * (double)l1p;
 }
 
 // v[k] for a run-time k in 0..3 without indexing a local array (keeps it in registers).
@@ -376,12 +397,13 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
   const R q2 = R(q * DD_LOG2E), qR = R(q), sR = R(sl), rR = R(rr);
 
   // ------------------------------------------------------- load X side
+  const double inv_eps = 1.0 / eps;
   double acc2[2] = {0.0, 0.0};
   for (int t = tid; t < nx; t += nthr) {
     int r = t / nx2, c = t - r * nx2;
     int x = (cd.i0 + r) * N + cd.j0 + c;
     int xi1 = cd.i0 + r - xc1, xi2 = cd.j0 + c - xc2;
-    acc2[0] += S.alpha[x] / eps - 2.0 * q * (double)(D1 * xi1 + D2 * xi2);
+    acc2[0] += S.alpha[x] * inv_eps - 2.0 * q * (double)(D1 * xi1 + D2 * xi2);
     acc2[1] += S.mu[x];
   }
   block_sum<2>(acc2, red);
@@ -398,7 +420,7 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
     int x = (cd.i0 + r) * N + cd.j0 + c;
     int xi1 = cd.i0 + r - xc1, xi2 = cd.j0 + c - xc2;
     double lin = 2.0 * q * (double)(D1 * xi1 + D2 * xi2);
-    R a = R(S.alpha[x] / eps - lin - A);
+    R a = R(S.alpha[x] * inv_eps - lin - A);
     R l = R(S.logmu[x]);
     av[t] = a;
     lm[t] = l;
@@ -612,11 +634,19 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
       }
       double p1 = (double)dd_ex2((lm[t] + av_c[t]) * L2E + Wv[t]);
       S.PXnew[x] = p1;
-      double p0 = S.PX[x], m = S.mu[x];
-      double ps = (1.0 - th_s) * p0 + th_s * p1;
-      double k0v = dd_kl_term(p0, m);
-      dk[0] += dd_kl_term(p1, m) - k0v;
-      dk[1] += dd_kl_term(ps, m) - k0v;
+      double p0 = S.PX[x];
+      if (sizeof(R) == 8) {
+        double m = S.mu[x];
+        double ps = (1.0 - th_s) * p0 + th_s * p1;
+        double k0v = dd_kl_term(p0, m);
+        dk[0] += dd_kl_term(p1, m) - k0v;
+        dk[1] += dd_kl_term(ps, m) - k0v;
+      } else {
+        // float cell solve: the KL_X changes from the cancellation-free form
+        // (the error scales with the change p1 - p0, not with p)
+        dk[0] += kl_change_f(p0, p1 - p0, lm[t]);
+        dk[1] += kl_change_f(p0, th_s * (p1 - p0), lm[t]);
+      }
     }
     if (bal) block_sum<4>(mubar, red);
     else block_sum<2>(dk, red);
@@ -884,22 +914,659 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
     if (o.status == CELL_MAXIT) atomicAdd(S.counters + 2, 1ull);
     atomicMax(S.counters + 5, (unsigned long long)it);
     atomicMax(S.counters + 6, (unsigned long long)ny);
+    atomicAdd(S.counters + 8, (unsigned long long)ny);
     atomicAdd(S.counters + 7, (unsigned long long)it *
                                   (unsigned long long)(nx1 * W * nx2 + H * W * nx1 + H * nx2 * W + nx * H));
     if (nonfinite) atomicOr(S.status, ST_NONFINITE);
   }
 }
 
+// ---------------------------------------------------------------------------
+// One cell solved by a cluster of C = S.dist_c CTAs, split by rows of its Y box.
+// CTA r owns rows [kb, ke) of B_J: the Y-side arrays (log rho, log nu, Z, beta,
+// beta + log nu) of those rows live in its shared memory only, so a cluster
+// holds C times the Y points of one CTA and the largest cells of a sub-batch
+// spread over C SMs.  Per iteration:
+//   T pass  (rows of X against the columns of B_J, the same for every slab):
+//           targets split over the cluster, every result written to all CTAs
+//           (distributed shared memory); cluster barrier;
+//   Z pass and the Newton roots of the Y-half on the own rows;
+//   U pass (rows of B_J against the columns of X) on the own rows;
+//   W partial: the column log-sum-exp of the X-half over the own rows only,
+//           written to the exchange buffer of every CTA; cluster barrier;
+//   every CTA combines the C partials of each x in rank order (so all CTAs
+//           hold the same W, gap and next alpha) -- no further exchange.
+// The epilogue splits the rows-of-X pass the same way and sums the
+// per-quadrant terms of the own rows; the first CTA adds the cluster's sums.
+constexpr int kDistMaxC = 8;
+
+template <typename R>
+__device__ __forceinline__ void cell_solve_dist(const DevState& S, const CellDesc cd, int cidx, int nbatch,
+                                                int crank, unsigned char* smem_raw) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = S.dist_c;
+  double* red = reinterpret_cast<double*>(smem_raw);   // 32 * 16 doubles (block reductions)
+  __shared__ BoxRec dbox[4];
+  __shared__ int dgeo[8];
+  __shared__ double dx[kDistMaxC * 16];                 // partial sums of every CTA of the cluster
+  CellOut* out = S.cout + cidx;
+  const double* __restrict__ arena = S.arena[*S.cur];
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int gtid = crank * nthr + tid, gthr = C * nthr;
+  const int N = S.N, s = S.s;
+  const int nx1 = cd.nx1, nx2 = cd.nx2, nx = nx1 * nx2;
+  auto csync = [&]() { cl.sync(); };
+
+  // ---------------------------------------------------------------- B_J
+  // every CTA computes the same box; the first one takes a spill slot for the
+  // new marginals when the box exceeds the per-cell marginal buffer and tells
+  // the others (its status decides for the whole cluster)
+  if (tid == 0) {
+    int k0 = 1 << 30, l0 = 1 << 30, k1 = -1, l1 = -1;
+    for (int q = 0; q < 4; ++q) {
+      BoxRec b = {0, 0, 0, 0, 0};
+      if (cd.mem[q] >= 0) b = S.box[cd.mem[q]];
+      dbox[q] = b;
+      if (cd.mem[q] < 0 || b.H * b.W == 0) continue;
+      k0 = min(k0, b.k0); l0 = min(l0, b.l0);
+      k1 = max(k1, b.k0 + b.H); l1 = max(l1, b.l0 + b.W);
+    }
+    int st = CELL_OK;
+    if (k1 < 0) {
+      st = CELL_EMPTY;
+      k0 = l0 = k1 = l1 = 0;
+    } else {
+      k0 = max(0, k0 - S.margin); l0 = max(0, l0 - S.margin);
+      k1 = min(N, k1 + S.margin); l1 = min(N, l1 + S.margin);
+    }
+    const int H = k1 - k0, W = l1 - l0;
+    dgeo[0] = k0; dgeo[1] = l0; dgeo[2] = H; dgeo[3] = W;
+    if (crank == 0) {
+      int slot = -1;
+      const int hl = (H + C - 1) / C;
+      if (st == CELL_OK && (H < C || W > S.dist_cap_w || hl > S.dist_cap_hl || hl * W > S.dist_cap_nyl))
+        st = CELL_TOOBIG;   // excluded by k_cell_order; kept as a guard
+      if (st == CELL_OK && H * W > S.cap_nut) {
+        const int sl = S.spill_slots > 0 ? (int)atomicAdd(S.spill_count, 1u) : S.spill_slots;
+        if (sl >= S.spill_slots) st = CELL_TOOBIG;
+        else slot = sl;
+      }
+      for (int r = 0; r < C; ++r) {
+        int* g = cl.map_shared_rank(dgeo, r);
+        g[4] = st;
+        g[7] = slot;
+      }
+    }
+  }
+  csync();
+  const int k0 = dgeo[0], l0 = dgeo[1], H = dgeo[2], W = dgeo[3];
+  const int slot = dgeo[7];
+  if (dgeo[4] != CELL_OK) {
+    if (tid == 0 && crank == 0) {
+      CellOut o;
+      o.k0 = k0; o.l0 = l0; o.H = H; o.W = W; o.iters = 0; o.status = dgeo[4];
+      o.D1 = o.D2 = 0; o.gap = 0.0; o.dKX[0] = o.dKX[1] = 0.0; o.slot = -1; o.pad = 0;
+      for (int q = 0; q < 4; ++q) {
+        const int bi = cd.mem[q];
+        o.Ct[q] = bi >= 0 ? S.Cc[bi] : 0.0;
+        o.Ht[q] = bi >= 0 ? S.Hh[bi] : 0.0;
+        o.mass[q] = 0.0;
+      }
+      *out = o;
+      atomicOr(S.status, dgeo[4] == CELL_EMPTY ? ST_EMPTY : ST_TOOBIG);
+    }
+    return;
+  }
+  const int kb = (int)(((long long)H * crank) / C), ke = (int)(((long long)H * (crank + 1)) / C);
+  const int Hl = ke - kb, nyl = Hl * W;
+
+  // ------------------------------------------------------- shared layout
+  const int cap_nx = 4 * s * s;
+  R* xa = reinterpret_cast<R*>(smem_raw + 32 * 16 * sizeof(double));
+  R* av = xa + cap_nx;
+  R* g0 = av + cap_nx;
+  R* Wv = g0 + cap_nx;       // W of the X-half, combined over the cluster
+  R* lm = Wv + cap_nx;
+  R* xa_nx = lm + cap_nx;
+  R* av_nx = xa_nx + cap_nx;
+  R* Wp = av_nx + cap_nx;    // own rows' part of W (the shift of the next iteration)
+  R* Wx = Wp + cap_nx;       // C x cap_nx: the parts of all CTAs
+  R* T = Wx + C * cap_nx;    // nx1 x W
+  R* U = T + 2 * s * S.dist_cap_w;   // Hl x nx2
+  R* bl = U + 2 * s * S.dist_cap_hl;
+  R* lrho = bl + S.dist_cap_nyl;
+  R* Zv = lrho + S.dist_cap_nyl;
+  R* bv = Zv + S.dist_cap_nyl;
+  R* lnu = bv + S.dist_cap_nyl;
+
+  // ------------------------------------------------- load Y side (a1), own rows
+  // rho = max(0, P_Y - nu_J)/nu and log nu; the barycentre of nu_J (the Y frame
+  // origin) is summed over the whole box from every CTA's part
+  int c1, c2;
+  {
+    double m3[3] = {0.0, 0.0, 0.0};
+    for (int ul = tid; ul < nyl; ul += nthr) {
+      const int kl = ul / W, ll = ul - kl * W, kk = kb + kl;
+      const int y1 = k0 + kk, y2 = l0 + ll, y = y1 * N + y2;
+      double nuJ = 0.0;
+#pragma unroll
+      for (int q4 = 0; q4 < 4; ++q4) nuJ += box_value(dbox[q4], arena, y1, y2);
+      const double num = fmax(0.0, S.PY[y] - nuJ);
+      const R rho = R(num) / R(S.nu[y]);
+      lrho[ul] = rho > R(0) ? dd_lg2(rho) * R(DD_LN2) : -dd_inf<R>();
+      lnu[ul] = R(S.lognu[y]);
+      m3[0] += nuJ; m3[1] += nuJ * kk; m3[2] += nuJ * ll;
+    }
+    block_sum<3>(m3, red);
+    if (tid == 0)
+      for (int r = 0; r < C; ++r) {
+        double* px = cl.map_shared_rank(dx, r);
+        for (int k = 0; k < 3; ++k) px[crank * 16 + k] = m3[k];
+      }
+    csync();
+    double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+    for (int r = 0; r < C; ++r) { t0 += dx[r * 16]; t1 += dx[r * 16 + 1]; t2 += dx[r * 16 + 2]; }
+    c1 = H / 2; c2 = W / 2;
+    if (t0 > 0.0) {
+      c1 = min(H - 1, max(0, (int)lrint(t1 / t0)));
+      c2 = min(W - 1, max(0, (int)lrint(t2 / t0)));
+    }
+  }
+  const int xc1 = cd.i0 + nx1 / 2, xc2 = cd.j0 + nx2 / 2;
+  const int yc1 = k0 + c1, yc2 = l0 + c2;
+  const int D1 = xc1 - yc1, D2 = xc2 - yc2;
+  const int offr = (k0 - cd.i0) + D1, offc = (l0 - cd.j0) + D2;
+  const double eps = S.eps, lam = S.lam;
+  const double q = S.h * S.h / eps;
+  const double sl = eps / lam;
+  const double rr = lam / (eps + lam);
+  const R q2 = R(q * DD_LOG2E), qR = R(q), sR = R(sl), rR = R(rr);
+
+  // ------------------------------------------------------- load X side (every CTA)
+  const double inv_eps = 1.0 / eps;
+  double acc2[2] = {0.0, 0.0};
+  for (int t = tid; t < nx; t += nthr) {
+    const int r = t / nx2, c = t - r * nx2;
+    const int x = (cd.i0 + r) * N + cd.j0 + c;
+    const int xi1 = cd.i0 + r - xc1, xi2 = cd.j0 + c - xc2;
+    acc2[0] += S.alpha[x] * inv_eps - 2.0 * q * (double)(D1 * xi1 + D2 * xi2);
+    acc2[1] += S.mu[x];
+  }
+  block_sum<2>(acc2, red);
+  const double A = acc2[0] / nx;
+  const double muJ = acc2[1];
+  const double qD2 = q * (double)(D1 * D1 + D2 * D2);
+  const R sB = R(sl * (qD2 - A));
+  const R cEta1 = R(sl * 2.0 * q * D1), cEta2 = R(sl * 2.0 * q * D2);
+  const R cA = R(-(1.0 - rr) * A);
+  const R gA = R(-sl * A);
+  const R cD1 = R(2.0 * (1.0 - rr) * q * D1), cD2 = R(2.0 * (1.0 - rr) * q * D2);
+  for (int t = tid; t < nx; t += nthr) {
+    const int r = t / nx2, c = t - r * nx2;
+    const int x = (cd.i0 + r) * N + cd.j0 + c;
+    const int xi1 = cd.i0 + r - xc1, xi2 = cd.j0 + c - xc2;
+    const double lin = 2.0 * q * (double)(D1 * xi1 + D2 * xi2);
+    const R a = R(S.alpha[x] * inv_eps - lin - A);
+    const R l = R(S.logmu[x]);
+    av[t] = a;
+    lm[t] = l;
+    g0[t] = R(-sl * lin);
+    xa[t] = (a + l) * R(DD_LOG2E);
+  }
+  __syncthreads();
+
+  // ------------------------------------------------------- Sinkhorn loop
+  const double tol = S.err * muJ;
+  const R LN2 = R(DD_LN2), L2E = R(DD_LOG2E);
+  int it = 0;
+  double gap = 0.0;
+  bool first = true;
+  R *xa_c = xa, *av_c = av, *xa_n = xa_nx, *av_n = av_nx;
+  for (;;) {
+    ++it;
+    // Y-half, T(r, ll) = log2 sum_c 2^{xa(r,c) - q2 (c - ll - offc)^2}: split, to every CTA
+    {
+      const int nt = nx1 * W, P = lanes_per_target(nt, nx2, gthr), ni = (nt * P + 31) & ~31;
+      for (int i = gtid; i < ni; i += gthr) {
+        const int tg0 = i / P, part = i - tg0 * P, tg = min(tg0, nt - 1);
+        const int r = tg / W, ll = tg - r * W;
+        const R* row = xa_c + r * nx2;
+        const R v = lse2_group<R>([&](int m) { return row[m]; }, nx2, R(ll + offc), q2, T[tg], !first, part, P);
+        __syncwarp();
+        if (part == 0 && tg0 < nt)
+          for (int rk = 0; rk < C; ++rk) *cl.map_shared_rank(T + tg, rk) = v;
+      }
+    }
+    csync();
+    // Y-half on the own rows: Z(kk, ll) = log2 sum_r 2^{T(r,ll) - q2 (r - kk - offr)^2}, Newton (a3)
+    if (nyl * 2 > nthr) {
+      const int rounds = (nyl + 2 * nthr - 1) / (2 * nthr);
+      for (int rd = 0; rd < rounds; ++rd) {
+        const int u = tid + rd * 2 * nthr;
+        const int uu[2] = {min(u, nyl - 1), min(u + nthr, nyl - 1)};
+        const bool ok[2] = {u < nyl, u + nthr < nyl};
+        R lr[2], c0[2], uw[2], root[2], Zn[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int kl = uu[k] / W, ll = uu[k] - kl * W, kk = kb + kl;
+          const R Z2 =
+              lse2_group<R>([&](int m) { return T[m * W + ll]; }, nx1, R(kk + offr), q2, Zv[uu[k]], !first, 0, 1);
+          Zn[k] = Z2 * LN2;
+          const R eta1 = R(k0 + kk - yc1), eta2 = R(l0 + ll - yc2);
+          c0[k] = sB - cEta1 * eta1 - cEta2 * eta2 - sR * Zn[k];
+          lr[k] = lrho[uu[k]];
+          uw[k] = first ? dd_inf<R>() : bv[uu[k]] + Zn[k];
+        }
+        newton_u2<R>(lr, c0, uw, sR, S.newton_maxit, root);
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          if (!ok[k]) continue;
+          Zv[uu[k]] = Zn[k] * L2E;
+          const R b = root[k] - Zn[k];
+          bv[uu[k]] = b;
+          bl[uu[k]] = (b + lnu[uu[k]]) * L2E;
+        }
+      }
+    } else {
+      const int P = lanes_per_target(nyl, nx1, nthr), ni = (nyl * P + 31) & ~31;
+      for (int i = tid; i < ni; i += nthr) {
+        const int u0 = i / P, part = i - u0 * P, u = min(u0, nyl - 1);
+        const int kl = u / W, ll = u - kl * W, kk = kb + kl;
+        const R Z2 = lse2_group<R>([&](int m) { return T[m * W + ll]; }, nx1, R(kk + offr), q2, Zv[u], !first,
+                                   part, P);
+        __syncwarp();
+        if (part == 0 && u0 < nyl) Zv[u] = Z2;
+      }
+      __syncthreads();
+      for (int u = tid; u < nyl; u += 2 * nthr) {
+        const int uu[2] = {u, min(u + nthr, nyl - 1)};
+        R lr[2], c0[2], uw[2], root[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int kl = uu[k] / W, ll = uu[k] - kl * W, kk = kb + kl;
+          const R Zn = Zv[uu[k]] * LN2;
+          const R eta1 = R(k0 + kk - yc1), eta2 = R(l0 + ll - yc2);
+          c0[k] = sB - cEta1 * eta1 - cEta2 * eta2 - sR * Zn;
+          lr[k] = lrho[uu[k]];
+          uw[k] = first ? dd_inf<R>() : bv[uu[k]] + Zn;
+        }
+        newton_u2<R>(lr, c0, uw, sR, S.newton_maxit, root);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          if (k == 1 && u + nthr >= nyl) break;
+          const R b = root[k] - Zv[uu[k]] * LN2;
+          bv[uu[k]] = b;
+          bl[uu[k]] = (b + lnu[uu[k]]) * L2E;
+        }
+      }
+    }
+    __syncthreads();
+    // X-half on the own rows: U(kl, c) = log2 sum_ll 2^{bl(kl,ll) - q2 (ll - (c - offc))^2}
+    {
+      const int nt = Hl * nx2, P = lanes_per_target(nt, W, nthr), ni = (nt * P + 31) & ~31;
+      for (int i = tid; i < ni; i += nthr) {
+        const int tg0 = i / P, part = i - tg0 * P, tg = min(tg0, nt - 1);
+        const int kl = tg / nx2, c = tg - kl * nx2;
+        const R* row = bl + kl * W;
+        const R v = lse2_group<R>([&](int m) { return row[m]; }, W, R(c - offc), q2, U[tg], !first, part, P);
+        __syncwarp();
+        if (part == 0 && tg0 < nt) U[tg] = v;
+      }
+    }
+    __syncthreads();
+    // the own rows' part of W(r, c) = log2 sum_kk 2^{U(kk,c) - q2 (kk - (r - offr))^2}, to every CTA
+    if (Hl > 0) {
+      const int P = lanes_per_target(nx, Hl, nthr), ni = (nx * P + 31) & ~31;
+      for (int i = tid; i < ni; i += nthr) {
+        const int tg0 = i / P, part = i - tg0 * P, t = min(tg0, nx - 1);
+        const int r = t / nx2, c = t - r * nx2;
+        const R v = lse2_group<R>([&](int m) { return U[m * nx2 + c]; }, Hl, R(r - offr - kb), q2, Wp[t], !first,
+                                  part, P);
+        __syncwarp();
+        if (part == 0 && tg0 < nx) {
+          Wp[t] = v;
+          for (int rk = 0; rk < C; ++rk) *cl.map_shared_rank(Wx + crank * cap_nx + t, rk) = v;
+        }
+      }
+    } else {
+      for (int t = tid; t < nx; t += nthr)
+        for (int rk = 0; rk < C; ++rk) *cl.map_shared_rank(Wx + crank * cap_nx + t, rk) = -dd_inf<R>();
+    }
+    csync();
+    // combine the parts (rank order: every CTA gets the same W), gap terms (a4), next alpha (a2)
+    double gl = 0.0;
+    for (int t = tid; t < nx; t += nthr) {
+      R mx = -dd_inf<R>();
+      for (int rk = 0; rk < C; ++rk) mx = max(mx, Wx[rk * cap_nx + t]);
+      R W2 = mx;
+      if (mx > -dd_inf<R>()) {
+        R acc = R(0);
+        for (int rk = 0; rk < C; ++rk) acc += dd_ex2(Wx[rk * cap_nx + t] - mx);
+        W2 = mx + dd_lg2(acc);
+      }
+      Wv[t] = W2;
+      const int r = t / nx2, c = t - r * nx2;
+      const R a = av_c[t];
+      const R tt = a + W2 * LN2;         // log(P_X pi / mu)
+      const R g = gA + g0[t] - sR * a;   // -alpha/lam
+      gl += (double)(dd_ex2((lm[t] + g) * L2E) * dd_psi<R>(tt - g));
+      const R xi1 = R(cd.i0 + r - xc1), xi2 = R(cd.j0 + c - xc2);
+      const R an = cA - rR * W2 * LN2 - cD1 * xi1 - cD2 * xi2;
+      av_n[t] = an;
+      xa_n[t] = (an + lm[t]) * L2E;
+    }
+    {
+      double gv[1] = {gl};
+      block_sum<1>(gv, red);
+      gap = gv[0];
+    }
+    first = false;
+    if ((S.err >= 0.0 && gap <= tol) || it >= S.maxit || !(gap == gap)) break;
+    R* tp = av_c; av_c = av_n; av_n = tp;
+    tp = xa_c; xa_c = xa_n; xa_n = tp;
+  }
+  const bool nonfinite = !(gap == gap);
+
+  // ------------------------------------------------------- epilogue (a5)
+  const double th_s = 1.0 / nbatch;
+  double dk[2] = {0.0, 0.0};
+  if (crank == 0) {
+    for (int t = tid; t < nx; t += nthr) {
+      const int r = t / nx2, c = t - r * nx2;
+      const int x = (cd.i0 + r) * N + cd.j0 + c;
+      const int xi1 = cd.i0 + r - xc1, xi2 = cd.j0 + c - xc2;
+      S.alpha[x] = eps * (A + (double)av_c[t] + 2.0 * q * (double)(D1 * xi1 + D2 * xi2));
+      const double p1 = (double)dd_ex2((lm[t] + av_c[t]) * L2E + Wv[t]);
+      S.PXnew[x] = p1;
+      const double p0 = S.PX[x];
+      if (sizeof(R) == 8) {
+        const double m = S.mu[x];
+        const double ps = (1.0 - th_s) * p0 + th_s * p1;
+        const double k0v = dd_kl_term(p0, m);
+        dk[0] += dd_kl_term(p1, m) - k0v;
+        dk[1] += dd_kl_term(ps, m) - k0v;
+      } else {
+        dk[0] += kl_change_f(p0, p1 - p0, lm[t]);
+        dk[1] += kl_change_f(p0, th_s * (p1 - p0), lm[t]);
+      }
+    }
+    block_sum<2>(dk, red);
+  }
+  R hs[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) hs[k] = R(0);
+  const int nhr = nx1 > s ? 2 : 1, nhc = nx2 > s ? 2 : 1;
+  int nst;
+  double* nut;
+  {
+    CellOut tmp;
+    tmp.slot = slot;
+    nut = cell_nut(S, tmp, cidx, &nst);
+  }
+  // rows of X against the columns of B_J per column half (split, to every CTA);
+  // the region T .. Zv is free after the loop
+  R* Te = T;
+  R* Ma = T + nx1 * W;
+  R* Md = Ma + nx1 * W;
+  for (int hc = 0; hc < nhc; ++hc) {
+    const int cb = hc * s, ce = min(nx2, cb + s);
+    for (int t = gtid; t < nx1 * W; t += gthr) {
+      const int r = t / W, ll = t - r * W;
+      const R* row = xa_c + r * nx2;
+      const R ctr = R(ll + offc);
+      const R T2 = lse2_1d<R>([&](int m) { return row[cb + m]; }, ce - cb, ctr - R(cb), q2, R(0), false);
+      R sw = 0, sa = 0, sd = 0;
+      for (int c = cb; c < ce; ++c) {
+        const R d = R(c) - ctr;
+        const R w = dd_ex2(row[c] - q2 * d * d - T2);
+        sw += w;
+        sa += w * (av_c[r * nx2 + c] - qR * d * d);
+        const R dt = d + R(D2);
+        sd += w * dt * dt;
+      }
+      const R isw = R(1) / sw;
+      for (int rk = 0; rk < C; ++rk) {
+        *cl.map_shared_rank(Te + t, rk) = T2;
+        *cl.map_shared_rank(Ma + t, rk) = sa * isw;
+        *cl.map_shared_rank(Md + t, rk) = sd * isw;
+      }
+    }
+    csync();
+    for (int ul = tid; ul < nyl; ul += nthr) {
+      const int kl = ul / W, ll = ul - kl * W, kk = kb + kl;
+      const int u = kk * W + ll;
+      const int y = (k0 + kk) * N + l0 + ll;
+      const R ctr = R(kk + offr);
+      const double nuy = S.nu[y];
+      for (int hr = 0; hr < nhr; ++hr) {
+        const int rb = hr * s, re = min(nx1, rb + s);
+        const R P2 = lse2_1d<R>([&](int m) { return Te[(rb + m) * W + ll]; }, re - rb, ctr - R(rb), q2, R(0), false);
+        R sw = 0, sa = 0, sd = 0;
+        for (int r = rb; r < re; ++r) {
+          const R d = R(r) - ctr;
+          const R w = dd_ex2(Te[r * W + ll] - q2 * d * d - P2);
+          sw += w;
+          sa += w * (Ma[r * W + ll] - qR * d * d);
+          const R dt = d + R(D1);
+          sd += w * (dt * dt + Md[r * W + ll]);
+        }
+        const R isw = R(1) / sw;
+        const int qd = 2 * hr + hc;
+        const R ntv = R(nuy) * dd_ex2(bv[ul] * L2E + P2);
+        nut[qd * nst + u] = (double)ntv;
+        hs[qd] += ntv * (sa * isw + bv[ul]);
+        hs[4 + qd] += ntv * (sd * isw);
+        hs[8 + qd] += ntv;
+      }
+    }
+    csync();   // Te/Ma/Md are rewritten by the next column half
+  }
+  // change of P_Y pi for the step-size decision (own rows)
+  for (int ul = tid; ul < nyl; ul += nthr) {
+    const int kl = ul / W, ll = ul - kl * W, kk = kb + kl;
+    const int u = kk * W + ll;
+    const int y1 = k0 + kk, y2 = l0 + ll;
+    double dlt = 0.0;
+#pragma unroll
+    for (int q4 = 0; q4 < 4; ++q4) {
+      if (cd.mem[q4] < 0) continue;
+      const int hr = q4 >> 1, hc = q4 & 1;
+      if (hr >= nhr || hc >= nhc) continue;
+      dlt += nut[q4 * nst + u] - box_value(dbox[q4], arena, y1, y2);
+    }
+    if (dlt != 0.0) atomicAdd(S.dPY + y1 * N + y2, dlt);
+  }
+  double hsd[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) hsd[k] = (double)hs[k];
+  block_sum<12>(hsd, red);
+  if (tid == 0) {
+    double* p0 = cl.map_shared_rank(dx, 0);
+    for (int k = 0; k < 12; ++k) p0[crank * 16 + k] = hsd[k];
+  }
+  csync();
+  if (crank != 0 || tid != 0) return;
+  for (int k = 0; k < 12; ++k) {
+    double a = 0.0;
+    for (int r = 0; r < C; ++r) a += dx[r * 16 + k];
+    hsd[k] = a;
+  }
+  CellOut o;
+  o.k0 = k0; o.l0 = l0; o.H = H; o.W = W;
+  o.iters = it;
+  o.status = nonfinite ? CELL_NONFINITE : ((S.err >= 0.0 && gap > tol) ? CELL_MAXIT : CELL_OK);
+  o.D1 = D1; o.D2 = D2;
+  o.slot = slot; o.pad = 0;
+  o.gap = gap;
+  o.dKX[0] = dk[0]; o.dKX[1] = dk[1];
+  for (int q4 = 0; q4 < 4; ++q4) {
+    const int bi = cd.mem[q4];
+    o.Ct[q4] = S.h * S.h * hsd[4 + q4];
+    o.mass[q4] = hsd[8 + q4];
+    o.Ht[q4] = bi >= 0 ? hsd[q4] - hsd[8 + q4] + S.muinu[bi] : 0.0;
+  }
+  *out = o;
+  atomicAdd(S.counters + 0, (unsigned long long)it);
+  atomicAdd(S.counters + 1, 1ull);
+  if (o.status == CELL_MAXIT) atomicAdd(S.counters + 2, 1ull);
+  atomicMax(S.counters + 5, (unsigned long long)it);
+  atomicMax(S.counters + 6, (unsigned long long)(H * W));
+  atomicAdd(S.counters + 8, (unsigned long long)(H * W));
+  atomicAdd(S.counters + 7, (unsigned long long)it *
+                                (unsigned long long)(nx1 * W * nx2 + H * W * nx1 + H * nx2 * W + nx * H));
+  if (nonfinite) atomicOr(S.status, ST_NONFINITE);
+}
+
+// One sub-batch, persistent grid over the resident CTAs in clusters of
+// C = S.dist_c.  Phase 1 (C > 1): each cluster takes the next of the first
+// nbig cells of `order` (the largest) and solves it with all its CTAs
+// (cell_solve_dist).  Phase 2: every CTA takes the remaining cells one at a
+// time (cell_solve_body on one CTA).  The order (largest estimated work first
+// within each phase, k_cell_order) only decides when a cell starts; the
+// results do not depend on it.
 template <typename R>
 __global__ void __launch_bounds__(512, 1)
-k_cell_solve(DevState S, const CellDesc* __restrict__ cells, int begin, int nbatch, int csize) {
+k_cell_solve(DevState S, const CellDesc* __restrict__ cells, const int* __restrict__ order,
+             const int* __restrict__ nbig_p, int begin, int nbatch) {
   namespace cg = cooperative_groups;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int crank = csize > 1 ? (int)cg::this_cluster().block_rank() : 0;
-  const int cidx = blockIdx.x / csize;
-  // the partner CTA must have started before its shared memory is written
-  if (csize > 1) cg::this_cluster().sync();
-  cell_solve_body<R>(S, cells[begin + cidx], cidx, nbatch, csize, crank, smem_raw);
+  __shared__ int sj;
+  const int C = S.dist_c;
+  const int nbig = (C > 1 && order) ? *nbig_p : 0;
+  if (C > 1) {
+    const int crank = (int)cg::this_cluster().block_rank();
+    // every CTA of the cluster must have started before one writes another's shared memory
+    cg::this_cluster().sync();
+    for (;;) {
+      if (crank == 0 && threadIdx.x == 0) {
+        const int j = (int)atomicAdd(S.queue, 1u);
+        for (int r = 0; r < C; ++r) *cg::this_cluster().map_shared_rank(&sj, r) = j;
+      }
+      cg::this_cluster().sync();
+      const int j = sj;
+      if (j >= nbig) break;
+      const int cidx = order[begin + j];
+      cell_solve_dist<R>(S, cells[begin + cidx], cidx, nbatch, crank, smem_raw);
+      cg::this_cluster().sync();
+    }
+  }
+  // no shared memory of another CTA is touched from here on
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) sj = (int)atomicAdd(S.queue + 1, 1u);
+    __syncthreads();
+    const int j = nbig + sj;
+    if (j >= nbatch) break;
+    const int cidx = order ? order[begin + j] : j;
+    cell_solve_body<R>(S, cells[begin + cidx], cidx, nbatch, 1, 0, smem_raw);
+  }
+}
+
+// Estimated work of one cell solve iteration: the exp terms of the four
+// separable passes, nx1 nx2 (W + H) + H W (nx1 + nx2), from the member boxes;
+// H, W: the cell's Y box.
+__device__ __forceinline__ unsigned int cell_cost(const DevState& S, const CellDesc& cd, int* Hout, int* Wout) {
+  int k0 = 1 << 30, l0 = 1 << 30, k1 = -1, l1 = -1;
+  for (int q = 0; q < 4; ++q) {
+    if (cd.mem[q] < 0) continue;
+    const BoxRec b = S.box[cd.mem[q]];
+    if (b.H * b.W == 0) continue;
+    k0 = min(k0, b.k0); l0 = min(l0, b.l0);
+    k1 = max(k1, b.k0 + b.H); l1 = max(l1, b.l0 + b.W);
+  }
+  if (k1 < 0) {
+    *Hout = *Wout = 0;
+    return 1u;
+  }
+  const long long H = min(S.N, k1 + S.margin) - max(0, k0 - S.margin);
+  const long long W = min(S.N, l1 + S.margin) - max(0, l0 - S.margin);
+  *Hout = (int)H;
+  *Wout = (int)W;
+  const long long c = (long long)cd.nx1 * cd.nx2 * (W + H) + H * W * (cd.nx1 + cd.nx2);
+  return (unsigned int)min(c + 1, 0x7fffffffLL);
+}
+
+constexpr int kOrderMax = 4096;   // largest batch sorted (larger ones keep their index order)
+
+// Order of the cells of each sub-batch of partition `part` (block b:
+// sub-batch b; one block for the whole partition when not staggered) and the
+// number of leading cells that a whole cluster solves.  mode 0: a cell goes
+// to a cluster if it fits the cluster layout and either does not fit one CTA
+// or its work exceeds twice the mean work per CTA (`slots` CTAs); mode 1:
+// every cell that fits the cluster layout; mode 2: none.  Within each group
+// the cells are sorted by decreasing work (bitonic sort of (group, cost,
+// index) keys in shared memory; ties keep the index order).
+__global__ void __launch_bounds__(1024) k_cell_order(DevState S, int part, int mode, int slots) {
+  __shared__ unsigned long long key[kOrderMax];
+  __shared__ double red[33];
+  const int b = blockIdx.x;
+  const int begin = S.staggered ? S.sub_start[part][b] : 0;
+  const int end = S.staggered ? S.sub_start[part][b + 1] : S.sub_start[part][4];
+  const int n = end - begin;
+  int* out = S.order[part] + begin;
+  int* nbig = S.nbig + part * 4 + b;
+  if (n <= 0) {
+    if (threadIdx.x == 0) *nbig = 0;
+    return;
+  }
+  int P = 1;
+  while (P < n) P <<= 1;
+  if (P > kOrderMax) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) out[i] = i;
+    if (threadIdx.x == 0) *nbig = 0;
+    return;
+  }
+  const CellDesc* cells = S.cells[part];
+  const int C = S.dist_c;
+  double tot[1] = {0.0};
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    int H, W;
+    tot[0] += (double)cell_cost(S, cells[begin + i], &H, &W);
+  }
+  block_sum<1>(tot, red);
+  const double thr = 2.0 * tot[0] / (double)max(1, slots);
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    unsigned long long k = 0ull;
+    if (i < n) {
+      int H, W;
+      const unsigned int cost = cell_cost(S, cells[begin + i], &H, &W);
+      const int hl = C > 0 ? (H + C - 1) / C : H;
+      const bool fits_dist = C > 1 && H >= C && W <= S.dist_cap_w && hl <= S.dist_cap_hl && hl * W <= S.dist_cap_nyl;
+      const bool fits_one = H <= S.cap_side && W <= S.cap_side && H * W <= S.cap_ny;
+      const bool big = mode != 2 && fits_dist && (mode == 1 || !fits_one || (double)cost > thr);
+      k = ((unsigned long long)big << 62) | ((unsigned long long)cost << 30) | (0x3fffffffu - (unsigned)i);
+    }
+    key[i] = k;
+  }
+  __syncthreads();
+  // descending bitonic sort
+  for (int k = 2; k <= P; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const unsigned long long a = key[i], c = key[ixj];
+          const bool first_half = (i & k) == 0;
+          if (first_half ? (a < c) : (a > c)) { key[i] = c; key[ixj] = a; }
+        }
+      }
+      __syncthreads();
+    }
+  int cnt = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    out[i] = (int)(0x3fffffffu - (unsigned)(key[i] & 0x3fffffffull));
+    cnt += (int)((key[i] >> 62) & 1ull);
+  }
+  double cv[1] = {(double)cnt};
+  block_sum<1>(cv, red);
+  if (threadIdx.x == 0) *nbig = (int)cv[0];
+}
+
+cudaError_t launch_cell_order(const DevState& S, int part, int mode, int slots, cudaStream_t st) {
+  k_cell_order<<<S.staggered ? 4 : 1, 1024, 0, st>>>(S, part, mode, slots);
+  return cudaGetLastError();
 }
 
 // Many independent instances: a persistent grid takes (instance, cell) items
@@ -946,7 +1613,26 @@ size_t cell_smem_bytes(int s, int cap_side, int cap_ny, int precision) {
   return 32 * 16 * sizeof(double) + rs * (7 * cap_nx + 2 * tsz + 5 * (size_t)cap_ny);
 }
 
-// Largest number of 2-CTA clusters of the cell kernel that can be resident at once.
+// Shared memory of the cluster-distributed layout (cell_solve_dist).
+size_t dist_smem_bytes(int s, int C, int cap_w, int cap_hl, int cap_nyl, int precision) {
+  const size_t rs = precision ? sizeof(double) : sizeof(float), cap_nx = 4 * (size_t)s * s;
+  return 32 * 16 * sizeof(double) +
+         rs * ((8 + (size_t)C) * cap_nx + 2 * (size_t)s * cap_w + 2 * (size_t)s * cap_hl + 5 * (size_t)cap_nyl);
+}
+
+// Static shared memory of the cell kernels (the dynamic part must leave room for it).
+int cell_static_smem(int precision) {
+  cudaFuncAttributes fa;
+  cudaError_t e = precision ? cudaFuncGetAttributes(&fa, k_cell_solve<double>)
+                            : cudaFuncGetAttributes(&fa, k_cell_solve<float>);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 4096;
+  }
+  return (int)fa.sharedSizeBytes;
+}
+
+// Largest number of 2-CTA clusters of the many-instance kernel resident at once.
 int cell_max_pair_clusters(int s, int cap_side, int cap_ny, int precision) {
   size_t smem = cell_smem_bytes(s, cap_side, cap_ny, precision);
   cudaLaunchConfig_t cfg = {};
@@ -963,11 +1649,11 @@ int cell_max_pair_clusters(int s, int cap_side, int cap_ny, int precision) {
   int n = 0;
   cudaError_t e;
   if (precision) {
-    cudaFuncSetAttribute(k_cell_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    e = cudaOccupancyMaxActiveClusters(&n, k_cell_solve<double>, &cfg);
+    cudaFuncSetAttribute(k_cell_solve_multi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaOccupancyMaxActiveClusters(&n, k_cell_solve_multi<double>, &cfg);
   } else {
-    cudaFuncSetAttribute(k_cell_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    e = cudaOccupancyMaxActiveClusters(&n, k_cell_solve<float>, &cfg);
+    cudaFuncSetAttribute(k_cell_solve_multi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaOccupancyMaxActiveClusters(&n, k_cell_solve_multi<float>, &cfg);
   }
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -976,28 +1662,74 @@ int cell_max_pair_clusters(int s, int cap_side, int cap_ny, int precision) {
   return n;
 }
 
-// csize = 2 launches one 2-CTA cluster per cell, csize = 1 one CTA per cell.
-cudaError_t launch_cell_solve(const DevState& S, const CellDesc* cells, int begin, int nbatch,
-                              int precision, int csize, cudaStream_t st) {
-  size_t smem = cell_smem_bytes(S.s, S.cap_side, S.cap_ny, precision);
+// Resident CTAs of the single-instance cell kernel with `smem` dynamic bytes:
+// C == 1 single CTAs, C > 1 the CTAs of the resident C-CTA clusters (0 if such
+// clusters cannot be scheduled).
+int cell_resident_ctas(size_t smem, int C, int precision) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e;
+  if (precision) e = cudaFuncSetAttribute(k_cell_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  else e = cudaFuncSetAttribute(k_cell_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (C <= 1) {
+    int per = 0;
+    e = precision ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cell_solve<double>, 512, smem)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cell_solve<float>, 512, smem);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return nsm > 0 ? nsm : 1;
+    }
+    return std::max(1, per * nsm);
+  }
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(nbatch * csize);
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(512);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  e = precision ? cudaOccupancyMaxActiveClusters(&n, k_cell_solve<double>, &cfg)
+                : cudaOccupancyMaxActiveClusters(&n, k_cell_solve<float>, &cfg);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n * C;
+}
+
+// One sub-batch: `nctas` persistent CTAs (a multiple of S.dist_c, at most the
+// resident ones) in clusters of S.dist_c, `smem` dynamic bytes.
+cudaError_t launch_cell_solve(const DevState& S, const CellDesc* cells, const int* order, const int* nbig_p,
+                              int begin, int nbatch, int precision, size_t smem, int nctas, cudaStream_t st) {
+  const int C = std::max(1, S.dist_c);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(std::max(C, nctas / C * C));
   cfg.blockDim = dim3(512);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = csize;
+  attr[0].val.clusterDim.x = C;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = C > 1 ? 1 : 0;
   if (precision) {
     cudaFuncSetAttribute(k_cell_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    return cudaLaunchKernelEx(&cfg, k_cell_solve<double>, S, cells, begin, nbatch, csize);
+    return cudaLaunchKernelEx(&cfg, k_cell_solve<double>, S, cells, order, nbig_p, begin, nbatch);
   }
   cudaFuncSetAttribute(k_cell_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  return cudaLaunchKernelEx(&cfg, k_cell_solve<float>, S, cells, begin, nbatch, csize);
+  return cudaLaunchKernelEx(&cfg, k_cell_solve<float>, S, cells, order, nbig_p, begin, nbatch);
 }
 
 cudaError_t launch_cell_solve_multi(const DevState* states, const CellRef* refs, int nref, int part,

@@ -47,6 +47,8 @@ struct DevState {
   double* line;                 // GetWeights_line state (16 doubles)
   int balance;                  // balancing step after each cell solve (0/1; one CTA per cell)
   int cap_ny, cap_side;
+  int cap_nut;                  // new marginals per quadrant in a cell position's buffer (>= cap_ny, and the
+                                //   cluster capacity dist_c * dist_cap_nyl)
   unsigned char* spill;         // spill slots: Y-side arrays and new marginals of cells too large
   long long spill_stride;       //   for shared memory (bytes per slot)
   long long spill_nut_off;      //   byte offset of the new marginals (4 N^2 doubles) inside a slot
@@ -62,11 +64,11 @@ struct DevState {
   unsigned long long* head;     // bump allocator of the live arena
   long long cap;                // capacity of each arena (doubles)
   CellOut* cout;
-  double* nut;                  // per cell position: 4 * cap_ny new marginals
+  double* nut;                  // per cell position: 4 * cap_nut new marginals
   double* theta;                // device scalar: last theta
   double* declog;               // per sub-batch: E0, E(1), E(safe), theta
   unsigned long long* counters; // 0 cell_iters, 1 cell_solves, 2 maxit cells, 3 greedy, 4 safe, 5 max iters,
-                                // 6 max ny, 7 lse terms
+                                // 6 max ny, 7 lse terms, 8 Y-box points of the cell solves
   int* status;
   double* red;                  // reduction scratch
   unsigned int* red_count;
@@ -76,6 +78,16 @@ struct DevState {
   int staggered;                // 1: four sub-batches per sweep, 0: one batch of all cells
   unsigned long long* slotctr;  // decision-log records written so far
   long long* newoff;            // compaction scratch: nbasic + 1 offsets
+  unsigned int* queue;          // work queues of the persistent cell kernel: [0] cluster phase,
+                                //   [1] single-CTA phase (reset by k_decide)
+  int* order[2];                // per partition: cells of each sub-batch, cluster cells first, each
+                                //   group by decreasing estimated work (k_cell_order)
+  int* nbig;                    // [part * 4 + sub]: leading cells of the order solved by a whole cluster
+  // capacities of the cluster-distributed cell solve (one cell over dist_c CTAs, split by Y rows)
+  int dist_c;                   // CTAs per cluster (1: no cluster phase)
+  int dist_cap_w;               // largest Y-box width
+  int dist_cap_hl;              // largest number of Y rows per CTA
+  int dist_cap_nyl;             // largest number of Y points per CTA
 };
 
 #define DD_LOGCAP 4096          // decision-log records kept per instance
@@ -196,6 +208,6 @@ __device__ __forceinline__ double* cell_nut(const DevState& S, const CellOut& o,
     *stride = S.N * S.N;
     return reinterpret_cast<double*>(S.spill + (long long)o.slot * S.spill_stride + S.spill_nut_off);
   }
-  *stride = S.cap_ny;
-  return S.nut + (long long)j * 4 * S.cap_ny;
+  *stride = S.cap_nut;
+  return S.nut + (long long)j * 4 * S.cap_nut;
 }

@@ -19,26 +19,27 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// kProbeUnroll independent ex2 per loop pass; the asm is volatile so that no
-// instruction is hoisted or merged, and every result register is distinct.
+// kProbeUnroll independent chains x <- 2^{-x} per thread (each ex2 takes the
+// previous one's result, so nothing can be hoisted out of the loop; the
+// values stay in [0.5, 0.71], no special cases).
 __global__ void __launch_bounds__(kProbeThreads)
 k_probe_ex2(int iters, float seed, float* sink, long long* clk) {
-  float x[kProbeUnroll], y[kProbeUnroll];
+  float x[kProbeUnroll];
 #pragma unroll
-  for (int k = 0; k < kProbeUnroll; ++k) x[k] = seed - 0.03125f * k - 1e-6f * threadIdx.x;
+  for (int k = 0; k < kProbeUnroll; ++k) x[k] = seed + 0.01f * k + 1e-6f * threadIdx.x;
   __syncthreads();
   const long long c0 = clock64();
   const unsigned long long t0 = global_ns();
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
-    for (int k = 0; k < kProbeUnroll; ++k) asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(y[k]) : "f"(x[k]));
+    for (int k = 0; k < kProbeUnroll; ++k) asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(x[k]) : "f"(-x[k]));
   }
   __syncthreads();
   const long long c1 = clock64();
   const unsigned long long t1 = global_ns();
   float acc = 0.f;
 #pragma unroll
-  for (int k = 0; k < kProbeUnroll; ++k) acc += y[k];
+  for (int k = 0; k < kProbeUnroll; ++k) acc += x[k];
   if (acc == 12345.f) sink[threadIdx.x] = acc;
   if (threadIdx.x == 0) {
     clk[4 * blockIdx.x + 0] = c0;
@@ -107,7 +108,7 @@ extern "C" int domdec_probe_peaks(int iters, double out[8], void* stream) {
     float ms = 0.f;
     for (int rep = 0; rep < 2; ++rep) {   // the first launch warms up, the second is timed
       cudaEventRecord(e0, st);
-      if (which == 0) k_probe_ex2<<<grid, kProbeThreads, 0, st>>>(iters, -0.5f, sink, clk);
+      if (which == 0) k_probe_ex2<<<grid, kProbeThreads, 0, st>>>(iters, 0.5f, sink, clk);
       else k_probe_ffma<<<grid, kProbeThreads, 0, st>>>(iters, 0.5f, sink, clk);
       cudaEventRecord(e1, st);
     }

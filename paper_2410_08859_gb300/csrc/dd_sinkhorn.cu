@@ -19,18 +19,6 @@ namespace {
 // of them change the sum by N 2^-cut relative (< 1e-15 in double, < 1e-7 in float).
 template <typename R> __device__ __forceinline__ R cut_log2() { return sizeof(R) == 4 ? R(32) : R(64); }
 
-// Buffers of one separable log-sum-exp: `in`/`tmp`/`out` in R; for R = double
-// the kernels also keep float shadows of `in` and `tmp` (for R = float the
-// shadow pointers alias the arrays themselves).
-template <typename R>
-struct SepBufs {
-  const R* in;
-  const float* inf;
-  R* tmp;
-  float* tmpf;
-  R* out;
-};
-
 // One 1-D log-sum-exp per target with P lanes: the maximum and the window
 // test run in float on the shadow values; only terms within `cut` of the
 // maximum are evaluated (in R) and summed.
@@ -63,43 +51,79 @@ __device__ __forceinline__ R lse_window(FS src, FF srcf, int M, int ctr, double 
   return mx + dd_lg2(acc);
 }
 
+// The same log-sum-exp against a shift `sig` (the previous iteration's value of
+// this target) in one pass: terms more than `cut` below the shift are skipped,
+// so the skipped mass is below N 2^-cut of the sum, as for the max-shifted
+// window.  When the shift is unusable -- NaN, a term more than 60 above it,
+// or a sum outside [2^-30, 2^60] -- the lane group falls back to lse_window
+// (warp-collective: every lane of the warp runs the fallback if one group needs it).
+template <typename R, bool FAST = false, typename FS, typename FF>
+__device__ __forceinline__ R lse_window_shift(FS src, FF srcf, int M, int ctr, double q2, int part, int P, R sig) {
+  const float q2f = (float)q2, sigf = (float)sig;
+  const float cutf = (float)cut_log2<R>() + 1.0f;
+  const R q2r = R(q2);
+  R acc = R(0);
+  bool bad = !(sigf > -INFINITY && sigf < INFINITY);
+  if (!bad) {
+    for (int m = part; m < M; m += P) {
+      const float d = (float)(ctr - m);
+      const float vf = srcf(m) - q2f * d * d - sigf;
+      if (vf > -cutf) {
+        bad |= vf > 60.0f;
+        const R dr = R(ctr - m);
+        if (FAST) acc += R(dd_ex2(float(src(m) - q2r * dr * dr - sig)));
+        else acc += dd_ex2(src(m) - q2r * dr * dr - sig);
+      }
+    }
+  }
+  for (int o = 1; o < P; o <<= 1) {
+    acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    bad |= __shfl_xor_sync(0xffffffffu, (int)bad, o) != 0;
+  }
+  bad |= !(acc >= R(9.313225746154785e-10) && acc <= R(1.152921504606847e18));   // [2^-30, 2^60]
+  if (__any_sync(0xffffffffu, bad)) {
+    const R v = lse_window<R, FAST>(src, srcf, M, ctr, q2, part, P);
+    if (bad) return v;
+  }
+  return sig + dd_lg2(acc);
+}
+
 constexpr int kSepLanes = 4;   // lanes per target in the separable passes
 
-// tmp[k*N + j] = log2 sum_l 2^{in[k*N + l] - q2 (j - l)^2}   (block = row k)
+// Row pass with a transposed store: dst[j*N + k] = log2 sum_l 2^{src[k*N + l] - q2 (j - l)^2}
+// (block = row k).  Applied twice it gives the 2-D log-sum-exp in the original
+// layout (the second pass runs along the columns of the original image), with
+// every source read from shared memory instead of strided global loads.
+// With `shifted`, dst holds the previous iteration's values on entry and each
+// target is evaluated in one pass against its previous value
+// (lse_window_shift); otherwise max-shifted (lse_window).
 template <typename R, bool FAST>
-__global__ void __launch_bounds__(1024) k_sep_rows(SepBufs<R> B, int N, double q2) {
+__global__ void __launch_bounds__(1024)
+k_sep_rows_t(const R* __restrict__ src, const float* __restrict__ srcf, R* dst,
+             float* __restrict__ dstf, int N, double q2, int shifted) {
   extern __shared__ __align__(16) unsigned char sm[];
   R* row = reinterpret_cast<R*>(sm);
   float* rowf = reinterpret_cast<float*>(row + N);
   const int k = blockIdx.x;
   for (int l = threadIdx.x; l < N; l += blockDim.x) {
-    row[l] = B.in[(long long)k * N + l];
-    rowf[l] = B.inf[(long long)k * N + l];
+    row[l] = src[(long long)k * N + l];
+    rowf[l] = srcf[(long long)k * N + l];
   }
   __syncthreads();
   const int P = kSepLanes, nt = (N * P + 31) & ~31;
   for (int i = threadIdx.x; i < nt; i += blockDim.x) {
     const int j0 = i / P, part = i % P, j = min(j0, N - 1);
-    R v = lse_window<R, FAST>([&](int m) { return row[m]; }, [&](int m) { return rowf[m]; }, N, j, q2, part, P);
+    auto srcv = [&](int m) { return row[m]; };
+    auto srcfv = [&](int m) { return rowf[m]; };
+    R v;
+    if (shifted) v = lse_window_shift<R, FAST>(srcv, srcfv, N, j, q2, part, P, dst[(long long)j * N + k]);
+    else v = lse_window<R, FAST>(srcv, srcfv, N, j, q2, part, P);
+    __syncwarp();
     if (part == 0 && j0 < N) {
-      B.tmp[(long long)k * N + j] = v;
-      if (sizeof(R) == 8) B.tmpf[(long long)k * N + j] = (float)v;
+      dst[(long long)j * N + k] = v;
+      if (dstf) dstf[(long long)j * N + k] = (float)v;
     }
   }
-}
-
-// out[i*N + j] = log2 sum_k 2^{tmp[k*N + j] - q2 (i - k)^2}   (block = (j tile, i))
-template <typename R, bool FAST>
-__global__ void __launch_bounds__(256) k_sep_cols(SepBufs<R> B, int N, double q2) {
-  const int P = kSepLanes;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j0 = t / P, part = t % P, j = min(j0, N - 1);
-  const int i = blockIdx.y;
-  const R* col = B.tmp + j;
-  const float* colf = B.tmpf + j;
-  R v = lse_window<R, FAST>([&](int m) { return col[(long long)m * N]; }, [&](int m) { return colf[(long long)m * N]; },
-                      N, i, q2, part, P);
-  if (part == 0 && j0 < N) B.out[(long long)i * N + j] = v;
 }
 
 // Dense: out[x] = log2 sum_y 2^{in[y] - q2 |x - y|^2}, shifted by the previous
@@ -240,29 +264,32 @@ void ti_step(const double* mu, const double* nu, double* alpha, const double* be
 
 template <typename R>
 struct Work {
-  R *in2, *tmp, *w2, *z2;
+  R *in2, *tmp, *w2, *z2, *tmpz;
   float *in2f, *tmpf;  // float shadows (double precision only)
 };
 
 // in2f / tmpf: float shadows (required for R = double; ignored for float).
+// use_shift (separable): tmp and out2 hold this evaluation's previous values
+// (tmp: the row pass, transposed) and every target is summed against them in
+// one pass; otherwise max-shifted.
 template <typename R>
 cudaError_t lse_all(const R* in2, R* tmp, R* out2, int N, double q, int variant, int use_shift, cudaStream_t st,
                     const float* in2f = nullptr, float* tmpf = nullptr, bool fast = false) {
   if (variant == 1) {
-    SepBufs<R> B;
-    B.in = in2;
-    B.inf = sizeof(R) == 8 ? in2f : reinterpret_cast<const float*>(in2);
-    B.tmp = tmp;
-    B.tmpf = sizeof(R) == 8 ? tmpf : reinterpret_cast<float*>(tmp);
-    B.out = out2;
+    const float* inf = sizeof(R) == 8 ? in2f : reinterpret_cast<const float*>(in2);
+    float* tf = sizeof(R) == 8 ? tmpf : nullptr;                       // shadow written by pass 1
+    const float* tfr = sizeof(R) == 8 ? tmpf : reinterpret_cast<const float*>(tmp);
     const double q2 = q * DD_LOG2E;
     const int thr_rows = min(1024, ((N * kSepLanes + 31) / 32) * 32);
+    const size_t sm = N * (sizeof(R) + sizeof(float));
+    // rows, stored transposed; then the rows of that (the original columns), transposed back
+    const int sh = use_shift ? 1 : 0;
     if (fast && sizeof(R) == 8) {
-      k_sep_rows<R, true><<<N, thr_rows, N * (sizeof(R) + sizeof(float)), st>>>(B, N, q2);
-      k_sep_cols<R, true><<<dim3((N * kSepLanes + 255) / 256, N), 256, 0, st>>>(B, N, q2);
+      k_sep_rows_t<R, true><<<N, thr_rows, sm, st>>>(in2, inf, tmp, tf, N, q2, sh);
+      k_sep_rows_t<R, true><<<N, thr_rows, sm, st>>>(tmp, tfr, out2, nullptr, N, q2, sh);
     } else {
-      k_sep_rows<R, false><<<N, thr_rows, N * (sizeof(R) + sizeof(float)), st>>>(B, N, q2);
-      k_sep_cols<R, false><<<dim3((N * kSepLanes + 255) / 256, N), 256, 0, st>>>(B, N, q2);
+      k_sep_rows_t<R, false><<<N, thr_rows, sm, st>>>(in2, inf, tmp, tf, N, q2, sh);
+      k_sep_rows_t<R, false><<<N, thr_rows, sm, st>>>(tmp, tfr, out2, nullptr, N, q2, sh);
     }
   } else {
     R q2 = R(q * DD_LOG2E);
@@ -300,11 +327,12 @@ static int full_sinkhorn_impl(const double* mu, const double* nu, const double* 
   const bool ti = (variant & DOMDEC_SINKHORN_TI) && std::isfinite(lam);
   variant &= ~DOMDEC_SINKHORN_TI;
   Work<R> w;
-  const size_t wbytes = (sizeof(R) * 4 * (size_t)n + sizeof(float) * 2 * (size_t)n + 255) & ~size_t(255);
+  const size_t wbytes = (sizeof(R) * 5 * (size_t)n + sizeof(float) * 2 * (size_t)n + 255) & ~size_t(255);
   *cerr = cudaMallocAsync(&w.in2, wbytes + sizeof(double) * 6 * kRedBlocks, st);
   if (*cerr != cudaSuccess) return -1;
-  w.tmp = w.in2 + n; w.w2 = w.tmp + n; w.z2 = w.w2 + n;
-  w.in2f = reinterpret_cast<float*>(w.z2 + n);
+  // row-pass results of the two half-steps kept apart (each is the next shift of its own half-step)
+  w.tmp = w.in2 + n; w.w2 = w.tmp + n; w.z2 = w.w2 + n; w.tmpz = w.z2 + n;
+  w.in2f = reinterpret_cast<float*>(w.tmpz + n);
   w.tmpf = w.in2f + n;
   double* partials = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(w.in2) + wbytes);
   const int grid = (n + 255) / 256;
@@ -328,7 +356,7 @@ static int full_sinkhorn_impl(const double* mu, const double* nu, const double* 
       k_half<R><<<grid, 256, 0, st>>>(w.w2, kap, alpha, n);
       if (ti) ti_step(mu, nu, alpha, beta, lam, n, d_eval + 6, partials, st);
       k_to_log2<R><<<grid, 256, 0, st>>>(alpha, logmu, 1.0 / e, w.in2, n, w.in2f);
-      lse_all<R>(w.in2, w.tmp, w.z2, N, q, variant, shift_ok, st, w.in2f, w.tmpf, fast);
+      lse_all<R>(w.in2, w.tmpz, w.z2, N, q, variant, shift_ok, st, w.in2f, w.tmpf, fast);
       k_half<R><<<grid, 256, 0, st>>>(w.z2, kap, beta, n);
       k_to_log2<R><<<grid, 256, 0, st>>>(beta, lognu, 1.0 / e, w.in2, n, w.in2f);
       lse_all<R>(w.in2, w.tmp, w.w2, N, q, variant, 1, st, w.in2f, w.tmpf, fast);
@@ -415,10 +443,10 @@ int full_sinkhorn_dev(const double* mu, const double* nu, const double* logmu, c
 // for the life of the process.
 namespace {
 constexpr int kNoAllocMaxN2 = 256 * 256;  // largest grid: N*N <= 65536 (N <= 256)
-// log mu, log nu (N*N doubles each), four N*N work arrays of the log-sum-exp
+// log mu, log nu (N*N doubles each), five N*N work arrays of the log-sum-exp
 // (double-sized slots, also used for float), one N*N double slot holding two
 // float shadow arrays, 8 doubles of reductions and the input-status word.
-constexpr long long kNoAllocDoubles = 7LL * kNoAllocMaxN2 + 16;
+constexpr long long kNoAllocDoubles = 8LL * kNoAllocMaxN2 + 16;
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
 
 // Device address of the scratch array in the current device's context (host
@@ -454,12 +482,13 @@ int full_sinkhorn_noalloc_impl(const double* mu, const double* nu, const double*
                                double* work, double* d_eval, cudaStream_t st, cudaError_t* cerr) {
   const int n = N * N;
   const double h = 1.0 / N;
-  // four work arrays in double-sized slots (float arrays use the first half of each)
+  // five work arrays in double-sized slots (float arrays use the first half of each)
   R* in2 = reinterpret_cast<R*>(work);
   R* tmp = reinterpret_cast<R*>(work + n);
   R* w2 = reinterpret_cast<R*>(work + 2 * (long long)n);
   R* z2 = reinterpret_cast<R*>(work + 3 * (long long)n);
-  float* in2f = reinterpret_cast<float*>(work + 4 * (long long)n);
+  R* tmpz = reinterpret_cast<R*>(work + 4 * (long long)n);
+  float* in2f = reinterpret_cast<float*>(work + 5 * (long long)n);
   float* tmpf = in2f + n;
   const int grid = (n + 255) / 256;
   double evalh[6];
@@ -477,7 +506,7 @@ int full_sinkhorn_noalloc_impl(const double* mu, const double* nu, const double*
     while (it < maxit) {
       k_half<R><<<grid, 256, 0, st>>>(w2, kap, alpha, n);
       k_to_log2<R><<<grid, 256, 0, st>>>(alpha, logmu, 1.0 / e, in2, n, in2f);
-      lse_all<R>(in2, tmp, z2, N, q, variant, shift_ok, st, in2f, tmpf);
+      lse_all<R>(in2, tmpz, z2, N, q, variant, shift_ok, st, in2f, tmpf);
       k_half<R><<<grid, 256, 0, st>>>(z2, kap, beta, n);
       k_to_log2<R><<<grid, 256, 0, st>>>(beta, lognu, 1.0 / e, in2, n, in2f);
       lse_all<R>(in2, tmp, w2, N, q, variant, 1, st, in2f, tmpf);
@@ -535,7 +564,7 @@ int domdec_full_sinkhorn_noalloc(const double* mu, const double* nu, int N, doub
   double* logmu = base;
   double* lognu = base + n;
   double* work = base + 2 * (long long)n;
-  double* d_eval = base + 7LL * kNoAllocMaxN2;
+  double* d_eval = base + 8LL * kNoAllocMaxN2;
   int* d_status = reinterpret_cast<int*>(d_eval + 8);
   // every call starts from a cleared status word and its own beta
   cudaError_t e = cudaMemsetAsync(d_status, 0, sizeof(int), st);

@@ -13,6 +13,12 @@ __device__ __forceinline__ float kl_term_f(double p, double m) {
   return pf * (dd_lg2(pf / mf) * (float)DD_LN2) - pf + mf;
 }
 
+// mu phi(p/mu) in double from log mu (no division).
+__device__ __forceinline__ double kl_term_log(double p, double m, double log_m) {
+  if (p <= 0.0) return m;
+  return p * (log(p) - log_m) - p + m;
+}
+
 // Tracked score (the sum of per-basic-cell transport cost and entropy plus the
 // two exact marginal penalties) and its value after mixing with theta = 1 and
 // theta = 1/|b|; decision on the device, deterministic fixed-order reductions.
@@ -23,22 +29,26 @@ __device__ __forceinline__ void decide_body(const DevState& S, const CellDesc* _
   const int n = S.N * S.N;
   const double lam = S.lam, eps = S.eps, th_s = 1.0 / nbatch;
   double v[5] = {0, 0, 0, 0, 0};
-  // The current score's marginal terms enter only the tie slack and the
-  // leniency test (they cancel in E(1) - E(1/|b|)), so they are summed with
-  // float logarithms.  The decision rests on E(1) - E(1/|b|), whose P_Y part
-  // sum_y [kl(p + d) - kl(p + d/|b|)] is summed in double (two double
-  // logarithms per pixel); E(1) - E alone (the leniency test, the decision
-  // record) takes the current term kl(p) in float.
+  // Every term that changes with the step is summed in double: on the pixels
+  // where the sub-batch changes P_Y (dP_Y != 0) kl(p), kl(p + d) and
+  // kl(p + d/|b|) all take double logarithms, so E(1) - E (the leniency test)
+  // and E(1) - E(1/|b|) (the swift comparison) are exact to double rounding.
+  // The terms that do not change (KL_X, and KL_Y where dP_Y = 0) cancel in both
+  // differences and only set the scale E of the tie slack 1e-12 |E| and of the
+  // leniency tau E (and the logged E): they are summed with float logarithms
+  // (relative error ~1e-7 of E).
   for (int y = bid * blockDim.x + threadIdx.x; y < n; y += nblk * blockDim.x) {
     v[0] += (double)kl_term_f(S.PX[y], S.mu[y]);
-    double p = S.PY[y], m = S.nu[y];
-    const double k0f = (double)kl_term_f(p, m);
-    v[1] += k0f;
-    double d = S.dPY[y];
+    const double p = S.PY[y], d = S.dPY[y];
     if (d != 0.0) {
-      const double k1 = dd_kl_term(fmax(0.0, p + d), m);
-      v[2] += k1 - k0f;
-      v[3] += k1 - dd_kl_term(fmax(0.0, p + th_s * d), m);
+      const double m = S.nu[y], lm = S.lognu[y];
+      const double k0 = kl_term_log(p, m, lm);
+      const double k1 = kl_term_log(fmax(0.0, p + d), m, lm);
+      v[1] += k0;
+      v[2] += k1 - k0;
+      v[3] += k1 - kl_term_log(fmax(0.0, p + th_s * d), m, lm);
+    } else {
+      v[1] += (double)kl_term_f(p, S.nu[y]);
     }
   }
   for (int i = bid * blockDim.x + threadIdx.x; i < S.nbasic; i += nblk * blockDim.x)
@@ -74,7 +84,7 @@ __device__ __forceinline__ void decide_body(const DevState& S, const CellDesc* _
   if (threadIdx.x != 0) return;
   const double dL = tot[5], dKX1 = tot[6], dKXs = tot[7];
   const double E0 = tot[4] + lam * tot[0] + lam * tot[1];
-  const double dg = dL + lam * dKX1 + lam * tot[2];          // E(1) - E (P_Y part against a float kl(p))
+  const double dg = dL + lam * dKX1 + lam * tot[2];          // E(1) - E
   // E(1) - E(1/|b|) in double: the P_Y part directly, the rest as before
   const double dgs = (1.0 - th_s) * dL + lam * (dKX1 - dKXs) + lam * tot[3];
   const double ds = dg - dgs;                                // E(1/|b|) - E
@@ -97,6 +107,7 @@ __device__ __forceinline__ void decide_body(const DevState& S, const CellDesc* _
   }
   *S.red_count = 0u;
   if (S.spill_count) *S.spill_count = 0u;
+  if (S.queue) { S.queue[0] = 0u; S.queue[1] = 0u; }
 }
 
 __global__ void __launch_bounds__(512)

@@ -48,6 +48,7 @@ class domdec_stats(ctypes.Structure):
                 ("cell_iters", ctypes.c_longlong), ("maxit_cells", ctypes.c_longlong),
                 ("greedy_steps", ctypes.c_longlong), ("safe_steps", ctypes.c_longlong),
                 ("box_entries", ctypes.c_longlong), ("lse_terms", ctypes.c_longlong),
+                ("box_points", ctypes.c_longlong),
                 ("max_cell_iters", ctypes.c_int),
                 ("max_ny", ctypes.c_int)]
 
@@ -65,6 +66,7 @@ _SIGS = {
     "domdec_default_params": (None, [ctypes.POINTER(domdec_params)]),
     "domdec_init": (_I, [ctypes.POINTER(_P), _P, _P, _I, ctypes.POINTER(domdec_params), _P, _P, _P]),
     "domdec_iterate": (_I, [_P, _I]),
+    "domdec_reset": (_I, [_P, _P, _P, _P, _P, _D]),
     "domdec_set_eps": (_I, [_P, _D]),
     "domdec_set_tolerance": (_I, [_P, _D]),
     "domdec_sync": (_I, [_P]),
@@ -72,6 +74,7 @@ _SIGS = {
     "domdec_plan_marginals": (_I, [_P, _P, _P]),
     "domdec_duals": (_I, [_P, _P]),
     "domdec_pd_gap": (_I, [_P, _DP, _P]),
+    "domdec_basic_costs": (_I, [_P, _P, _P]),
     "domdec_basic_marginals": (ctypes.c_longlong, [_P, ctypes.POINTER(ctypes.c_int), _P, ctypes.c_longlong]),
     "domdec_get_stats": (_I, [_P, ctypes.POINTER(domdec_stats)]),
     "domdec_decision_log": (_I, [_P, _DP, _I]),
@@ -180,6 +183,12 @@ def domdec_init(mu, nu, N, params, alpha0=None, beta0=None, stream=None):
     return h
 
 
+def domdec_reset(h, mu, nu, N, alpha0=None, beta0=None, eps_init=0.0):
+    n = N * N
+    return _check(lib().domdec_reset(h, _ptr(mu, n), _ptr(nu, n), _ptr(alpha0, n), _ptr(beta0, n),
+                                     float(eps_init)), "domdec_reset")
+
+
 def domdec_iterate(h, n_sweeps):
     return _check(lib().domdec_iterate(h, int(n_sweeps)), "domdec_iterate")
 
@@ -209,6 +218,13 @@ def domdec_plan_marginals(h, PX, PY):
 
 def domdec_duals(h, alpha):
     return _check(lib().domdec_duals(h, _ptr(alpha, writable=True)), "domdec_duals")
+
+
+def domdec_basic_costs(h, nbasic):
+    """(C, H): the tracked transport cost and entropy of every basic cell's plan part."""
+    C, H = np.empty(nbasic), np.empty(nbasic)
+    _check(lib().domdec_basic_costs(h, C.ctypes.data, H.ctypes.data), "domdec_basic_costs")
+    return C, H
 
 
 def domdec_pd_gap(h, beta=None):
@@ -387,6 +403,11 @@ class DomDec:
         domdec_iterate(self.h, n)
         return self
 
+    def reset(self, mu, nu, alpha0=None, beta0=None, eps_init=0.0):
+        """Load a new problem of the same size into this handle (domdec_reset)."""
+        domdec_reset(self.h, mu, nu, self.N, alpha0, beta0, eps_init)
+        return self
+
     def sync(self):
         return domdec_sync(self.h)
 
@@ -417,6 +438,9 @@ class DomDec:
 
     def basic_marginals(self):
         return domdec_basic_marginals(self.h, self.nbasic)
+
+    def basic_costs(self):
+        return domdec_basic_costs(self.h, self.nbasic)
 
     def gradients(self, precision=FP64, grad_mu=None, grad_nu=None, grad_x=None, beta=None):
         """d(score)/d mu, d(score)/d nu, d(score)/d x at the current state

@@ -1,14 +1,16 @@
-"""Full-size checks in the benchmark's launch configuration (FP32 cells, one CTA
-or a 2-CTA cluster per cell, staggered swift, warm start by global Sinkhorn to
-2 eps):
+"""Full-size checks in the benchmark's launch configuration (FP32 cells, the
+automatic choice of one CTA or a cluster per cell, staggered swift, warm start
+by global Sinkhorn to 2 eps):
 
-* blobs256 (256 x 256, s = 8, eps = (1/256)^2) and lognormal1024 (1024 x 1024,
-  s = 16, eps = (2/1024)^2): sampled cells of the first staggered sub-batch
-  against the oracle solving the same cell problems one by one from the GPU's
-  state (fixed iteration count, so that only FP32 against FP64 arithmetic
-  differs), and invariants that hold at any size: P_Y equals the sum of the
-  basic-cell marginals, |P_X| = |P_Y|, the tracked score does not increase over
-  sweeps, and weak duality of the certificate.
+* blobs256 (256 x 256, s = 8, eps = (1/256)^2) at lam = 0.1, 1, 10: every cell
+  of the first staggered sub-batch against the FP64 oracle solving the same
+  cell problems from the GPU's state, both converged to a cell tolerance of
+  1e-7, and the step size against the oracle's own decision;
+* lognormal1024 (1024 x 1024, s = 16, eps = (2/1024)^2): the largest and some
+  random cells of that sub-batch the same way;
+* invariants that hold at any size: P_Y equals the sum of the basic-cell
+  marginals, |P_X| = |P_Y|, the tracked score does not increase over sweeps,
+  and weak duality of the certificate.
 """
 import numpy as np
 import pytest
@@ -35,6 +37,7 @@ def oracle_state(g, geo, mu, nu, eps, lam):
     st = odd.State(geo, mu, nu, eps, lam, 1e-15)
     st.alpha = g.duals()
     st.PX, st.PY = g.marginals()
+    st.Cc, st.Hh = g.basic_costs()
     box, vals = g.basic_marginals()
     pos = 0
     for i in range(geo.nbasic):
@@ -79,51 +82,118 @@ def check_invariants(dd, g, mu, nu, N, s):
     assert cert[1] <= cert[0] + 1e-12 * abs(cert[0])   # weak duality: D <= E_hat
 
 
-@pytest.mark.parametrize("name,ncheck,quick", [("blobs256", 8, False), ("lognormal1024", 4, False)])
-def test_sampled_cells_and_invariants(dd, name, ncheck, quick):
-    import torch
-    mu, nu, N, s, eps, lam, md, nd, a0, b0 = warm_started(dd, torch, name, quick)
-    iters = 20
+def compare_subbatch(dd, torch, name, lam, ncheck, err, maxit, report):
+    """One sweep of partition A in FP32 from the warm start, cells solved to the
+    tolerance `err` on both sides; the cells of staggered sub-batch 0 (all of
+    them, or the `ncheck` largest and `ncheck` random ones) are solved again by
+    the FP64 oracle from the GPU's state before the sweep.  Compares every
+    checked cell's potentials on X_J and its members' new marginals after the
+    mixing with the GPU's theta; with all cells, also theta against the
+    oracle's own GetWeights decision.  Returns the error figures."""
+    mu, nu, spec = inputs.workload(name)
+    N, s, eps = spec["N"], spec["s"], spec["eps"]
+    mu, nu = mu.ravel(), nu.ravel()
+    md = torch.from_numpy(mu.copy()).cuda()
+    nd = torch.from_numpy(nu.copy()).cuda()
+    a0 = torch.empty(N * N, dtype=torch.float64, device="cuda")
+    b0 = torch.empty_like(a0)
+    dd.domdec_full_sinkhorn(md, nd, N, 2 * eps, lam, eps_start=1.0, variant=dd.SINKHORN_SEPARABLE,
+                            precision=dd.MIXED, maxit=4000, err=5e-6, check_every=10, alpha=a0, beta=b0)
+    # the bench's launch configuration (automatic cluster choice), tighter cell tolerance
     g = dd.DomDec(md, nd, eps, lam, s, alpha0=a0, beta0=b0, eps_init=2 * eps, precision="fp32", tau=0.0,
-                  err=-1.0, maxit=iters)
+                  err=err, maxit=maxit)
     geo = odd.Geometry(N, s)
     st = oracle_state(g, geo, mu, nu, eps, lam)
-    scores = [g.score()[0]]
-    g.iterate(1)                     # partition A; sub-batch 0 saw exactly the state read above
+    g.iterate(1)
     g.sync()
-    scores.append(g.score()[0])
     theta = g.decisions()[0][3]
     box, vals = g.basic_marginals()
     starts = np.concatenate([[0], np.cumsum(box[:, 2] * box[:, 3])])
     alpha_new = g.duals()
+    g.close()
     cells = [c for c in geo.parts["A"] if c["sub"] == 0]
-    rng = np.random.default_rng(5)
-    picks = rng.choice(len(cells), ncheck, replace=False)
+    probs_all = [odd.cell_problem(st, c) for c in cells]
+    if ncheck is None:
+        picks = list(range(len(cells)))
+    else:
+        size = [0 if p is None else p["Y"].size for p in probs_all]
+        order = list(np.argsort(size)[::-1])
+        rng = np.random.default_rng(7)
+        rest = order[ncheck:]
+        picks = order[:ncheck] + list(rng.choice(rest, min(ncheck, len(rest)), replace=False))
+    sols = [None] * len(cells)
+    l1_num, mass_tot, worst_cell, worst_alpha = 0.0, 0.0, 0.0, 0.0
     for ci in picks:
-        cell = cells[ci]
-        prob = odd.cell_problem(st, cell)
+        cell, prob = cells[ci], probs_all[ci]
         if prob is None:
             continue
-        sol = odd.solve_cell(st, cell, prob, err=-1.0, maxit=iters)
-        # the cell's potentials after the solve (kept whatever theta, R7)
+        sol = odd.solve_cell(st, cell, prob, err=err, maxit=maxit)
+        sols[ci] = sol
         a_ref = sol["alpha"]
-        assert np.abs(alpha_new[cell["X"]] - a_ref).max() <= 1e-4 * (eps + np.abs(a_ref).max()) + 2e-3 * eps
+        worst_alpha = max(worst_alpha, float(np.abs(alpha_new[cell["X"]] - a_ref).max() / eps))
+        lo, hi = prob["lo"], prob["hi"]
         for i in cell["members"]:
             exp_full = np.zeros((N, N))
-            lo, hi = prob["lo"], prob["hi"]
             mixed = (1 - theta) * st.embed(i, lo, hi) + theta * sol["nut"][i]
-            mixed = np.where(mixed < st.thr, 0.0, mixed)
-            exp_full[lo[0]:hi[0], lo[1]:hi[1]] = mixed
+            exp_full[lo[0]:hi[0], lo[1]:hi[1]] = np.where(mixed < st.thr, 0.0, mixed)
             got_full = np.zeros((N, N))
             k0, l0, H, W = (int(v) for v in box[i])
             got_full[k0:k0 + H, l0:l0 + W] = vals[starts[i]:starts[i] + H * W].reshape(H, W)
-            mass = max(exp_full.sum(), 1e-300)
-            # FP32 cell arithmetic: a plan entry carries ~2^-24 x |exponent| relative error, with
-            # exponents up to ~1e3 in the cell frame, over 20 iterations: 2e-4 of the cell's mass
-            err = np.abs(got_full - exp_full).sum() / mass
-            assert err <= 2e-4, (name, ci, i, err)
-    # a few more sweeps: invariants and a non-increasing tracked score
-    for _ in range(3):
+            d = np.abs(got_full - exp_full).sum()
+            m = max(exp_full.sum(), 1e-300)
+            l1_num += d
+            mass_tot += m
+            worst_cell = max(worst_cell, d / m)
+    out = {"name": name, "lam": lam, "cells": len(picks), "theta": theta, "l1_rel": l1_num / mass_tot,
+           "worst_cell_l1_rel": worst_cell, "alpha_max_over_eps": worst_alpha}
+    if ncheck is None:
+        th_ref, E0, Eg, Es = odd.get_weights(st, cells, probs_all, sols, "staggered", 0.0)
+        out["theta_oracle"] = th_ref
+        out["E_greedy_minus_safe_rel"] = (Eg - Es) / abs(E0)
+    report.append(out)
+    print("full-size parity:", out)
+    return out
+
+
+@pytest.mark.parametrize("lam", [0.1, 1.0, 10.0])
+def test_blobs256_all_cells_of_a_subbatch_at_contract_tolerance(dd, lam):
+    """blobs256 (256 x 256, s = 8, eps = (1/256)^2): every cell of the first
+    staggered sub-batch, FP32 GPU against the FP64 oracle, both solved to a
+    cell tolerance of 1e-7.  The new marginals agree to <= 1e-5 of their mass in
+    L1 over the sub-batch (the stated plan-marginal tolerance), each cell to
+    <= 5e-5, the potentials to 1e-3 eps, and theta equals the oracle's decision
+    unless greedy and safe tie within the FP32 error of the score (1e-6)."""
+    import torch
+    r = compare_subbatch(dd, torch, "blobs256", lam, None, 1e-7, 3000, [])
+    assert r["l1_rel"] <= 1e-5, r
+    assert r["worst_cell_l1_rel"] <= 5e-5, r
+    assert r["alpha_max_over_eps"] <= 1e-3, r
+    assert r["theta"] == r["theta_oracle"] or abs(r["E_greedy_minus_safe_rel"]) <= 1e-6, r
+
+
+def test_lognormal1024_largest_and_random_cells(dd):
+    """lognormal1024 (1024 x 1024, s = 16, eps = (2/1024)^2): the 3 largest and
+    3 random cells of the first sub-batch (cluster-solved and single-CTA ones),
+    FP32 GPU against the FP64 oracle at a cell tolerance of 1e-7: new marginals
+    within 1e-5 of their mass in L1 over the checked cells, 5e-5 per cell."""
+    import torch
+    r = compare_subbatch(dd, torch, "lognormal1024", 1.0, 3, 1e-7, 3000, [])
+    assert r["l1_rel"] <= 1e-5, r
+    assert r["worst_cell_l1_rel"] <= 5e-5, r
+    assert r["alpha_max_over_eps"] <= 1e-3, r
+
+
+@pytest.mark.parametrize("name", ["blobs256", "lognormal1024"])
+def test_invariants_over_sweeps(dd, name):
+    """At full size in the bench's configuration (cell tolerance 2e-5): P_Y is
+    the sum of the basic-cell marginals, |P_X| = |P_Y|, the tracked score does
+    not increase over sweeps (staggered swift, no leniency), weak duality."""
+    import torch
+    mu, nu, N, s, eps, lam, md, nd, a0, b0 = warm_started(dd, torch, name, False)
+    g = dd.DomDec(md, nd, eps, lam, s, alpha0=a0, beta0=b0, eps_init=2 * eps, precision="fp32", tau=0.0,
+                  err=2e-5)
+    scores = [g.score()[0]]
+    for _ in range(4):
         g.iterate(1)
         g.sync()
         scores.append(g.score()[0])
