@@ -392,7 +392,7 @@ def run_batch(dd, torch, steps, warmup, peaks_meas):
     torch.cuda.synchronize()
     t_warm = time.perf_counter() - t0
     B = dd.DomDecBatch(handles_b)
-    chosen = B.autotune()
+    chosen_c, chosen_f = B.autotune()
     B.iterate(warmup)
     B.sync()
     it0 = sum(h.stats()["cell_iters"] for h in handles_b)
@@ -426,7 +426,8 @@ def run_batch(dd, torch, steps, warmup, peaks_meas):
         h.close()
     peak = peaks_meas["ex2_per_s"] / 1e12
     return {"value": it_b / (t_b / 1000.0), "unit": UNIT, "ms_per_sweep": t_b / steps, "instances": len(probs),
-            "sides": sorted(set(p["N"] for p in probs)), "autotuned": chosen,
+            "sides": sorted(set(p["N"] for p in probs)),
+            "autotuned": {"cluster_ctas": chosen_c, "split_factor_mean_works_per_cta": chosen_f},
             "sequential_single_handles": {"value": it_s / (t_s / 1000.0), "ms_per_sweep": t_s / steps},
             "batch_speedup": (it_b / t_b) / max(it_s / t_s, 1e-30),
             # exp terms of all cell iterations over the whole sweep time (decide, apply and

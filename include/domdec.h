@@ -306,8 +306,9 @@ int domdec_full_sinkhorn(const double* mu, const double* nu, int N, double eps_s
 
 /* Many independent problems swept together (many-instance batching): every
  * launch of a sweep covers the cells of one staggered sub-batch of all
- * instances, taken from a work queue by a persistent grid (larger grids
- * first).  `handles` (n >= 1) must share precision and strategy and have done
+ * instances, taken from a work queue by a persistent grid over the resident
+ * CTAs in order of decreasing estimated work (from the current box sizes,
+ * sorted on the device), the largest ones by thread-block clusters.  `handles` (n >= 1) must share precision and strategy and have done
  * the same number of sweeps; N, eps, lambda, s may differ.  The batch does not
  * own the handles; the handles stay usable (query them after
  * domdec_batch_sync) and must outlive the batch.  Work is enqueued on the
@@ -318,10 +319,14 @@ int domdec_batch_create(domdec_batch_t* out, domdec_t* handles, int n);
 int domdec_batch_iterate(domdec_batch_t b, int n_sweeps);
 /* domdec_sync of every handle; returns the first error, else the largest warning.  Synchronises. */
 int domdec_batch_sync(domdec_batch_t b);
-/* Autotuner: runs one sweep with one CTA per cell and one with a 2-CTA cluster
- * per cell, times both (CUDA events) and keeps the higher cell-iteration rate
- * for later sweeps; *chosen (if not NULL) receives 1 or 2.  Synchronises. */
-int domdec_batch_autotune(domdec_batch_t b, int* chosen);
+/* Autotuner of the batch's cell kernel: runs one sweep with each candidate --
+ * one CTA per cell, and clusters of 2 and 4 CTAs (as far as every instance's
+ * cluster layout allows) for the cells whose estimated work exceeds 1, 2 or 4
+ * times the mean work per CTA (plus the cells too large for one CTA) -- times
+ * each with CUDA events, and keeps the highest cell-iteration rate for later
+ * sweeps.  *cluster_ctas and *split_factor (if not NULL) receive the choice.
+ * The timed sweeps are real sweeps of every instance.  Synchronises. */
+int domdec_batch_autotune(domdec_batch_t b, int* cluster_ctas, double* split_factor);
 void domdec_batch_free(domdec_batch_t b);
 
 /* Allocation-free variant of domdec_full_sinkhorn (no counterpart in the

@@ -18,15 +18,16 @@
 // ---- kernels' launch wrappers (dd_cell.cu, dd_sweep.cu, dd_sinkhorn.cu)
 size_t cell_smem_bytes(int s, int cap_side, int cap_ny, int precision);
 cudaError_t launch_cell_solve(const DevState& S, const CellDesc* cells, const int* order, const int* nbig_p,
-                              int begin, int nbatch, int precision, size_t smem, int nctas, cudaStream_t st);
+                              int begin, int nbatch, int precision, size_t smem, int nctas, int cluster,
+                              cudaStream_t st);
 cudaError_t launch_cell_order(const DevState& S, int part, int mode, int slots, cudaStream_t st);
-int cell_max_pair_clusters(int s, int cap_side, int cap_ny, int precision);
 size_t dist_smem_bytes(int s, int C, int cap_w, int cap_hl, int cap_nyl, int precision);
 int cell_static_smem(int precision);
 int cell_resident_ctas(size_t smem, int C, int precision);
-cudaError_t launch_cell_solve_multi(const DevState* states, const CellRef* refs, int nref, int part,
-                                    unsigned int* queue, int s, int cap_side, int cap_ny, int precision, int csize,
-                                    int nctas, cudaStream_t st);
+cudaError_t launch_cell_solve_multi(const DevState* states, const CellRef* refs, int nref, int part, int* order,
+                                    int* nbig, unsigned int* queue, size_t smem, int precision, int C,
+                                    double factor, int nctas, cudaStream_t st);
+int cell_multi_resident_ctas(size_t smem, int C, int precision);
 cudaError_t launch_decide_multi(const DevState* states, int ninst, int maxn, int part, int sub, cudaStream_t st);
 cudaError_t launch_apply_multi(const DevState* states, const CellRef* refs, int nref, int part, cudaStream_t st);
 cudaError_t launch_compact_multi(const DevState* states, int ninst, int max_nbasic, cudaStream_t st);
@@ -42,7 +43,8 @@ cudaError_t launch_init_product_boxes(const DevState& S, double* nu_mom, double*
 cudaError_t launch_init_product_fill(const DevState& S, double* nu_mom, double* mumass, long long* newoff,
                                      cudaStream_t st);
 cudaError_t launch_init_duals_boxes(const DevState& S, const double* alpha0, const double* beta0, double eps0,
-                                    double* nu_mom, double* mumass, long long* newoff, cudaStream_t st);
+                                    double* nu_mom, double* mumass, long long* newoff, float* gscratch,
+                                    cudaStream_t st);
 cudaError_t launch_init_duals_fill(const DevState& S, const double* alpha0, const double* beta0, double eps0,
                                    const double* w, long long* newoff, cudaStream_t st);
 cudaError_t launch_score(const DevState& S, double* out, cudaStream_t st, double* partials);
@@ -89,6 +91,9 @@ struct domdec_s {
   double eps0 = 0.0, err0 = 0.0;           // eps and err given at domdec_init (restored by domdec_reset)
   double *d_a0 = nullptr, *d_b0 = nullptr, *d_w4 = nullptr;  // warm-start duals and 4 N*N scratch
   int cell_nctas = 0;      // persistent CTAs of the cell kernel (whole clusters of S.dist_c)
+  int helper_ctas = 0;     // single CTAs on the SMs that the resident clusters leave idle
+  cudaStream_t st2 = nullptr;               // their stream, forked from and joined to st per sub-batch
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   size_t cell_smem = 0;    // its dynamic shared memory
   int order_mode = 0;      // k_cell_order: 0 automatic, 1 every fitting cell on a cluster, 2 none
   // profiling: pending event pairs per kernel class
@@ -260,9 +265,18 @@ int enqueue_sweep(domdec_s* h, int part, long long slot0) {
     cudaEvent_t ev = prof_begin(h);
     const int sub = (int)(&bt - batches.data());
     const int* nbig_p = h->S.nbig + part * 4 + (batches.size() == 4 ? sub : 0);
+    const int C = std::max(1, h->S.dist_c);
     if (launch_cell_solve(h->S, h->d_cells[part], h->S.order[part], nbig_p, begin, nbt, prec, h->cell_smem,
-                          h->cell_nctas, h->st) != cudaSuccess)
+                          h->cell_nctas, C, h->st) != cudaSuccess)
       return DOMDEC_ECUDA;
+    if (h->helper_ctas > 0) {
+      // single CTAs on the SMs left idle by the clusters, same phase-2 queue
+      if (cudaEventRecord(h->ev_fork, h->st) != cudaSuccess || cudaStreamWaitEvent(h->st2, h->ev_fork, 0) != cudaSuccess ||
+          launch_cell_solve(h->S, h->d_cells[part], h->S.order[part], nbig_p, begin, nbt, prec, h->cell_smem,
+                            h->helper_ctas, 1, h->st2) != cudaSuccess ||
+          cudaEventRecord(h->ev_join, h->st2) != cudaSuccess || cudaStreamWaitEvent(h->st, h->ev_join, 0) != cudaSuccess)
+        return DOMDEC_ECUDA;
+    }
     prof_end(h, ev, 0);
     ev = prof_begin(h);
     if (launch_decide(h->S, h->d_cells[part], begin, nbt, h->st) != cudaSuccess) return DOMDEC_ECUDA;
@@ -319,7 +333,9 @@ int load_problem(domdec_s* h, const double* mu, const double* nu, const double* 
   if (alpha0) {
     e = cudaMemcpyAsync(ad, alpha0, n * sizeof(double), cudaMemcpyDefault, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(bd, beta0, n * sizeof(double), cudaMemcpyDefault, st);
-    if (e == cudaSuccess) e = launch_init_duals_boxes(S, ad, bd, eps0, h->d_numom, h->d_mumass, h->d_newoff, st);
+    if (e == cudaSuccess)
+      e = launch_init_duals_boxes(S, ad, bd, eps0, h->d_numom, h->d_mumass, h->d_newoff,
+                                  reinterpret_cast<float*>(wtmp), st);
   } else {
     e = launch_init_product_boxes(S, h->d_numom, h->d_mumass, h->d_newoff, st);
   }
@@ -412,6 +428,9 @@ void domdec_free(domdec_t h) {
   cudaStreamSynchronize(h->st);
   prof_collect(h);
   for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
+  if (h->st2) { cudaStreamSynchronize(h->st2); cudaStreamDestroy(h->st2); }
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   for (void* q : h->allocs)
     if (q) cudaFree(q);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
@@ -498,6 +517,17 @@ int domdec_init(domdec_t* out, const double* mu, const double* nu, int N, const 
     }
     h->cell_smem = smem;
     h->cell_nctas = std::max(1, nctas);
+    if (S.dist_c > 1) {
+      const int single = cell_resident_ctas(smem, 1, pin->precision);
+      h->helper_ctas = std::max(0, single - h->cell_nctas);
+    }
+    if (h->helper_ctas > 0 &&
+        (cudaStreamCreateWithFlags(&h->st2, cudaStreamNonBlocking) != cudaSuccess ||
+         cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+         cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess)) {
+      cudaGetLastError();
+      h->helper_ctas = 0;
+    }
   }
   std::vector<CellDesc> cells[2];
   for (int w = 0; w < 2; ++w) {
@@ -965,10 +995,15 @@ struct domdec_batch_s {
   CellRef* d_refs = nullptr;           // all reference lists, back to back
   int ref_off[2][5] = {{0}};           // list (part, sub) starts at ref_off; sub 4 = whole partition
   int ref_cnt[2][5] = {{0}};
-  unsigned int* d_queue = nullptr;
-  int precision = 0, s_max = 0, cap_side_max = 0, cap_ny_max = 0;
-  int maxn = 0, max_nbasic = 0, nsm = 152, max_pairs = 0;
-  int csize = 0;                       // 0 = automatic, 1 or 2 fixed (autotuner)
+  unsigned int* d_queue = nullptr;     // two work counters of the cell kernel
+  int* d_order = nullptr;              // reference order of a launch (k_ref_order)
+  int* d_nbig = nullptr;
+  int precision = 0, maxn = 0, max_nbasic = 0, max_ref = 0;
+  size_t smem = 0;                     // dynamic shared memory of the cell kernel (largest of the handles')
+  int c_max = 1;                       // largest cluster size every instance's layout allows
+  int res[4] = {0, 0, 0, 0};           // resident CTAs with clusters of 1, 2, 4, 8
+  int C = 0;                           // cluster size of the sweeps (0: automatic)
+  double factor = 2.0;                 // cluster-split threshold in mean works per CTA
   long long sweeps = 0;
   std::vector<DevState> host_states;
 };
@@ -991,17 +1026,15 @@ int domdec_batch_create(domdec_batch_t* out, domdec_t* handles, int n) {
   b->st = handles[0]->st;
   b->precision = handles[0]->p.precision;
   b->sweeps = handles[0]->sweeps;
+  b->c_max = 8;
   for (auto h : b->hs) {
-    b->s_max = std::max(b->s_max, h->s);
-    b->cap_side_max = std::max(b->cap_side_max, h->S.cap_side);
-    b->cap_ny_max = std::max(b->cap_ny_max, h->S.cap_ny);
+    b->smem = std::max(b->smem, h->cell_smem);
+    b->c_max = std::min(b->c_max, std::max(1, h->S.dist_c));
     b->maxn = std::max(b->maxn, h->N);
     b->max_nbasic = std::max(b->max_nbasic, h->nbasic);
   }
-  int dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
-  b->max_pairs = cell_max_pair_clusters(b->s_max, b->cap_side_max, b->cap_ny_max, b->precision);
+  for (int k = 0, c = 1; k < 4; ++k, c *= 2)
+    b->res[k] = c <= b->c_max ? cell_multi_resident_ctas(b->smem, c, b->precision) : 0;
   // reference lists: for each (partition, sub-batch) the cells of every
   // instance, larger grids first (their boxes are larger: longest jobs first)
   std::vector<int> order(n);
@@ -1019,9 +1052,13 @@ int domdec_batch_create(domdec_batch_t* out, domdec_t* handles, int n) {
       }
       b->ref_cnt[part][sub] = (int)refs.size() - b->ref_off[part][sub];
     }
+  for (int part = 0; part < 2; ++part)
+    for (int sub = 0; sub < 5; ++sub) b->max_ref = std::max(b->max_ref, b->ref_cnt[part][sub]);
   if (cudaMalloc(&b->d_states, n * sizeof(DevState)) != cudaSuccess ||
       cudaMalloc(&b->d_refs, std::max<size_t>(1, refs.size()) * sizeof(CellRef)) != cudaSuccess ||
-      cudaMalloc(&b->d_queue, sizeof(unsigned int)) != cudaSuccess) {
+      cudaMalloc(&b->d_queue, 2 * sizeof(unsigned int)) != cudaSuccess ||
+      cudaMalloc(&b->d_order, std::max(1, b->max_ref) * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&b->d_nbig, sizeof(int)) != cudaSuccess) {
     domdec_batch_free(b);
     return DOMDEC_ENOMEM;
   }
@@ -1040,6 +1077,8 @@ void domdec_batch_free(domdec_batch_t b) {
   if (b->d_states) cudaFree(b->d_states);
   if (b->d_refs) cudaFree(b->d_refs);
   if (b->d_queue) cudaFree(b->d_queue);
+  if (b->d_order) cudaFree(b->d_order);
+  if (b->d_nbig) cudaFree(b->d_nbig);
   delete b;
 }
 
@@ -1055,24 +1094,28 @@ static int batch_upload(domdec_batch_t b) {
   return DOMDEC_OK;
 }
 
-static int batch_enqueue_sweep(domdec_batch_t b, int csize_fixed) {
+// One sweep of every instance with clusters of C CTAs (0: automatic) and the
+// cluster-split threshold `factor`.
+static int batch_enqueue_sweep(domdec_batch_t b, int C, double factor) {
   const int part = (int)(b->sweeps % 2);
   const int ninst = (int)b->hs.size();
   const bool stag = b->hs[0]->p.strategy == DOMDEC_STAGGERED;
   const int subs[4] = {0, 1, 2, 3};
   const int nsub = stag ? 4 : 1;
+  if (C <= 0) C = b->c_max >= 4 ? 4 : b->c_max;
+  int ci = 0;
+  while ((1 << ci) < C) ++ci;
+  if (ci > 3 || b->res[ci] < C) { C = 1; ci = 0; }
+  const int nctas = std::max(C, b->res[ci]);
   for (int k = 0; k < nsub; ++k) {
     const int sub = stag ? subs[k] : 4;
     const int nref = b->ref_cnt[part][sub];
     if (nref == 0) continue;
     const CellRef* refs = b->d_refs + b->ref_off[part][sub];
-    int csize = csize_fixed ? csize_fixed : (b->max_pairs > 0 && nref >= 2 * b->nsm ? 1 : (b->max_pairs > 0 ? 2 : 1));
-    if (csize == 2 && b->max_pairs == 0) csize = 1;
-    const int nctas = csize == 2 ? 2 * std::min(nref, b->max_pairs) : std::min(nref, b->nsm);
-    if (launch_cell_solve_multi(b->d_states, refs, nref, part, b->d_queue, b->s_max, b->cap_side_max,
-                                b->cap_ny_max, b->precision, csize, nctas, b->st) != cudaSuccess)
+    if (launch_cell_solve_multi(b->d_states, refs, nref, part, b->d_order, b->d_nbig, b->d_queue, b->smem,
+                                b->precision, C, factor, nctas, b->st) != cudaSuccess)
       return DOMDEC_ECUDA;
-    if (launch_decide_multi(b->d_states, ninst, b->maxn, part, stag ? sub : -1, b->st) != cudaSuccess)
+  if (launch_decide_multi(b->d_states, ninst, b->maxn, part, stag ? sub : -1, b->st) != cudaSuccess)
       return DOMDEC_ECUDA;
     if (launch_apply_multi(b->d_states, refs, nref, part, b->st) != cudaSuccess) return DOMDEC_ECUDA;
   }
@@ -1090,7 +1133,7 @@ int domdec_batch_iterate(domdec_batch_t b, int n_sweeps) {
   int rc = batch_upload(b);
   if (rc) return rc;
   for (int k = 0; k < n_sweeps; ++k) {
-    rc = batch_enqueue_sweep(b, b->csize);
+    rc = batch_enqueue_sweep(b, b->C, b->factor);
     if (rc) {
       for (auto h : b->hs) fail(h, rc);
       return rc;
@@ -1110,12 +1153,21 @@ int domdec_batch_sync(domdec_batch_t b) {
   return worst;
 }
 
-int domdec_batch_autotune(domdec_batch_t b, int* chosen) {
+int domdec_batch_autotune(domdec_batch_t b, int* cluster_ctas, double* split_factor) {
   if (!b) return DOMDEC_EINVAL;
-  // one sweep with each cell-group size; keep the higher cell-iteration rate
-  double rate[3] = {0, 0, 0};
-  for (int cs = 1; cs <= 2; ++cs) {
-    if (cs == 2 && b->max_pairs == 0) break;
+  // candidates: one CTA per cell, or clusters of 2 / 4 CTAs for the cells above
+  // 1, 2 or 4 mean works per CTA (and those too large for one CTA); one sweep
+  // each, timed with CUDA events; the highest cell-iteration rate is kept
+  struct Cand { int C; double f; };
+  std::vector<Cand> cands = {{1, 2.0}};
+  for (int C = 2; C <= std::min(4, b->c_max); C *= 2) {
+    int ci = C == 2 ? 1 : 2;
+    if (b->res[ci] < C) continue;
+    for (double f : {1.0, 2.0, 4.0}) cands.push_back({C, f});
+  }
+  double best = -1.0;
+  Cand pick = cands[0];
+  for (const Cand& c : cands) {
     int rc = domdec_batch_sync(b);
     if (rc < 0) return rc;
     long long it0 = 0;
@@ -1130,7 +1182,7 @@ int domdec_batch_autotune(domdec_batch_t b, int* chosen) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, b->st);
-    rc = batch_enqueue_sweep(b, cs);
+    rc = batch_enqueue_sweep(b, c.C, c.f);
     cudaEventRecord(e1, b->st);
     if (rc) return rc;
     rc = domdec_batch_sync(b);
@@ -1145,10 +1197,13 @@ int domdec_batch_autotune(domdec_batch_t b, int* chosen) {
       if (domdec_get_stats(h, &st)) return DOMDEC_ECUDA;
       it1 += st.cell_iters;
     }
-    rate[cs] = ms > 0.f ? (double)(it1 - it0) / ms : 0.0;
+    const double rate = ms > 0.f ? (double)(it1 - it0) / ms : 0.0;
+    if (rate > best) { best = rate; pick = c; }
   }
-  b->csize = rate[2] > rate[1] ? 2 : 1;
-  if (chosen) *chosen = b->csize;
+  b->C = pick.C;
+  b->factor = pick.f;
+  if (cluster_ctas) *cluster_ctas = pick.C;
+  if (split_factor) *split_factor = pick.f;
   return DOMDEC_OK;
 }
 }  // extern "C"

@@ -25,6 +25,13 @@
 
 #include "dd_common.cuh"
 
+// Threads per CTA of the cell kernels (the cell body works with any multiple
+// of 32 up to 1024; the block reductions assume at most 32 warps).
+#ifndef DD_CELL_THREADS
+#define DD_CELL_THREADS 512
+#endif
+constexpr int kCellThreads = DD_CELL_THREADS;
+
 namespace {
 
 template <typename R, typename F>
@@ -226,35 +233,22 @@ __device__ __forceinline__ double box_value(const BoxRec& b, const double* arena
 
 }  // namespace
 
-// One composite cell per CTA (csize = 1) or per pair of CTAs in a thread-block
-// cluster (csize = 2).  With a pair, both CTAs load the whole cell state, every
-// pass splits its targets between them and writes each result into both
-// CTAs' shared memory (distributed shared memory); pass boundaries are cluster
-// barriers.
-// Body of the cell solve for cell `cd` at position `cidx` of a sub-batch of
-// `nbatch` cells, run by CTA `crank` of a group of `csize` CTAs.
+// One composite cell on one CTA: cell `cd` at position `cidx` of a sub-batch
+// of `nbatch` cells.
 template <typename R>
 __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDesc cd, int cidx, int nbatch,
-                                                int csize, int crank, unsigned char* smem_raw) {
+                                                unsigned char* smem_raw) {
   namespace cg = cooperative_groups;
   double* red = reinterpret_cast<double*>(smem_raw);  // 32 * 16 doubles (block reductions)
   __shared__ BoxRec sbox[4];
   __shared__ int sgeo[8];
-  __shared__ double xchg[16];                         // cross-CTA partial sums
   CellOut* out = S.cout + cidx;
   const double* __restrict__ arena = S.arena[*S.cur];
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int gtid = crank * nthr + tid, gthr = csize * nthr;  // thread index / count across the pair
+  const int gtid = tid, gthr = nthr;
   const int N = S.N, s = S.s;
   const int nx1 = cd.nx1, nx2 = cd.nx2, nx = nx1 * nx2;
-  auto csync = [&]() {
-    if (csize > 1) cg::this_cluster().sync();
-    else __syncthreads();
-  };
-  // address of the same shared-memory object in the partner CTA (nullptr without a pair)
-  auto peer = [&](auto* p) -> decltype(p) {
-    return csize > 1 ? cg::this_cluster().map_shared_rank(p, crank ^ 1) : nullptr;
-  };
+  auto csync = [&]() { __syncthreads(); };
 
   // ---------------------------------------------------------------- B_J
   if (tid == 0) {
@@ -276,26 +270,19 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
       k1 = min(N, k1 + S.margin); l1 = min(N, l1 + S.margin);
       int H = k1 - k0, W = l1 - l0;
       // boxes beyond the shared-memory capacity run from a global spill slot
-      // (taken once per cell, by the first CTA of a pair)
-      if ((H * W > S.cap_ny || H > S.cap_side || W > S.cap_side) && crank == 0) {
+      if (H * W > S.cap_ny || H > S.cap_side || W > S.cap_side) {
         int sl = S.spill_slots > 0 ? (int)atomicAdd(S.spill_count, 1u) : S.spill_slots;
         if (sl >= S.spill_slots) st = CELL_TOOBIG;
         else slot = sl;
       }
     }
     sgeo[0] = k0; sgeo[1] = l0; sgeo[2] = k1 - k0; sgeo[3] = l1 - l0;
-    if (crank == 0) {
-      sgeo[4] = st; sgeo[7] = slot;
-      if (csize > 1) {
-        int* ps = peer(sgeo);
-        ps[4] = st; ps[7] = slot;
-      }
-    }
+    sgeo[4] = st; sgeo[7] = slot;
   }
   csync();
   const int k0 = sgeo[0], l0 = sgeo[1], H = sgeo[2], W = sgeo[3];
   if (sgeo[4] != CELL_OK) {
-    if (tid == 0 && crank == 0) {
+    if (tid == 0) {
       CellOut o;
       o.k0 = k0; o.l0 = l0; o.H = H; o.W = W; o.iters = 0; o.status = sgeo[4];
       o.D1 = o.D2 = 0; o.gap = 0.0; o.dKX[0] = o.dKX[1] = 0.0; o.slot = -1; o.pad = 0;
@@ -335,27 +322,11 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
   R* Zv = lrho + cap_ny;
   R* bv = Zv + cap_ny;
   R* lnu = bv + cap_ny;
-  // partner copies (Y-side arrays in a spill slot are shared, nothing to copy)
-  R* const xa_p = peer(xa);
-  R* const av_p = peer(av);
-  R* const xanx_p = peer(xa_nx);
-  R* const avnx_p = peer(av_nx);
-  R* const Wv_p = peer(Wv);
-  R* const T_p = spilled ? nullptr : peer(T);
-  R* const U_p = spilled ? nullptr : peer(U);
-  R* const bl_p = spilled ? nullptr : peer(bl);
-  R* const Zv_p = spilled ? nullptr : peer(Zv);
-  R* const bv_p = spilled ? nullptr : peer(bv);
-  auto put = [](R* a, R* ap, int i, R v) {
-    a[i] = v;
-    if (ap) ap[i] = v;
-  };
 
   // ------------------------------------------------------- load Y side (a1)
   // rho = max(0, P_Y - nu_J)/nu and log nu on B_J; the same pass accumulates
   // the barycentre of nu_J, whose nearest pixel is the Y frame origin (so
-  // that 2 q D.xi carries the cell's mean displacement).  Both CTAs of a
-  // pair load everything.
+  // that 2 q D.xi carries the cell's mean displacement).
   double a_tot = 0.0;   // |nu_{-J}| on B_J (translation step)
   {
     double m3[4] = {0.0, 0.0, 0.0, 0.0};
@@ -368,10 +339,8 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
       double nuy = S.nu[y];
       const double num = fmax(0.0, S.PY[y] - nuJ);
       R rho = R(num) / R(nuy);
-      if (!spilled || crank == 0) {
-        lrho[u] = rho > R(0) ? dd_lg2(rho) * R(DD_LN2) : -dd_inf<R>();
-        lnu[u] = R(S.lognu[y]);
-      }
+      lrho[u] = rho > R(0) ? dd_lg2(rho) * R(DD_LN2) : -dd_inf<R>();
+      lnu[u] = R(S.lognu[y]);
       m3[0] += nuJ; m3[1] += nuJ * kk; m3[2] += nuJ * ll; m3[3] += num;
     }
     block_sum<4>(m3, red);
@@ -435,20 +404,17 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
   // the gap is reduced from per-warp partials after that pass's barrier.
   const double tol = S.err * muJ;
   const R LN2 = R(DD_LN2), L2E = R(DD_LOG2E);
-  R* gpart = reinterpret_cast<R*>(red) + 32 * 12;   // per-warp gap partials of both CTAs
-  R* const gpart_p = peer(gpart);
+  R* gpart = reinterpret_cast<R*>(red) + 32 * 12;   // per-warp gap partials
   R* apart = gpart + 32;                             // per-warp <e^{-alpha/lam}, mu> (translation step)
   R* bpart = gpart + 64;                             // per-warp <e^{-beta/lam}, nu>
-  R* const apart_p = peer(apart);
-  R* const bpart_p = peer(bpart);
   const bool ti = S.ti && sl > 0.0;
   const int lane = tid & 31, wid = tid >> 5, nwarp = nthr >> 5;
   int it = 0;
   double gap = 0.0;
   bool first = true;
   const bool fused_y = ny * 2 > gthr;   // large boxes: one lane per y, LSE and Newton fused
-  R *xa_c = xa, *xa_cp = xa_p, *av_c = av, *av_cp = av_p;          // current iterate
-  R *xa_n = xa_nx, *xa_np = xanx_p, *av_n = av_nx, *av_np = avnx_p;  // next iterate
+  R *xa_c = xa, *av_c = av;          // current iterate
+  R *xa_n = xa_nx, *av_n = av_nx;    // next iterate
   for (;;) {
     ++it;
     // Y-half, pass over columns of X: T(r, ll) = log2 sum_c 2^{xa(r,c) - q2 (c - ll - offc)^2}
@@ -460,7 +426,7 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
         const R* row = xa_c + r * nx2;
         R v = lse2_group<R>([&](int m) { return row[m]; }, nx2, R(ll + offc), q2, T[tg], !first, part, P);
         __syncwarp();
-        if (part == 0 && tg0 < nt) put(T, T_p, tg, v);
+        if (part == 0 && tg0 < nt) T[tg] = v;
       }
     }
     csync();
@@ -489,10 +455,10 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
           if (!ok[k]) continue;
-          put(Zv, Zv_p, uu[k], Zn[k] * L2E);
+          Zv[uu[k]] = Zn[k] * L2E;
           R b = root[k] - Zn[k];
-          put(bv, bv_p, uu[k], b);
-          put(bl, bl_p, uu[k], (b + lnu[uu[k]]) * L2E);
+          bv[uu[k]] = b;
+          bl[uu[k]] = (b + lnu[uu[k]]) * L2E;
           // nu e^{-beta/lam}: -s beta/eps = -(s root + c0)
           if (ti) bsum += dd_ex2((lnu[uu[k]] - sR * root[k] - c0[k]) * L2E);
         }
@@ -504,7 +470,7 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
         const int kk = u / W, ll = u - kk * W;
         R Z2 = lse2_group<R>([&](int m) { return T[m * W + ll]; }, nx1, R(kk + offr), q2, Zv[u], !first, part, P);
         __syncwarp();
-        if (part == 0 && u0 < ny) put(Zv, Zv_p, u, Z2);
+        if (part == 0 && u0 < ny) Zv[u] = Z2;
       }
       csync();
       for (int u = gtid; u < ny; u += 2 * gthr) {
@@ -524,15 +490,15 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
         for (int k = 0; k < 2; ++k) {
           if (k == 1 && u + gthr >= ny) break;
           R b = root[k] - Zv[uu[k]] * LN2;
-          put(bv, bv_p, uu[k], b);
-          put(bl, bl_p, uu[k], (b + lnu[uu[k]]) * L2E);
+          bv[uu[k]] = b;
+          bl[uu[k]] = (b + lnu[uu[k]]) * L2E;
           if (ti) bsum += dd_ex2((lnu[uu[k]] - sR * root[k] - c0[k]) * L2E);
         }
       }
     }
     if (ti) {
       bsum = warp_sum(bsum);
-      if (lane == 0) put(bpart, bpart_p, crank * nwarp + wid, bsum);
+      if (lane == 0) bpart[wid] = bsum;
     }
     csync();
     // X-half, pass over columns of B_J: U(kk, c) = log2 sum_ll 2^{bl(kk,ll) - q2 (ll - (c - offc))^2}
@@ -544,7 +510,7 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
         const R* row = bl + kk * W;
         R v = lse2_group<R>([&](int m) { return row[m]; }, W, R(c - offc), q2, U[tg], !first, part, P);
         __syncwarp();
-        if (part == 0 && tg0 < nt) put(U, U_p, tg, v);
+        if (part == 0 && tg0 < nt) U[tg] = v;
       }
     }
     csync();
@@ -558,29 +524,29 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
         R W2 = lse2_group<R>([&](int m) { return U[m * nx2 + c]; }, H, R(r - offr), q2, Wv[t], !first, part, P);
         __syncwarp();
         if (part == 0 && tg0 < nx) {
-          put(Wv, Wv_p, t, W2);
+          Wv[t] = W2;
           R a = av_c[t];
           R tt = a + W2 * LN2;         // log(P_X pi / mu)
           R g = gA + g0[t] - sR * a;   // -alpha/lam
           gl += dd_ex2((lm[t] + g) * L2E) * dd_psi<R>(tt - g);
           R xi1 = R(cd.i0 + r - xc1), xi2 = R(cd.j0 + c - xc2);
           R an = cA - rR * W2 * LN2 - cD1 * xi1 - cD2 * xi2;
-          put(av_n, av_np, t, an);
-          put(xa_n, xa_np, t, (an + lm[t]) * L2E);
+          av_n[t] = an;
+          xa_n[t] = (an + lm[t]) * L2E;
           if (ti) asum += dd_ex2((lm[t] + gA + g0[t] - sR * an) * L2E);   // mu e^{-alpha_new/lam}
         }
       }
       gl = warp_sum(gl);
-      if (lane == 0) put(gpart, gpart_p, crank * nwarp + wid, gl);
+      if (lane == 0) gpart[wid] = gl;
       if (ti) {
         asum = warp_sum(asum);
-        if (lane == 0) put(apart, apart_p, crank * nwarp + wid, asum);
+        if (lane == 0) apart[wid] = asum;
       }
     }
     csync();
     {
       R gs = R(0);
-      for (int w = 0; w < csize * nwarp; ++w) gs += gpart[w];
+      for (int w = 0; w < nwarp; ++w) gs += gpart[w];
       gap = (double)gs;
     }
     first = false;
@@ -588,9 +554,9 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
     if (ti) {
       // translation step: alpha += t*, e^{t*/lam} = (a + sqrt(a^2 + 4 A_s B_s)) / (2 B_s); in the
       // cell frame alpha/eps = A + a(xi) + 2qD.xi it moves A by t*/eps = log(u)/s (same in
-      // every thread of both CTAs: the partials are replicated)
+      // every thread: the partials are replicated)
       double As = 0.0, Bs = 0.0;
-      for (int w = 0; w < csize * nwarp; ++w) {
+      for (int w = 0; w < nwarp; ++w) {
         As += (double)apart[w];
         Bs += (double)bpart[w];
       }
@@ -602,22 +568,20 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
         gA = R(-sl * A);
       }
     }
-    // accept the X-update: swap the buffers (every thread of both CTAs does the same)
+    // accept the X-update: swap the buffers
     R* tp = av_c; av_c = av_n; av_n = tp;
-    tp = av_cp; av_cp = av_np; av_np = tp;
     tp = xa_c; xa_c = xa_n; xa_n = tp;
-    tp = xa_cp; xa_cp = xa_np; xa_np = tp;
   }
   const bool nonfinite = !(gap == gap);
 
   // ------------------------------------------------------- epilogue (a5)
   // alpha, P_X of the new plan and the KL_X change: first CTA only.  With
   // balancing (one CTA per cell) P_X and the KL_X change follow the balancing.
-  const bool bal = S.balance && csize == 1;
+  const bool bal = S.balance;
   const double th_s = 1.0 / nbatch;
   double dk[2] = {0.0, 0.0};
   double mubar[4] = {0.0, 0.0, 0.0, 0.0};   // balancing: mu_bar(X_q), X-marginal after one more X-half
-  if (crank == 0) {
+  {
     for (int t = tid; t < nx; t += nthr) {
       int r = t / nx2, c = t - r * nx2;
       int x = (cd.i0 + r) * N + cd.j0 + c;
@@ -666,9 +630,6 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
   R* Te = T;                 // epilogue scratch spans T, U, bl, lrho, Zv
   R* Ma = T + nx1 * W;
   R* Md = Ma + nx1 * W;
-  R* const Te_p = spilled ? nullptr : peer(Te);
-  R* const Ma_p = spilled ? nullptr : peer(Ma);
-  R* const Md_p = spilled ? nullptr : peer(Md);
   for (int hc = 0; hc < nhc; ++hc) {
     const int cb = hc * s, ce = min(nx2, cb + s);
     // rows of X_J against columns of B_J, restricted to the column half hc
@@ -687,9 +648,9 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
         sd += w * dt * dt;
       }
       R isw = R(1) / sw;
-      put(Te, Te_p, t, T2);
-      put(Ma, Ma_p, t, sa * isw);
-      put(Md, Md_p, t, sd * isw);
+      Te[t] = T2;
+      Ma[t] = sa * isw;
+      Md[t] = sd * isw;
     }
     csync();
     for (int u = gtid; u < ny; u += gthr) {
@@ -883,16 +844,6 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
 #pragma unroll
   for (int k = 0; k < 12; ++k) hsd[k] = (double)hs[k];
   block_sum<12>(hsd, red);
-  if (csize > 1) {
-    // the second CTA hands its partial sums to the first
-    if (crank == 1 && tid == 0) {
-      double* px = peer(xchg);
-      for (int k = 0; k < 12; ++k) px[k] = hsd[k];
-    }
-    csync();
-    if (crank == 1) return;
-    for (int k = 0; k < 12; ++k) hsd[k] += xchg[k];
-  }
   if (tid == 0) {
     CellOut o;
     o.k0 = k0; o.l0 = l0; o.H = H; o.W = W;
@@ -1426,16 +1377,19 @@ __device__ __forceinline__ void cell_solve_dist(const DevState& S, const CellDes
 // time (cell_solve_body on one CTA).  The order (largest estimated work first
 // within each phase, k_cell_order) only decides when a cell starts; the
 // results do not depend on it.
+// `cluster`: the cluster size of this launch -- S.dist_c for the main grid, 1
+// for a helper grid that runs phase 2 only on the SMs the clusters leave idle
+// (both take phase-2 cells from the same queue).
 template <typename R>
-__global__ void __launch_bounds__(512, 1)
+__global__ void __launch_bounds__(kCellThreads, 1)
 k_cell_solve(DevState S, const CellDesc* __restrict__ cells, const int* __restrict__ order,
-             const int* __restrict__ nbig_p, int begin, int nbatch) {
+             const int* __restrict__ nbig_p, int begin, int nbatch, int cluster) {
   namespace cg = cooperative_groups;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int sj;
   const int C = S.dist_c;
   const int nbig = (C > 1 && order) ? *nbig_p : 0;
-  if (C > 1) {
+  if (C > 1 && cluster > 1) {
     const int crank = (int)cg::this_cluster().block_rank();
     // every CTA of the cluster must have started before one writes another's shared memory
     cg::this_cluster().sync();
@@ -1460,7 +1414,7 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, const int* __restri
     const int j = nbig + sj;
     if (j >= nbatch) break;
     const int cidx = order ? order[begin + j] : j;
-    cell_solve_body<R>(S, cells[begin + cidx], cidx, nbatch, 1, 0, smem_raw);
+    cell_solve_body<R>(S, cells[begin + cidx], cidx, nbatch, smem_raw);
   }
 }
 
@@ -1569,42 +1523,125 @@ cudaError_t launch_cell_order(const DevState& S, int part, int mode, int slots, 
   return cudaGetLastError();
 }
 
-// Many independent instances: a persistent grid takes (instance, cell) items
-// from a queue (one item per CTA or CTA pair at a time) until it is empty.
+// Many independent instances, one staggered sub-batch of every instance per
+// launch: the same two phases as k_cell_solve over the (instance, cell)
+// references in the order of k_ref_order -- clusters of C CTAs take the first
+// nbig references (each CTA loads that instance's state), then every CTA takes
+// the rest one at a time.  C must not exceed any instance's dist_c (its
+// cluster layout was sized for dist_c CTAs).
 template <typename R>
-__global__ void __launch_bounds__(512, 1)
-k_cell_solve_multi(const DevState* __restrict__ states, const CellRef* __restrict__ refs, int nref, int part,
-                   unsigned int* queue, int csize) {
+__global__ void __launch_bounds__(kCellThreads, 1)
+k_cell_solve_multi(const DevState* __restrict__ states, const CellRef* __restrict__ refs,
+                   const int* __restrict__ order, const int* __restrict__ nbig_p, int nref, int part,
+                   unsigned int* queue, int C) {
   namespace cg = cooperative_groups;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ DevState sS;
   __shared__ int sj;
-  const int crank = csize > 1 ? (int)cg::this_cluster().block_rank() : 0;
-  auto csync = [&]() {
-    if (csize > 1) cg::this_cluster().sync();
-    else __syncthreads();
-  };
-  // the partner CTA must have started before its shared memory is written
-  if (csize > 1) cg::this_cluster().sync();
-  for (;;) {
-    if (crank == 0 && threadIdx.x == 0) {
-      int j = (int)atomicAdd(queue, 1u);
-      sj = j;
-      if (csize > 1) *cg::this_cluster().map_shared_rank(&sj, 1) = j;
-    }
-    csync();
-    const int j = sj;
-    if (j >= nref) break;
-    const CellRef rf = refs[j];
-    {
-      const int* src = reinterpret_cast<const int*>(states + rf.inst);
-      int* dst = reinterpret_cast<int*>(&sS);
-      for (int w = threadIdx.x; w < (int)(sizeof(DevState) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
-    }
+  auto load_state = [&](int inst) {
+    const int* src = reinterpret_cast<const int*>(states + inst);
+    int* dst = reinterpret_cast<int*>(&sS);
+    for (int w = threadIdx.x; w < (int)(sizeof(DevState) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
     __syncthreads();
-    cell_solve_body<R>(sS, sS.cells[part][rf.cell], rf.pos, rf.nbatch, csize, crank, smem_raw);
-    csync();
+    if (threadIdx.x == 0) sS.dist_c = C;
+    __syncthreads();
+  };
+  const int nbig = C > 1 ? *nbig_p : 0;
+  if (C > 1) {
+    const int crank = (int)cg::this_cluster().block_rank();
+    // every CTA of the cluster must have started before one writes another's shared memory
+    cg::this_cluster().sync();
+    for (;;) {
+      if (crank == 0 && threadIdx.x == 0) {
+        const int j = (int)atomicAdd(queue, 1u);
+        for (int r = 0; r < C; ++r) *cg::this_cluster().map_shared_rank(&sj, r) = j;
+      }
+      cg::this_cluster().sync();
+      const int j = sj;
+      if (j >= nbig) break;
+      const CellRef rf = refs[order[j]];
+      load_state(rf.inst);
+      cell_solve_dist<R>(sS, sS.cells[part][rf.cell], rf.pos, rf.nbatch, crank, smem_raw);
+      cg::this_cluster().sync();
+    }
   }
+  // no shared memory of another CTA is touched from here on
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) sj = (int)atomicAdd(queue + 1, 1u);
+    __syncthreads();
+    const int j = nbig + sj;
+    if (j >= nref) break;
+    const CellRef rf = refs[order ? order[j] : j];
+    load_state(rf.inst);
+    cell_solve_body<R>(sS, sS.cells[part][rf.cell], rf.pos, rf.nbatch, smem_raw);
+  }
+}
+
+constexpr int kRefOrderMax = 8192;   // largest reference list sorted (longer ones keep their order)
+
+// Order of the nref references of one many-instance launch (one block): cluster
+// references first -- those whose box fits the instance's cluster layout for C
+// CTAs and whose estimated work exceeds `factor` times the mean work per CTA
+// (`slots` CTAs), or that do not fit one CTA -- each group by decreasing
+// estimated work (as k_cell_order); *nbig = the number of cluster references.
+__global__ void __launch_bounds__(1024)
+k_ref_order(const DevState* __restrict__ states, const CellRef* __restrict__ refs, int nref, int part, int C,
+            double factor, int slots, int* order, int* nbig) {
+  extern __shared__ unsigned long long rkey[];
+  __shared__ double red[33];
+  int P = 1;
+  while (P < nref) P <<= 1;
+  if (P > kRefOrderMax) {
+    for (int i = threadIdx.x; i < nref; i += blockDim.x) order[i] = i;
+    if (threadIdx.x == 0) *nbig = 0;
+    return;
+  }
+  double tot[1] = {0.0};
+  for (int i = threadIdx.x; i < nref; i += blockDim.x) {
+    const CellRef rf = refs[i];
+    int H, W;
+    tot[0] += (double)cell_cost(states[rf.inst], states[rf.inst].cells[part][rf.cell], &H, &W);
+  }
+  block_sum<1>(tot, red);
+  const double thr = factor * tot[0] / (double)max(1, slots);
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    unsigned long long k = 0ull;
+    if (i < nref) {
+      const CellRef rf = refs[i];
+      const DevState& S = states[rf.inst];
+      int H, W;
+      const unsigned int cost = cell_cost(S, S.cells[part][rf.cell], &H, &W);
+      const int hl = (H + C - 1) / C;
+      const bool fits_dist = C > 1 && C <= S.dist_c && H >= C && W <= S.dist_cap_w && hl <= S.dist_cap_hl &&
+                             hl * W <= S.dist_cap_nyl;
+      const bool fits_one = H <= S.cap_side && W <= S.cap_side && H * W <= S.cap_ny;
+      const bool big = fits_dist && (!fits_one || (double)cost > thr);
+      k = ((unsigned long long)big << 62) | ((unsigned long long)cost << 30) | (0x3fffffffu - (unsigned)i);
+    }
+    rkey[i] = k;
+  }
+  __syncthreads();
+  for (int k = 2; k <= P; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const unsigned long long a = rkey[i], c = rkey[ixj];
+          const bool first_half = (i & k) == 0;
+          if (first_half ? (a < c) : (a > c)) { rkey[i] = c; rkey[ixj] = a; }
+        }
+      }
+      __syncthreads();
+    }
+  int cnt = 0;
+  for (int i = threadIdx.x; i < nref; i += blockDim.x) {
+    order[i] = (int)(0x3fffffffu - (unsigned)(rkey[i] & 0x3fffffffull));
+    cnt += (int)((rkey[i] >> 62) & 1ull);
+  }
+  double cv[1] = {(double)cnt};
+  block_sum<1>(cv, red);
+  if (threadIdx.x == 0) *nbig = (int)cv[0];
 }
 
 size_t cell_smem_bytes(int s, int cap_side, int cap_ny, int precision) {
@@ -1620,46 +1657,19 @@ size_t dist_smem_bytes(int s, int C, int cap_w, int cap_hl, int cap_nyl, int pre
          rs * ((8 + (size_t)C) * cap_nx + 2 * (size_t)s * cap_w + 2 * (size_t)s * cap_hl + 5 * (size_t)cap_nyl);
 }
 
-// Static shared memory of the cell kernels (the dynamic part must leave room for it).
+// Static shared memory of the cell kernels, the larger of the single- and the
+// many-instance kernel (the dynamic part must leave room for it).
 int cell_static_smem(int precision) {
-  cudaFuncAttributes fa;
-  cudaError_t e = precision ? cudaFuncGetAttributes(&fa, k_cell_solve<double>)
-                            : cudaFuncGetAttributes(&fa, k_cell_solve<float>);
-  if (e != cudaSuccess) {
+  cudaFuncAttributes a1, a2;
+  cudaError_t e1 = precision ? cudaFuncGetAttributes(&a1, k_cell_solve<double>)
+                             : cudaFuncGetAttributes(&a1, k_cell_solve<float>);
+  cudaError_t e2 = precision ? cudaFuncGetAttributes(&a2, k_cell_solve_multi<double>)
+                             : cudaFuncGetAttributes(&a2, k_cell_solve_multi<float>);
+  if (e1 != cudaSuccess || e2 != cudaSuccess) {
     cudaGetLastError();
     return 4096;
   }
-  return (int)fa.sharedSizeBytes;
-}
-
-// Largest number of 2-CTA clusters of the many-instance kernel resident at once.
-int cell_max_pair_clusters(int s, int cap_side, int cap_ny, int precision) {
-  size_t smem = cell_smem_bytes(s, cap_side, cap_ny, precision);
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(2);
-  cfg.blockDim = dim3(512);
-  cfg.dynamicSmemBytes = smem;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = 2;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  int n = 0;
-  cudaError_t e;
-  if (precision) {
-    cudaFuncSetAttribute(k_cell_solve_multi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    e = cudaOccupancyMaxActiveClusters(&n, k_cell_solve_multi<double>, &cfg);
-  } else {
-    cudaFuncSetAttribute(k_cell_solve_multi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    e = cudaOccupancyMaxActiveClusters(&n, k_cell_solve_multi<float>, &cfg);
-  }
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  return n;
+  return (int)std::max(a1.sharedSizeBytes, a2.sharedSizeBytes);
 }
 
 // Resident CTAs of the single-instance cell kernel with `smem` dynamic bytes:
@@ -1678,8 +1688,8 @@ int cell_resident_ctas(size_t smem, int C, int precision) {
   }
   if (C <= 1) {
     int per = 0;
-    e = precision ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cell_solve<double>, 512, smem)
-                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cell_solve<float>, 512, smem);
+    e = precision ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cell_solve<double>, kCellThreads, smem)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cell_solve<float>, kCellThreads, smem);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return nsm > 0 ? nsm : 1;
@@ -1688,7 +1698,7 @@ int cell_resident_ctas(size_t smem, int C, int precision) {
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(C);
-  cfg.blockDim = dim3(512);
+  cfg.blockDim = dim3(kCellThreads);
   cfg.dynamicSmemBytes = smem;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1708,13 +1718,15 @@ int cell_resident_ctas(size_t smem, int C, int precision) {
 }
 
 // One sub-batch: `nctas` persistent CTAs (a multiple of S.dist_c, at most the
-// resident ones) in clusters of S.dist_c, `smem` dynamic bytes.
+// resident ones) in clusters of S.dist_c, `smem` dynamic bytes; cluster = 1
+// launches single CTAs that run phase 2 only.
 cudaError_t launch_cell_solve(const DevState& S, const CellDesc* cells, const int* order, const int* nbig_p,
-                              int begin, int nbatch, int precision, size_t smem, int nctas, cudaStream_t st) {
-  const int C = std::max(1, S.dist_c);
+                              int begin, int nbatch, int precision, size_t smem, int nctas, int cluster,
+                              cudaStream_t st) {
+  const int C = std::max(1, cluster);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(std::max(C, nctas / C * C));
-  cfg.blockDim = dim3(512);
+  cfg.blockDim = dim3(kCellThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -1726,33 +1738,88 @@ cudaError_t launch_cell_solve(const DevState& S, const CellDesc* cells, const in
   cfg.numAttrs = C > 1 ? 1 : 0;
   if (precision) {
     cudaFuncSetAttribute(k_cell_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    return cudaLaunchKernelEx(&cfg, k_cell_solve<double>, S, cells, order, nbig_p, begin, nbatch);
+    return cudaLaunchKernelEx(&cfg, k_cell_solve<double>, S, cells, order, nbig_p, begin, nbatch, C);
   }
   cudaFuncSetAttribute(k_cell_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  return cudaLaunchKernelEx(&cfg, k_cell_solve<float>, S, cells, order, nbig_p, begin, nbatch);
+  return cudaLaunchKernelEx(&cfg, k_cell_solve<float>, S, cells, order, nbig_p, begin, nbatch, C);
 }
 
-cudaError_t launch_cell_solve_multi(const DevState* states, const CellRef* refs, int nref, int part,
-                                    unsigned int* queue, int s, int cap_side, int cap_ny, int precision, int csize,
-                                    int nctas, cudaStream_t st) {
-  size_t smem = cell_smem_bytes(s, cap_side, cap_ny, precision);
-  cudaMemsetAsync(queue, 0, sizeof(unsigned int), st);
+// One many-instance launch: order the references (k_ref_order), then `nctas`
+// persistent CTAs (a multiple of C) in clusters of C; `order` and `nbig` are
+// device scratch (nref ints, one int), `queue` two counters.
+cudaError_t launch_cell_solve_multi(const DevState* states, const CellRef* refs, int nref, int part, int* order,
+                                    int* nbig, unsigned int* queue, size_t smem, int precision, int C,
+                                    double factor, int nctas, cudaStream_t st) {
+  C = std::max(1, C);
+  int P = 1;
+  while (P < nref) P <<= 1;
+  const size_t osm = (size_t)std::min(P, kRefOrderMax) * sizeof(unsigned long long);
+  cudaFuncSetAttribute(k_ref_order, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)osm);
+  k_ref_order<<<1, 1024, osm, st>>>(states, refs, nref, part, C, factor, nctas, order, nbig);
+  cudaMemsetAsync(queue, 0, 2 * sizeof(unsigned int), st);
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(nctas);
-  cfg.blockDim = dim3(512);
+  cfg.gridDim = dim3(std::max(C, nctas / C * C));
+  cfg.blockDim = dim3(kCellThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = csize;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = C > 1 ? 1 : 0;
+  if (precision) {
+    cudaFuncSetAttribute(k_cell_solve_multi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaLaunchKernelEx(&cfg, k_cell_solve_multi<double>, states, refs, (const int*)order, (const int*)nbig,
+                              nref, part, queue, C);
+  }
+  cudaFuncSetAttribute(k_cell_solve_multi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return cudaLaunchKernelEx(&cfg, k_cell_solve_multi<float>, states, refs, (const int*)order, (const int*)nbig, nref,
+                            part, queue, C);
+}
+
+// Resident CTAs of the many-instance kernel in clusters of C (0: not schedulable).
+int cell_multi_resident_ctas(size_t smem, int C, int precision) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = precision
+                      ? cudaFuncSetAttribute(k_cell_solve_multi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem)
+                      : cudaFuncSetAttribute(k_cell_solve_multi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (C <= 1) {
+    int per = 0;
+    e = precision ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cell_solve_multi<double>, kCellThreads, smem)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cell_solve_multi<float>, kCellThreads, smem);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return nsm;
+    }
+    return std::max(1, per * nsm);
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(kCellThreads);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (precision) {
-    cudaFuncSetAttribute(k_cell_solve_multi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    return cudaLaunchKernelEx(&cfg, k_cell_solve_multi<double>, states, refs, nref, part, queue, csize);
+  int n = 0;
+  e = precision ? cudaOccupancyMaxActiveClusters(&n, k_cell_solve_multi<double>, &cfg)
+                : cudaOccupancyMaxActiveClusters(&n, k_cell_solve_multi<float>, &cfg);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
   }
-  cudaFuncSetAttribute(k_cell_solve_multi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  return cudaLaunchKernelEx(&cfg, k_cell_solve_multi<float>, states, refs, nref, part, queue, csize);
+  return n * C;
 }

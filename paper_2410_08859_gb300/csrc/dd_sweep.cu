@@ -501,14 +501,26 @@ __global__ void k_px_product(DevState S, const double* nu_mom) {
   }
 }
 
+// g[y] = log nu(y) + beta0(y)/eps0 in float (the test pass of k_init_duals).
+__global__ void k_log_nu_beta(const double* __restrict__ lognu, const double* __restrict__ beta0, double eps0,
+                              int n, float* __restrict__ g) {
+  for (int y = blockIdx.x * blockDim.x + threadIdx.x; y < n; y += gridDim.x * blockDim.x)
+    g[y] = (float)(lognu[y] + beta0[y] / eps0);
+}
+
 // Plan from duals pi = exp((alpha0 + beta0 - c)/eps0) mu x nu, per basic cell.
 // mode 0: tight box of {y : nu_i(y) >= thr} from the full-grid log marginal,
-//         computed with two 1-D log-sum-exp passes over X_i (FP64);
+//         two 1-D log-sum-exp passes over X_i: the first in FP64 (s N values),
+//         the second over every y of the grid first in float (gf = the float
+//         log nu + beta0/eps0); only where the float value lies within a
+//         safety band of log thr (its float error is ~1e-2 at |values| ~ 1e5)
+//         is the FP64 value computed and compared, so the box is the one of
+//         the FP64 test;
 // mode 1: values on the box (dense over X_i), C_i, H_i, P_Y.
 __global__ void __launch_bounds__(256)
 k_init_duals(DevState S, const double* __restrict__ alpha0, const double* __restrict__ beta0,
-             double eps0, int mode) {
-  extern __shared__ double tsm[];   // s * N doubles (mode 0)
+             double eps0, int mode, const float* __restrict__ gf) {
+  extern __shared__ double tsm[];   // s * N doubles, then s * N floats (mode 0)
   __shared__ int bb[4];
   __shared__ double red[33 * 2];
   const int i = blockIdx.x, s = S.s, N = S.N, I = i / S.nb, J = i % S.nb;
@@ -516,6 +528,7 @@ k_init_duals(DevState S, const double* __restrict__ alpha0, const double* __rest
   const double q = S.h * S.h / eps0;
   double* arena = S.arena[*S.cur];
   if (mode == 0) {
+    float* tsmf = reinterpret_cast<float*>(tsm + s * N);
     // T(r, l) = log sum_{c in cols(X_i)} exp(alpha0/eps0 + log mu - q (c - l)^2), r in rows(X_i)
     for (int t = threadIdx.x; t < s * N; t += blockDim.x) {
       int r = t / N, l = t % N;
@@ -532,19 +545,39 @@ k_init_duals(DevState S, const double* __restrict__ alpha0, const double* __rest
         acc += exp(alpha0[x] / eps0 + S.logmu[x] - q * d * d - mx);
       }
       tsm[t] = mx + log(acc);
+      tsmf[t] = (float)tsm[t];
     }
     if (threadIdx.x == 0) { bb[0] = 1 << 30; bb[1] = -1; bb[2] = 1 << 30; bb[3] = -1; }
     __syncthreads();
     int lb[4] = {1 << 30, -1, 1 << 30, -1};
     const double lthr = log(S.thr);
+    const float lthrf = (float)lthr, qf = (float)q, L2E = (float)DD_LOG2E;
     for (int y = threadIdx.x; y < N * N; y += blockDim.x) {
       int k = y / N, l = y % N;
-      double mx = -INFINITY;
-      for (int r = 0; r < s; ++r) { double d = r0 + r - k; mx = fmax(mx, tsm[r * N + l] - q * d * d); }
-      double acc = 0.0;
-      for (int r = 0; r < s; ++r) { double d = r0 + r - k; acc += exp(tsm[r * N + l] - q * d * d - mx); }
-      double lv = S.lognu[y] + beta0[y] / eps0 + mx + log(acc);
-      if (lv >= lthr) {
+      // float value and its error bound (a few ulps of the magnitudes that cancel)
+      float mxf = -INFINITY, big = fabsf(gf[y]);
+      for (int r = 0; r < s; ++r) {
+        const float d = (float)(r0 + r - k), v = tsmf[r * N + l];
+        mxf = fmaxf(mxf, v - qf * d * d);
+        big = fmaxf(big, fabsf(v) + qf * d * d);
+      }
+      float accf = 0.0f;
+      for (int r = 0; r < s; ++r) {
+        const float d = (float)(r0 + r - k);
+        accf += dd_ex2((tsmf[r * N + l] - qf * d * d - mxf) * L2E);
+      }
+      const float lvf = gf[y] + mxf + dd_lg2(accf) * (float)DD_LN2;
+      const float band = 0.5f + 1e-5f * big;
+      bool in = lvf >= lthrf + band;
+      if (!in && lvf > lthrf - band) {
+        double mx = -INFINITY;
+        for (int r = 0; r < s; ++r) { double d = r0 + r - k; mx = fmax(mx, tsm[r * N + l] - q * d * d); }
+        double acc = 0.0;
+        for (int r = 0; r < s; ++r) { double d = r0 + r - k; acc += exp(tsm[r * N + l] - q * d * d - mx); }
+        const double lv = S.lognu[y] + beta0[y] / eps0 + mx + log(acc);
+        in = lv >= lthr;
+      }
+      if (in) {
         lb[0] = min(lb[0], k); lb[1] = max(lb[1], k); lb[2] = min(lb[2], l); lb[3] = max(lb[3], l);
       }
     }
@@ -732,20 +765,24 @@ cudaError_t launch_init_product_fill(const DevState& S, double* nu_mom, double* 
   k_px_product<<<(S.N * S.N + 255) / 256, 256, 0, st>>>(S, nu_mom);
   return cudaGetLastError();
 }
+// gscratch: N*N floats of device scratch
 cudaError_t launch_init_duals_boxes(const DevState& S, const double* alpha0, const double* beta0, double eps0,
-                                    double* nu_mom, double* mumass, long long* newoff, cudaStream_t st) {
+                                    double* nu_mom, double* mumass, long long* newoff, float* gscratch,
+                                    cudaStream_t st) {
   k_moments<<<1, 512, 0, st>>>(S.nu, S.N, S.h, nu_mom);
   k_basic_masses<<<S.nbasic, 256, 0, st>>>(S, nu_mom, mumass);
-  size_t sm = (size_t)S.s * S.N * sizeof(double);
+  const int n = S.N * S.N;
+  k_log_nu_beta<<<(n + 255) / 256, 256, 0, st>>>(S.lognu, beta0, eps0, n, gscratch);
+  size_t sm = (size_t)S.s * S.N * (sizeof(double) + sizeof(float));
   cudaFuncSetAttribute(k_init_duals, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_init_duals<<<S.nbasic, 256, sm, st>>>(S, alpha0, beta0, eps0, 0);
+  k_init_duals<<<S.nbasic, 256, sm, st>>>(S, alpha0, beta0, eps0, 0, gscratch);
   k_scan_boxes<<<1, 1024, 0, st>>>(S, newoff);
   return cudaGetLastError();
 }
 cudaError_t launch_init_duals_fill(const DevState& S, const double* alpha0, const double* beta0, double eps0,
                                    const double* w, long long* newoff, cudaStream_t st) {
   k_set_offsets<<<(S.nbasic + 255) / 256, 256, 0, st>>>(S, newoff);
-  k_init_duals<<<S.nbasic, 256, 0, st>>>(S, alpha0, beta0, eps0, 1);
+  k_init_duals<<<S.nbasic, 256, 0, st>>>(S, alpha0, beta0, eps0, 1, nullptr);
   k_px_duals<<<(S.N * S.N + 255) / 256, 256, 0, st>>>(S, alpha0, w, eps0);
   return cudaGetLastError();
 }

@@ -89,7 +89,7 @@ _SIGS = {
     "domdec_batch_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(_P), _I]),
     "domdec_batch_iterate": (_I, [_P, _I]),
     "domdec_batch_sync": (_I, [_P]),
-    "domdec_batch_autotune": (_I, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "domdec_batch_autotune": (_I, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
     "domdec_batch_free": (None, [_P]),
     "domdec_probe_peaks": (_I, [_I, _DP, _P]),
 }
@@ -366,9 +366,12 @@ class DomDecBatch:
         return _check(lib().domdec_batch_sync(self.b), "domdec_batch_sync")
 
     def autotune(self):
+        """Time the candidate cluster sizes / split thresholds for one sweep each
+        and keep the fastest; returns (cluster CTAs, split factor)."""
         c = ctypes.c_int(0)
-        _check(lib().domdec_batch_autotune(self.b, ctypes.byref(c)), "domdec_batch_autotune")
-        return c.value
+        f = ctypes.c_double(0.0)
+        _check(lib().domdec_batch_autotune(self.b, ctypes.byref(c), ctypes.byref(f)), "domdec_batch_autotune")
+        return c.value, f.value
 
     def close(self):
         if self.b:
