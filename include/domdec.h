@@ -43,7 +43,7 @@ extern "C" {
 #define DOMDEC_ENOMEM   -2   /* device allocation failed */
 #define DOMDEC_ECUDA    -3   /* a CUDA runtime call failed */
 #define DOMDEC_ETOOBIG  -4   /* a cell Y-box exceeds the kernel's shared-memory capacity (max_ny) */
-#define DOMDEC_EARENA   -5   /* the box arena overflowed (raise arena_factor) */
+#define DOMDEC_EARENA   -5   /* the box arena could not be grown after an overflow */
 #define DOMDEC_ESTATE   -6   /* the handle is in an error state */
 #define DOMDEC_ENOLIB   -7   /* reserved for bindings: library not loaded */
 #define DOMDEC_EEMPTY   -8   /* a composite cell has no Y-support left: every member basic-cell marginal
@@ -83,7 +83,11 @@ typedef struct {
   int    precision;    /* DOMDEC_FP32 | DOMDEC_FP64 */
   int    box_margin;   /* pixels added around B_J (0 in the paper) */
   int    max_ny;       /* capacity of a cell Y-box in the kernel (0: default 8192 for FP32, 4096 for FP64) */
-  double arena_factor; /* box arena capacity in units of N*N doubles (0: default 48) */
+  double arena_factor; /* box arena capacity in units of N*N doubles (0: default 48, and at least 8x the
+                          initial plan).  When the new boxes of a sub-batch would not fit, the sweep kernels
+                          stop changing the state from that sub-batch on; the next synchronising call grows
+                          the arena (twice the capacity) and runs the skipped sub-batches, so the result is
+                          the same as with a large arena (DOMDEC_EARENA only if growth fails repeatedly) */
   double eps_init;     /* eps of the warm-start duals passed to domdec_init (ignored without duals) */
   int    profile;      /* 1: time every kernel of a sweep with CUDA events on the handle's stream */
   int    spill_slots;  /* cells whose Y-box exceeds max_ny run from global memory slots (per sub-batch): 0 = default
@@ -121,6 +125,7 @@ typedef struct {
   long long lse_terms;       /* exp terms of the cell log-sum-exp passes (algorithmic work of the cell kernel) */
   long long box_points;      /* sum over the cell solves of the Y-box size |B_J| (the points that the mixing
                                 and box refresh of a7 read and write) */
+  long long arena_regrows;   /* arena growths after a sub-batch's new boxes did not fit (see arena_factor) */
   int       max_cell_iters;  /* largest iteration count of one cell solve */
   int       max_ny;          /* largest cell Y-box seen */
 } domdec_stats;
@@ -261,9 +266,10 @@ int domdec_decision_log(domdec_t h, double* out, int max_records);
 int domdec_kernel_times(domdec_t h, double ms[4], long long launches[4], int reset);
 
 /* Per-cell records of the most recent sub-batch (diagnostics): record j is
- * out[8j..8j+7] = (k0, l0, H, W of the cell's Y-box B_J, cell Sinkhorn
+ * out[9j..9j+8] = (k0, l0, H, W of the cell's Y-box B_J, cell Sinkhorn
  * iterations, status (0 ok, 1 maxit, 2 empty, 3 too big, 4 non-finite), last
- * PD/lam, spill slot or -1).  Returns the number of records (<= max_records).
+ * PD/lam, spill slot or -1, duration of the solve in microseconds on the GPU's
+ * global timer).  Returns the number of records (<= max_records).
  * Synchronises. */
 int domdec_cell_log(domdec_t h, double* out, int max_records);
 
@@ -371,6 +377,13 @@ int domdec_full_sinkhorn_noalloc(const double* mu, const double* nu, int N, doub
  * out[6] SM count, out[7] blocks launched.  Allocates a few KB with
  * cudaMallocAsync; synchronises. */
 int domdec_probe_peaks(int iters, double out[8], void* stream);
+
+/* Diagnostics helper (the paper has no counterpart): y[i] = the library's
+ * table-driven double logarithm of x[i] (the one the step-size decision
+ * uses), for n DEVICE values x > 0 (finite, normal or subnormal); y is a device
+ * buffer of n doubles.  Lets a test compare it with CUDA's log.
+ * Synchronises `stream`. */
+int domdec_probe_log(const double* x, double* y, int n, void* stream);
 
 #ifdef __cplusplus
 }

@@ -45,7 +45,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     """Compile (if sources are newer than the library) and return its path."""
     os.makedirs(LIBDIR, exist_ok=True)
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
-    deps = srcs + [os.path.join(CSRC, "dd_common.cuh"), os.path.join(ROOT, "include", "domdec.h")]
+    deps = srcs + [os.path.join(CSRC, "dd_common.cuh"), os.path.join(CSRC, "dd_log_table.cuh"),
+                   os.path.join(ROOT, "include", "domdec.h")]
     if not force and os.path.exists(LIB):
         newest = max(os.path.getmtime(p) for p in deps)
         if os.path.getmtime(LIB) >= newest:

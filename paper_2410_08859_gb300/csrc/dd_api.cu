@@ -86,6 +86,7 @@ struct domdec_s {
   long long sweeps = 0;
   long long slot = 0;
   unsigned long long maxit_seen = 0;  // maxit-cell counter at the previous domdec_sync
+  long long arena_regrows = 0;        // arena growths after a halted sub-batch
   int sticky = 0;
   int last_batch = 0;
   double eps0 = 0.0, err0 = 0.0;           // eps and err given at domdec_init (restored by domdec_reset)
@@ -166,16 +167,28 @@ int check_params(const domdec_params* p, int N) {
   return DOMDEC_OK;
 }
 
+int enqueue_sweep(domdec_s* h, int part, long long slot0, int first);
+int batches_per_sweep(domdec_s* h, int part);
+int recover_arena(domdec_s* h);
+
 int read_status(domdec_s* h) {
   // slot 63 of the pinned buffer is reserved for the status word
   int* hs = reinterpret_cast<int*>(h->h_pinned + 63);
-  cudaError_t e = cudaMemcpyAsync(hs, h->S.status, sizeof(int), cudaMemcpyDeviceToHost, h->st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
-  if (e != cudaSuccess) return fail(h, DOMDEC_ECUDA);
-  int st = *hs;
+  int st = 0;
+  for (int attempt = 0;; ++attempt) {
+    cudaError_t e = cudaMemcpyAsync(hs, h->S.status, sizeof(int), cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) return fail(h, DOMDEC_ECUDA);
+    st = *hs;
+    if (st != ST_ARENA) break;
+    // a sub-batch's new boxes did not fit: grow the arena and rerun what did not run
+    if (attempt >= 4) return fail(h, DOMDEC_EARENA);
+    const int rc = recover_arena(h);
+    if (rc) return fail(h, rc);
+  }
   if (st & ST_BADINPUT) return fail(h, DOMDEC_EINVAL);
   if (st & ST_TOOBIG) return fail(h, DOMDEC_ETOOBIG);
-  if (st & ST_ARENA) return fail(h, DOMDEC_EARENA);
+  if (st & (ST_ARENA | ST_ARENA_LOST)) return fail(h, DOMDEC_EARENA);
   if (st & ST_EMPTY) return fail(h, DOMDEC_EEMPTY);
   if (st & ST_NONFINITE) return fail(h, DOMDEC_ENONFINITE);
   return DOMDEC_OK;
@@ -201,6 +214,51 @@ int ensure_arena(domdec_s* h) {
   h->S.arena[0] = a0;
   h->S.arena[1] = a1;
   h->S.cap = ncap;
+  return DOMDEC_OK;
+}
+
+// Grow the arena of a handle halted by the reservation of k_decide (the state
+// is that after the last completed sub-batch), clear the halt and enqueue the
+// sub-batches that were skipped: the device's decision count says how many of
+// the enqueued sub-batches completed.
+int recover_arena(domdec_s* h) {
+  unsigned long long done = 0, live = 0;
+  cudaError_t e = cudaMemcpyAsync(&done, h->S.slotctr, sizeof(done), cudaMemcpyDeviceToHost, h->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&live, h->S.head, sizeof(live), cudaMemcpyDeviceToHost, h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return DOMDEC_ECUDA;
+  const long long ncap = std::max(2 * h->S.cap, 4 * (long long)live + 1024);
+  double *a0 = nullptr, *a1 = nullptr;
+  if (cudaMalloc(&a0, ncap * sizeof(double)) != cudaSuccess) return DOMDEC_ENOMEM;
+  if (cudaMalloc(&a1, ncap * sizeof(double)) != cudaSuccess) { cudaFree(a0); return DOMDEC_ENOMEM; }
+  if (launch_regrow(h->S, a0, a1, h->d_newoff, h->st) != cudaSuccess) return DOMDEC_ECUDA;
+  if (cudaStreamSynchronize(h->st) != cudaSuccess) return DOMDEC_ECUDA;
+  for (auto& q : h->allocs)
+    if (q == h->S.arena[0] || q == h->S.arena[1]) { cudaFree(q); q = nullptr; }
+  h->allocs.push_back(a0);
+  h->allocs.push_back(a1);
+  h->S.arena[0] = a0;
+  h->S.arena[1] = a1;
+  h->S.cap = ncap;
+  ++h->arena_regrows;
+  if (cudaMemsetAsync(h->S.status, 0, sizeof(int), h->st) != cudaSuccess) return DOMDEC_ECUDA;
+  // the enqueued sweeps, oldest first: find the first sub-batch that did not run
+  long long cum = 0;
+  for (long long k = 0; k < h->sweeps; ++k) {
+    const int part = (int)(k % 2);
+    const int nb = batches_per_sweep(h, part);
+    if ((unsigned long long)(cum + nb) > done) {
+      const int first = (int)((long long)done - cum);
+      int rc = enqueue_sweep(h, part, cum, first);
+      long long c2 = cum + nb;
+      for (long long k2 = k + 1; rc == DOMDEC_OK && k2 < h->sweeps; ++k2) {
+        rc = enqueue_sweep(h, (int)(k2 % 2), c2, 0);
+        c2 += batches_per_sweep(h, (int)(k2 % 2));
+      }
+      return rc;
+    }
+    cum += nb;
+  }
   return DOMDEC_OK;
 }
 
@@ -244,8 +302,9 @@ void prof_collect(domdec_s* h) {
   h->pend.clear();
 }
 
-// Enqueue one sweep of partition `part`.
-int enqueue_sweep(domdec_s* h, int part, long long slot0) {
+// Enqueue one sweep of partition `part`, from its `first`-th non-empty batch on
+// (0: the whole sweep).
+int enqueue_sweep(domdec_s* h, int part, long long slot0, int first = 0) {
   const int prec = h->p.precision;
   std::vector<std::pair<int, int>> batches;
   if (h->p.strategy == DOMDEC_STAGGERED || h->p.strategy == DOMDEC_STAGGERED_LINE) {
@@ -257,9 +316,11 @@ int enqueue_sweep(domdec_s* h, int part, long long slot0) {
   // largest-first order of the cells of every sub-batch of this sweep (the
   // member boxes of a sub-batch do not change before its own cell solve)
   if (launch_cell_order(h->S, part, h->order_mode, h->cell_nctas, h->st) != cudaSuccess) return DOMDEC_ECUDA;
+  int nonempty = 0;
   for (auto& bt : batches) {
     const int begin = bt.first, nbt = bt.second - bt.first;
     if (nbt <= 0) continue;
+    if (nonempty++ < first) continue;
     const int slot = (int)((slot0 + k++) % LOGCAP);
     (void)slot;
     cudaEvent_t ev = prof_begin(h);
@@ -346,9 +407,12 @@ int load_problem(domdec_s* h, const double* mu, const double* nu, const double* 
   if (e != cudaSuccess) return DOMDEC_ECUDA;
   int rc = read_status(h);
   if (rc) return rc;
+  // default: 48 N^2 and at least 8x the initial plan; an explicit arena_factor is
+  // taken as given (down to the initial plan itself: growth happens on demand)
   const double fac = h->p.arena_factor > 0 ? h->p.arena_factor : 48.0;
-  const long long need = std::max((long long)(fac * n), 8 * total + 1024);
-  if (!S.arena[0] || S.cap < 8 * total + 1024) {
+  const long long floor_cap = h->p.arena_factor > 0 ? total + 1024 : 8 * total + 1024;
+  const long long need = std::max((long long)(fac * n), floor_cap);
+  if (!S.arena[0] || S.cap < floor_cap) {
     for (auto& q : h->allocs)
       if (q && (q == S.arena[0] || q == S.arena[1])) { cudaFree(q); q = nullptr; }
     S.arena[0] = S.arena[1] = nullptr;
@@ -825,8 +889,9 @@ int domdec_cell_log(domdec_t h, double* out, int max_records) {
     return fail(h, DOMDEC_ECUDA);
   for (int j = 0; j < cnt; ++j) {
     const CellOut& o = rec[j];
-    double* r = out + 8 * j;
+    double* r = out + 9 * j;
     r[0] = o.k0; r[1] = o.l0; r[2] = o.H; r[3] = o.W; r[4] = o.iters; r[5] = o.status; r[6] = o.gap; r[7] = o.slot;
+    r[8] = o.usec;
   }
   return cnt;
 }
@@ -848,6 +913,7 @@ int domdec_get_stats(domdec_t h, domdec_stats* s) {
   s->safe_steps = (long long)c[4];
   s->lse_terms = (long long)c[7];
   s->box_points = (long long)c[8];
+  s->arena_regrows = h->arena_regrows;
   s->max_cell_iters = (int)c[5];
   s->max_ny = (int)c[6];
   s->box_entries = (long long)h->h_pinned[4];

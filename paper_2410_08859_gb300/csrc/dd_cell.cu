@@ -243,6 +243,7 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
   __shared__ BoxRec sbox[4];
   __shared__ int sgeo[8];
   CellOut* out = S.cout + cidx;
+  const unsigned long long t_start = dd_global_ns();
   const double* __restrict__ arena = S.arena[*S.cur];
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int gtid = tid, gthr = nthr;
@@ -285,7 +286,7 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
     if (tid == 0) {
       CellOut o;
       o.k0 = k0; o.l0 = l0; o.H = H; o.W = W; o.iters = 0; o.status = sgeo[4];
-      o.D1 = o.D2 = 0; o.gap = 0.0; o.dKX[0] = o.dKX[1] = 0.0; o.slot = -1; o.pad = 0;
+      o.D1 = o.D2 = 0; o.gap = 0.0; o.dKX[0] = o.dKX[1] = 0.0; o.slot = -1; o.usec = 0;
       for (int q = 0; q < 4; ++q) {
         int bi = cd.mem[q];
         o.Ct[q] = bi >= 0 ? S.Cc[bi] : 0.0;
@@ -850,7 +851,8 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
     o.iters = it;
     o.status = nonfinite ? CELL_NONFINITE : ((S.err >= 0.0 && gap > tol) ? CELL_MAXIT : CELL_OK);
     o.D1 = D1; o.D2 = D2;
-    o.slot = slot; o.pad = 0;
+    o.slot = slot;
+    o.usec = (int)min((dd_global_ns() - t_start) / 1000ull, 2147483647ull);
     o.gap = gap;
     o.dKX[0] = dk[0]; o.dKX[1] = dk[1];
     for (int q4 = 0; q4 < 4; ++q4) {
@@ -902,6 +904,7 @@ __device__ __forceinline__ void cell_solve_dist(const DevState& S, const CellDes
   __shared__ int dgeo[8];
   __shared__ double dx[kDistMaxC * 16];                 // partial sums of every CTA of the cluster
   CellOut* out = S.cout + cidx;
+  const unsigned long long t_start = dd_global_ns();
   const double* __restrict__ arena = S.arena[*S.cur];
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int gtid = crank * nthr + tid, gthr = C * nthr;
@@ -957,7 +960,7 @@ __device__ __forceinline__ void cell_solve_dist(const DevState& S, const CellDes
     if (tid == 0 && crank == 0) {
       CellOut o;
       o.k0 = k0; o.l0 = l0; o.H = H; o.W = W; o.iters = 0; o.status = dgeo[4];
-      o.D1 = o.D2 = 0; o.gap = 0.0; o.dKX[0] = o.dKX[1] = 0.0; o.slot = -1; o.pad = 0;
+      o.D1 = o.D2 = 0; o.gap = 0.0; o.dKX[0] = o.dKX[1] = 0.0; o.slot = -1; o.usec = 0;
       for (int q = 0; q < 4; ++q) {
         const int bi = cd.mem[q];
         o.Ct[q] = bi >= 0 ? S.Cc[bi] : 0.0;
@@ -1349,7 +1352,8 @@ __device__ __forceinline__ void cell_solve_dist(const DevState& S, const CellDes
   o.iters = it;
   o.status = nonfinite ? CELL_NONFINITE : ((S.err >= 0.0 && gap > tol) ? CELL_MAXIT : CELL_OK);
   o.D1 = D1; o.D2 = D2;
-  o.slot = slot; o.pad = 0;
+  o.slot = slot;
+  o.usec = (int)min((dd_global_ns() - t_start) / 1000ull, 2147483647ull);
   o.gap = gap;
   o.dKX[0] = dk[0]; o.dKX[1] = dk[1];
   for (int q4 = 0; q4 < 4; ++q4) {
@@ -1387,6 +1391,7 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, const int* __restri
   namespace cg = cooperative_groups;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int sj;
+  if (*(volatile int*)S.status & ST_ARENA) return;   // halted until the host grows the arena
   const int C = S.dist_c;
   const int nbig = (C > 1 && order) ? *nbig_p : 0;
   if (C > 1 && cluster > 1) {
@@ -1561,7 +1566,8 @@ k_cell_solve_multi(const DevState* __restrict__ states, const CellRef* __restric
       if (j >= nbig) break;
       const CellRef rf = refs[order[j]];
       load_state(rf.inst);
-      cell_solve_dist<R>(sS, sS.cells[part][rf.cell], rf.pos, rf.nbatch, crank, smem_raw);
+      if (!(*(volatile int*)sS.status & ST_ARENA))   // the same value in every CTA of the cluster
+        cell_solve_dist<R>(sS, sS.cells[part][rf.cell], rf.pos, rf.nbatch, crank, smem_raw);
       cg::this_cluster().sync();
     }
   }
@@ -1574,7 +1580,7 @@ k_cell_solve_multi(const DevState* __restrict__ states, const CellRef* __restric
     if (j >= nref) break;
     const CellRef rf = refs[order ? order[j] : j];
     load_state(rf.inst);
-    cell_solve_body<R>(sS, sS.cells[part][rf.cell], rf.pos, rf.nbatch, smem_raw);
+    if (!(*(volatile int*)sS.status & ST_ARENA)) cell_solve_body<R>(sS, sS.cells[part][rf.cell], rf.pos, rf.nbatch, smem_raw);
   }
 }
 

@@ -3,14 +3,20 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "dd_log_table.cuh"
+
 #define DD_LOG2E 1.4426950408889634
 #define DD_LN2 0.6931471805599453
 
 // ---------------------------------------------------------------- status codes
 // Per-cell status written by the cell kernel.
 enum { CELL_OK = 0, CELL_MAXIT = 1, CELL_EMPTY = 2, CELL_TOOBIG = 3, CELL_NONFINITE = 4 };
-// Bits of the handle's device status word.
-enum { ST_TOOBIG = 1, ST_ARENA = 2, ST_EMPTY = 4, ST_NONFINITE = 8, ST_BADINPUT = 16 };
+// Bits of the handle's device status word.  ST_ARENA: a sub-batch's new boxes
+// would not fit the arena; the decision kernel set it before any state
+// changed, and every later sweep kernel leaves the state untouched until the
+// host has grown the arena and re-enqueued the sub-batches that did not run.
+// ST_ARENA_LOST: the allocation guard of the mixing kernel fired (state lost).
+enum { ST_TOOBIG = 1, ST_ARENA = 2, ST_EMPTY = 4, ST_NONFINITE = 8, ST_BADINPUT = 16, ST_ARENA_LOST = 32 };
 
 // ------------------------------------------------------------------ geometry
 // One composite cell: its X box [i0, i0+nx1) x [j0, j0+nx2) (always a
@@ -26,7 +32,7 @@ struct CellDesc {
 struct CellOut {
   int k0, l0, H, W;      // the cell's Y box B_J
   int iters, status, D1, D2;
-  int slot, pad;         // spill slot of an oversized box (-1: none)
+  int slot, usec;        // spill slot of an oversized box (-1: none); duration of the solve (microseconds)
   double Ct[4], Ht[4], mass[4];  // per quadrant: <c, pi~_i>, KL(pi~_i | mu_i x nu), |nu~_i|
   double dKX[2];         // sum_{x in X_J} [mu phi(P'/mu) - mu phi(P/mu)] for theta = 1 and theta_safe
   double gap;            // last PD/lam of the cell
@@ -98,6 +104,13 @@ struct CellRef {
   int inst, cell, pos, nbatch;
 };
 
+// Global nanosecond timer (the same on every SM).
+__device__ __forceinline__ unsigned long long dd_global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
 // ------------------------------------------------------------------ math
 __device__ __forceinline__ float dd_ex2(float x) {
   float y;
@@ -132,6 +145,44 @@ template <typename R> __device__ __forceinline__ R dd_psi(R d) {
   }
   R e = dd_ex2(d * R(DD_LOG2E));
   return e * (d - R(1)) + R(1);
+}
+
+// Natural logarithm of a positive finite double by Tang's table-driven method
+// (ACM TOMS 16, 1990): x = 2^e m with m in [1, 2); c_j = 1 + j/128 is the
+// nearest to m (j = 128 moves to e + 1 with c = 1); f = m - c_j is exact;
+// r = f / c_j as f times the rounded reciprocal (|r| <= 2^-8); log1p(r) by its
+// Taylor polynomial up to r^7 (remainder below 2^-59 relative);
+// log x = e log 2 + log c_j + log1p(r).  About 12 FP64 operations against the
+// library logarithm's longer sequence; the GPU test compares it with CUDA's
+// log (a few ulp).  The tables are generated by gen_log_table.py.
+__device__ __forceinline__ double dd_log(double x) {
+  int hi = __double2hiint(x);
+  int lo = __double2loint(x);
+  int e = 0;
+  if (hi < 0x00100000) {   // subnormal: scale into the normal range
+    x *= 18014398509481984.0;   // 2^54
+    hi = __double2hiint(x);
+    lo = __double2loint(x);
+    e = -54;
+  }
+  e += (hi >> 20) - 1023;
+  const int mant = hi & 0x000fffff;
+  int j = ((mant >> 12) + 1) >> 1;   // the leading 7 fraction bits, rounded: 0..128
+  double m = __hiloint2double(mant | 0x3ff00000, lo);
+  if (j == 128) {
+    e += 1;
+    m *= 0.5;
+    j = 0;
+  }
+  const double f = m - (1.0 + j * 0.0078125);
+  const double r = f * kInvC[j];
+  double p = fma(r, 1.0 / 7.0, -1.0 / 6.0);
+  p = fma(p, r, 0.2);
+  p = fma(p, r, -0.25);
+  p = fma(p, r, 1.0 / 3.0);
+  p = fma(p, r, -0.5);
+  const double l1p = fma(p, r * r, r);
+  return fma((double)e, 0.6931471805599453, kLogC[j] + l1p);
 }
 
 // mu phi(p/mu) with phi(s) = s log s - s + 1 (phi(0) = 1), in double.

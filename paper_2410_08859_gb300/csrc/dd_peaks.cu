@@ -5,6 +5,7 @@
 // global nanosecond timer).
 #include <cuda_runtime.h>
 
+#include "dd_common.cuh"
 #include "domdec.h"
 
 namespace {
@@ -140,4 +141,18 @@ extern "C" int domdec_probe_peaks(int iters, double out[8], void* stream) {
   cudaFreeAsync(clk, st);
   if (cudaStreamSynchronize(st) != cudaSuccess && rc == DOMDEC_OK) rc = DOMDEC_ECUDA;
   return rc;
+}
+
+namespace {
+__global__ void k_probe_log(const double* __restrict__ x, double* __restrict__ y, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) y[i] = dd_log(x[i]);
+}
+}  // namespace
+
+extern "C" int domdec_probe_log(const double* x, double* y, int n, void* stream) {
+  if (!x || !y || n < 0) return DOMDEC_EINVAL;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (n) k_probe_log<<<(n + 255) / 256, 256, 0, st>>>(x, y, n);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) return DOMDEC_ECUDA;
+  return DOMDEC_OK;
 }

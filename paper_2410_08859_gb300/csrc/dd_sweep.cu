@@ -16,7 +16,7 @@ __device__ __forceinline__ float kl_term_f(double p, double m) {
 // mu phi(p/mu) in double from log mu (no division).
 __device__ __forceinline__ double kl_term_log(double p, double m, double log_m) {
   if (p <= 0.0) return m;
-  return p * (log(p) - log_m) - p + m;
+  return p * (dd_log(p) - log_m) - p + m;
 }
 
 // Tracked score (the sum of per-basic-cell transport cost and entropy plus the
@@ -26,6 +26,7 @@ __device__ __forceinline__ void decide_body(const DevState& S, const CellDesc* _
                                             int nbatch, int bid, int nblk) {
   __shared__ double red[33 * 5];
   __shared__ bool is_last;
+  if (*(volatile int*)S.status & ST_ARENA) return;   // halted until the host grows the arena
   const int n = S.N * S.N;
   const double lam = S.lam, eps = S.eps, th_s = 1.0 / nbatch;
   double v[5] = {0, 0, 0, 0, 0};
@@ -64,7 +65,7 @@ __device__ __forceinline__ void decide_body(const DevState& S, const CellDesc* _
   if (!is_last) return;
   __threadfence();
   // last block: fixed-order reduction of the block partials and the per-cell terms
-  double tot[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  double tot[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   for (int b = threadIdx.x; b < nblk; b += blockDim.x)
     for (int k = 0; k < 5; ++k) tot[k] += ((volatile double*)S.red)[b * 5 + k];
   for (int j = threadIdx.x; j < nbatch; j += blockDim.x) {
@@ -75,13 +76,22 @@ __device__ __forceinline__ void decide_body(const DevState& S, const CellDesc* _
       int bi = cd.mem[q];
       if (bi < 0) continue;
       tot[5] += (o.Ct[q] - S.Cc[bi]) + eps * (o.Ht[q] - S.Hh[bi]);
+      tot[8] += (double)o.H * o.W;   // the new box of member q lies inside B_J
     }
     tot[6] += o.dKX[0];
     tot[7] += o.dKX[1];
   }
-  __shared__ double red8[33 * 8];
-  block_sum<8>(tot, red8);
+  __shared__ double red8[33 * 9];
+  block_sum<9>(tot, red8);
   if (threadIdx.x != 0) return;
+  // reserve the arena space of the sub-batch's new boxes before anything changes
+  if ((double)*S.head + tot[8] > (double)S.cap) {
+    atomicOr(S.status, ST_ARENA);
+    *S.red_count = 0u;
+    if (S.spill_count) *S.spill_count = 0u;
+    if (S.queue) { S.queue[0] = 0u; S.queue[1] = 0u; }
+    return;
+  }
   const double dL = tot[5], dKX1 = tot[6], dKXs = tot[7];
   const double E0 = tot[4] + lam * tot[0] + lam * tot[1];
   const double dg = dL + lam * dKX1 + lam * tot[2];          // E(1) - E
@@ -158,7 +168,7 @@ constexpr double kLineGtol = 1e-12, kLineXtol = 1e-12, kLinePfloor = 1e-300;
 __global__ void __launch_bounds__(512)
 k_line_eval(DevState S, const CellDesc* __restrict__ cells, int begin, int nbatch, int first, double* partials) {
   __shared__ double red[33 * 4];
-  if (S.line[5] != 0.0) return;   // uniform: every block reads the same flag
+  if (S.line[5] != 0.0 || (*(volatile int*)S.status & ST_ARENA)) return;   // uniform across blocks
   const double z = first ? 1.0 : S.line[2], lo = S.line[6];
   double v[4] = {0.0, 0.0, 0.0, 0.0};
   auto term = [&](double p0, double d, double m) {
@@ -192,7 +202,7 @@ k_line_eval(DevState S, const CellDesc* __restrict__ cells, int begin, int nbatc
 
 // One step of the search from the sums of the last evaluation (one thread).
 __global__ void k_line_step(DevState S, int first, int last) {
-  if (threadIdx.x != 0 || S.line[5] != 0.0) return;
+  if (threadIdx.x != 0 || S.line[5] != 0.0 || (*(volatile int*)S.status & ST_ARENA)) return;
   double* L = S.line;
   const double lam = S.lam;
   const double g = L[7] + lam * L[12], h = lam * L[13], scale = fabs(L[7]) + lam * L[14];
@@ -240,7 +250,7 @@ __device__ __forceinline__ void apply_body(const DevState& S, const CellDesc cd,
     S.dPY[(o.k0 + kk) * N + o.l0 + ll] = 0.0;
   }
   const int bi = cd.mem[q];
-  if (bi < 0) return;
+  if (bi < 0 || (*(volatile int*)S.status & ST_ARENA)) return;
   const double th = *S.theta, thr = S.thr;
   double* arena = S.arena[*S.cur];
   int nst;
@@ -282,8 +292,8 @@ __device__ __forceinline__ void apply_body(const DevState& S, const CellDesc cd,
     }
     long long sz = (long long)nb.H * nb.W;
     unsigned long long off = atomicAdd(S.head, (unsigned long long)sz);
-    if ((long long)off + sz > S.cap) {
-      atomicOr(S.status, ST_ARENA);
+    if ((long long)off + sz > S.cap) {   // excluded by the reservation in k_decide
+      atomicOr(S.status, ST_ARENA_LOST);
       nb.H = nb.W = 0;
       off = 0;
     }

@@ -48,7 +48,7 @@ class domdec_stats(ctypes.Structure):
                 ("cell_iters", ctypes.c_longlong), ("maxit_cells", ctypes.c_longlong),
                 ("greedy_steps", ctypes.c_longlong), ("safe_steps", ctypes.c_longlong),
                 ("box_entries", ctypes.c_longlong), ("lse_terms", ctypes.c_longlong),
-                ("box_points", ctypes.c_longlong),
+                ("box_points", ctypes.c_longlong), ("arena_regrows", ctypes.c_longlong),
                 ("max_cell_iters", ctypes.c_int),
                 ("max_ny", ctypes.c_int)]
 
@@ -92,6 +92,7 @@ _SIGS = {
     "domdec_batch_autotune": (_I, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
     "domdec_batch_free": (None, [_P]),
     "domdec_probe_peaks": (_I, [_I, _DP, _P]),
+    "domdec_probe_log": (_I, [_P, _P, _I, _P]),
 }
 
 
@@ -257,10 +258,11 @@ def domdec_kernel_times(h, reset=True):
 
 
 def domdec_cell_log(h, max_records=4096):
-    """(n, 8) array per cell of the last sub-batch: k0, l0, H, W, iters, status, gap, spill slot."""
-    out = (ctypes.c_double * (8 * max_records))()
+    """(n, 9) array per cell of the last sub-batch: k0, l0, H, W, iters, status, gap, spill slot,
+    solve duration (us)."""
+    out = (ctypes.c_double * (9 * max_records))()
     cnt = _check(lib().domdec_cell_log(h, out, int(max_records)), "domdec_cell_log")
-    return np.array(out[:8 * cnt]).reshape(cnt, 8)
+    return np.array(out[:9 * cnt]).reshape(cnt, 9)
 
 
 def domdec_get_stats(h):
@@ -345,6 +347,12 @@ def domdec_probe_peaks(iters=20000, stream=None):
     return {"ex2_per_s": out[0], "ex2_per_sm_clk": out[1], "ex2_sm_mhz": out[2],
             "ffma_per_s": out[3], "ffma_per_sm_clk": out[4], "ffma_sm_mhz": out[5],
             "sms": int(out[6]), "blocks": int(out[7])}
+
+
+def domdec_probe_log(x, y, stream=None):
+    """y = the library's double logarithm of x (device float64 tensors)."""
+    _check(lib().domdec_probe_log(_ptr(x), _ptr(y, writable=True), int(x.numel()), _stream_ptr(stream)),
+           "domdec_probe_log")
 
 
 class DomDecBatch:
