@@ -217,6 +217,7 @@ def sweep_config(dd, torch, name, lam, steps, warmup, flush, peaks_meas, pk, pre
     a0, b0, t_w, it_w = warm_start(dd, torch, mu_d, nu_d, N, eps, lam)
     g = dd.DomDec(mu_d, nu_d, eps, lam, s, alpha0=a0, beta0=b0, eps_init=2 * eps, precision=precision,
                   tau=0.0, err=2e-5, profile=1, cell_ctas=cell_ctas)
+    tuned = g.autotune() if cell_ctas == 0 else None
     d = timed_sweeps(dd, torch, g, steps, warmup, flush)
     cert = g.pd_gap()
     g.close()
@@ -224,6 +225,7 @@ def sweep_config(dd, torch, name, lam, steps, warmup, flush, peaks_meas, pk, pre
     return {"value": d["cell_iters"] / (d["ms"] / 1e3), "unit": UNIT, "ms_per_sweep": d["ms"] / steps,
             "mufu_frac": rl["frac"], "cell_kernel_share": rl["kernel_share"],
             "mean_iters_per_solve": d["cell_iters"] / max(d["cell_solves"], 1), "max_ny": d["max_ny"],
+            "autotuned": None if tuned is None else {"cluster_ctas": tuned[0], "split": tuned[1]},
             "warm_start_s": t_w, "warm_start_iters": it_w, "rel_gap_after": float(cert[2])}
 
 
@@ -622,6 +624,8 @@ def main():
     a0, b0, t_warm, it_warm = warm_start(dd, torch, mu_d, nu_d, N, eps, lam)
     g = dd.DomDec(mu_d, nu_d, eps, lam, s, alpha0=a0, beta0=b0, eps_init=2 * eps, precision="fp32",
                   tau=0.0, err=2e-5, profile=1, cell_ctas=args.cell_ctas)
+    # the cell launch's cluster size and split threshold, chosen on this GPU (untimed sweeps)
+    tuned = g.autotune() if args.cell_ctas == 0 else None
     if world > 1:
         dist.barrier()
     d = timed_sweeps(dd, torch, g, args.steps, args.warmup, flush, sample_clocks=(rank == 0))
@@ -674,7 +678,9 @@ def main():
             "config": {"workload": args.workload, "N": N, "basic_cell": s, "eps": eps, "lam": lam,
                        "eps_scaling": "1 -> 2 eps by global Sinkhorn (warm start), DomDec at eps",
                        "strategy": "staggered", "tau": 0.0, "err": 2e-5, "precision": "fp32 cell / fp64 score",
-                       "cell_ctas": args.cell_ctas, "l2": "flushed (256 MB write) between timed steps",
+                       "cell_ctas": args.cell_ctas,
+                       "autotuned": None if tuned is None else {"cluster_ctas": tuned[0], "split": tuned[1]},
+                       "l2": "flushed (256 MB write) between timed steps",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": d["clocks"],
             "gpu_launches": launches, "cell_iters_timed": int(iters_all),

@@ -112,6 +112,9 @@ typedef struct {
                           plan rows by m_i/|nu_i|, receivers share the donated mass at every y in
                           proportion to their deficits (nu_J preserved); C_i, H_i, P_X follow the
                           balanced plan.  Cells then run on one CTA each; not for batches.  0: off */
+  double cell_split;   /* a cell goes to a cluster when its estimated work exceeds cell_split times the mean
+                          work per resident CTA of its sub-batch (or when its box exceeds one CTA's shared
+                          memory); 0: default 2.  domdec_autotune chooses it with the cluster size */
 } domdec_params;
 
 typedef struct {
@@ -162,6 +165,15 @@ int domdec_init(domdec_t* out, const double* mu, const double* nu, int N,
  * Synchronises. */
 int domdec_reset(domdec_t h, const double* mu, const double* nu, const double* alpha0,
                  const double* beta0, double eps_init);
+
+/* Autotuner of the cell kernel's launch: runs one sweep with each candidate --
+ * one CTA per cell, and clusters of 2, 4 and 8 CTAs (as far as the handle's
+ * cluster layout and the GPU allow) with the split thresholds 0.5, 1 and 2
+ * (cell_split) -- times each with CUDA events on the handle's stream and keeps
+ * the highest cell-iteration rate for later sweeps.  The timed sweeps are real
+ * sweeps (they continue the alternation).  *cluster_ctas and *split_factor (if
+ * not NULL) receive the choice.  Synchronises. */
+int domdec_autotune(domdec_t h, int* cluster_ctas, double* split_factor);
 
 /* Run n_sweeps partition sweeps (A, B, A, ... continuing the alternation of
  * earlier calls).  Enqueues only; errors found on the device are reported by

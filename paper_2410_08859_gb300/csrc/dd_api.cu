@@ -18,9 +18,10 @@
 // ---- kernels' launch wrappers (dd_cell.cu, dd_sweep.cu, dd_sinkhorn.cu)
 size_t cell_smem_bytes(int s, int cap_side, int cap_ny, int precision);
 cudaError_t launch_cell_solve(const DevState& S, const CellDesc* cells, const int* order, const int* nbig_p,
-                              int begin, int nbatch, int precision, size_t smem, int nctas, int cluster,
+                              int begin, int nbatch, int precision, size_t smem, int nctas, int crun, int cluster,
                               cudaStream_t st);
-cudaError_t launch_cell_order(const DevState& S, int part, int mode, int slots, cudaStream_t st);
+cudaError_t launch_cell_order(const DevState& S, int part, int mode, int slots, int C, double factor,
+                              cudaStream_t st);
 size_t dist_smem_bytes(int s, int C, int cap_w, int cap_hl, int cap_nyl, int precision);
 int cell_static_smem(int precision);
 int cell_resident_ctas(size_t smem, int C, int precision);
@@ -91,7 +92,10 @@ struct domdec_s {
   int last_batch = 0;
   double eps0 = 0.0, err0 = 0.0;           // eps and err given at domdec_init (restored by domdec_reset)
   double *d_a0 = nullptr, *d_b0 = nullptr, *d_w4 = nullptr;  // warm-start duals and 4 N*N scratch
-  int cell_nctas = 0;      // persistent CTAs of the cell kernel (whole clusters of S.dist_c)
+  int res[4] = {0, 0, 0, 0};   // resident CTAs of the cell kernel with clusters of 1, 2, 4, 8
+  int crun = 1;            // cluster size of the cell launches (<= S.dist_c)
+  double split = 2.0;      // cluster cells: work above split x the mean work per CTA
+  int cell_nctas = 0;      // persistent CTAs of the cell kernel (whole clusters of crun)
   int helper_ctas = 0;     // single CTAs on the SMs that the resident clusters leave idle
   cudaStream_t st2 = nullptr;               // their stream, forked from and joined to st per sub-batch
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -164,6 +168,7 @@ int check_params(const domdec_params* p, int N) {
       p->cell_ti < 0 || p->cell_ti > 1)
     return DOMDEC_EINVAL;
   if (p->balance < 0 || p->balance > 1) return DOMDEC_EINVAL;
+  if (!(p->cell_split >= 0.0) || std::isinf(p->cell_split)) return DOMDEC_EINVAL;
   return DOMDEC_OK;
 }
 
@@ -302,6 +307,22 @@ void prof_collect(domdec_s* h) {
   h->pend.clear();
 }
 
+// Cluster size of the cell launches: C (1, 2, 4, 8; at most the layout's
+// dist_c, and only if such clusters are resident), the grid size, and the
+// helper grid on the SMs the clusters leave idle.
+void set_cluster(domdec_s* h, int C) {
+  int ci = 0;
+  while ((1 << ci) < C && ci < 3) ++ci;
+  C = 1 << ci;
+  if (C > std::max(1, h->S.dist_c) || h->res[ci] < C) {
+    C = 1;
+    ci = 0;
+  }
+  h->crun = C;
+  h->cell_nctas = std::max(C, h->res[ci] / C * C);
+  h->helper_ctas = C > 1 && h->st2 ? std::max(0, h->res[0] - h->cell_nctas) : 0;
+}
+
 // Enqueue one sweep of partition `part`, from its `first`-th non-empty batch on
 // (0: the whole sweep).
 int enqueue_sweep(domdec_s* h, int part, long long slot0, int first = 0) {
@@ -315,7 +336,9 @@ int enqueue_sweep(domdec_s* h, int part, long long slot0, int first = 0) {
   int k = 0;
   // largest-first order of the cells of every sub-batch of this sweep (the
   // member boxes of a sub-batch do not change before its own cell solve)
-  if (launch_cell_order(h->S, part, h->order_mode, h->cell_nctas, h->st) != cudaSuccess) return DOMDEC_ECUDA;
+  if (launch_cell_order(h->S, part, h->crun > 1 ? h->order_mode : 2, h->cell_nctas, h->crun, h->split, h->st) !=
+      cudaSuccess)
+    return DOMDEC_ECUDA;
   int nonempty = 0;
   for (auto& bt : batches) {
     const int begin = bt.first, nbt = bt.second - bt.first;
@@ -326,15 +349,15 @@ int enqueue_sweep(domdec_s* h, int part, long long slot0, int first = 0) {
     cudaEvent_t ev = prof_begin(h);
     const int sub = (int)(&bt - batches.data());
     const int* nbig_p = h->S.nbig + part * 4 + (batches.size() == 4 ? sub : 0);
-    const int C = std::max(1, h->S.dist_c);
+    const int C = h->crun;
     if (launch_cell_solve(h->S, h->d_cells[part], h->S.order[part], nbig_p, begin, nbt, prec, h->cell_smem,
-                          h->cell_nctas, C, h->st) != cudaSuccess)
+                          h->cell_nctas, C, C, h->st) != cudaSuccess)
       return DOMDEC_ECUDA;
     if (h->helper_ctas > 0) {
       // single CTAs on the SMs left idle by the clusters, same phase-2 queue
       if (cudaEventRecord(h->ev_fork, h->st) != cudaSuccess || cudaStreamWaitEvent(h->st2, h->ev_fork, 0) != cudaSuccess ||
           launch_cell_solve(h->S, h->d_cells[part], h->S.order[part], nbig_p, begin, nbt, prec, h->cell_smem,
-                            h->helper_ctas, 1, h->st2) != cudaSuccess ||
+                            h->helper_ctas, C, 1, h->st2) != cudaSuccess ||
           cudaEventRecord(h->ev_join, h->st2) != cudaSuccess || cudaStreamWaitEvent(h->st, h->ev_join, 0) != cudaSuccess)
         return DOMDEC_ECUDA;
     }
@@ -579,19 +602,20 @@ int domdec_init(domdec_t* out, const double* mu, const double* nu, int N, const 
       h->order_mode = 2;
       nctas = cell_resident_ctas(smem, 1, pin->precision);
     }
+    (void)nctas;
     h->cell_smem = smem;
-    h->cell_nctas = std::max(1, nctas);
-    if (S.dist_c > 1) {
-      const int single = cell_resident_ctas(smem, 1, pin->precision);
-      h->helper_ctas = std::max(0, single - h->cell_nctas);
-    }
-    if (h->helper_ctas > 0 &&
+    for (int k = 0, c = 1; k < 4; ++k, c *= 2)
+      h->res[k] = c <= std::max(1, S.dist_c) ? cell_resident_ctas(smem, c, pin->precision) : 0;
+    h->split = pin->cell_split > 0.0 ? pin->cell_split : 2.0;
+    set_cluster(h, S.dist_c);
+    if (S.dist_c > 1 &&
         (cudaStreamCreateWithFlags(&h->st2, cudaStreamNonBlocking) != cudaSuccess ||
          cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
          cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess)) {
       cudaGetLastError();
-      h->helper_ctas = 0;
+      h->st2 = nullptr;
     }
+    set_cluster(h, S.dist_c);
   }
   std::vector<CellDesc> cells[2];
   for (int w = 0; w < 2; ++w) {
@@ -692,6 +716,48 @@ int domdec_iterate(domdec_t h, int n_sweeps) {
     h->slot += batches_per_sweep(h, part);
     ++h->sweeps;
   }
+  return DOMDEC_OK;
+}
+
+int domdec_autotune(domdec_t h, int* cluster_ctas, double* split_factor) {
+  if (!h) return DOMDEC_EINVAL;
+  if (h->sticky) return DOMDEC_ESTATE;
+  struct Cand { int C; double f; };
+  std::vector<Cand> cands = {{1, 2.0}};
+  for (int k = 1, c = 2; k < 4; ++k, c *= 2) {
+    if (c > h->S.dist_c || h->res[k] < c) continue;
+    for (double f : {0.5, 1.0, 2.0}) cands.push_back({c, f});
+  }
+  double best = -1.0;
+  Cand pick = {h->crun, h->split};
+  cudaEvent_t e0 = take_event(h), e1 = take_event(h);
+  for (const Cand& c : cands) {
+    int rc = domdec_sync(h);
+    if (rc < 0) return rc;
+    unsigned long long it0 = 0, it1 = 0;
+    if (cudaMemcpy(&it0, h->S.counters, sizeof(it0), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(h, DOMDEC_ECUDA);
+    set_cluster(h, c.C);
+    h->split = c.f;
+    cudaEventRecord(e0, h->st);
+    rc = domdec_iterate(h, 1);
+    cudaEventRecord(e1, h->st);
+    if (rc) return rc;
+    rc = domdec_sync(h);
+    if (rc < 0) return rc;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (cudaMemcpy(&it1, h->S.counters, sizeof(it1), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(h, DOMDEC_ECUDA);
+    const double rate = ms > 0.f ? (double)(it1 - it0) / ms : 0.0;
+    if (h->crun == c.C && rate > best) { best = rate; pick = c; }
+  }
+  h->pool.push_back(e0);
+  h->pool.push_back(e1);
+  set_cluster(h, pick.C);
+  h->split = pick.f;
+  if (cluster_ctas) *cluster_ctas = h->crun;
+  if (split_factor) *split_factor = h->split;
   return DOMDEC_OK;
 }
 

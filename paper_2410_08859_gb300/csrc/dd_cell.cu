@@ -875,7 +875,9 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
 }
 
 // ---------------------------------------------------------------------------
-// One cell solved by a cluster of C = S.dist_c CTAs, split by rows of its Y box.
+// One cell solved by a cluster of C <= S.dist_c CTAs (the layout's capacities
+// were sized for S.dist_c, a smaller C only leaves more room), split by rows
+// of its Y box.
 // CTA r owns rows [kb, ke) of B_J: the Y-side arrays (log rho, log nu, Z, beta,
 // beta + log nu) of those rows live in its shared memory only, so a cluster
 // holds C times the Y points of one CTA and the largest cells of a sub-batch
@@ -895,10 +897,9 @@ constexpr int kDistMaxC = 8;
 
 template <typename R>
 __device__ __forceinline__ void cell_solve_dist(const DevState& S, const CellDesc cd, int cidx, int nbatch,
-                                                int crank, unsigned char* smem_raw) {
+                                                int crank, int C, unsigned char* smem_raw) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
-  const int C = S.dist_c;
   double* red = reinterpret_cast<double*>(smem_raw);   // 32 * 16 doubles (block reductions)
   __shared__ BoxRec dbox[4];
   __shared__ int dgeo[8];
@@ -1375,26 +1376,27 @@ __device__ __forceinline__ void cell_solve_dist(const DevState& S, const CellDes
 }
 
 // One sub-batch, persistent grid over the resident CTAs in clusters of
-// C = S.dist_c.  Phase 1 (C > 1): each cluster takes the next of the first
+// C = crun.  Phase 1 (C > 1): each cluster takes the next of the first
 // nbig cells of `order` (the largest) and solves it with all its CTAs
 // (cell_solve_dist).  Phase 2: every CTA takes the remaining cells one at a
 // time (cell_solve_body on one CTA).  The order (largest estimated work first
 // within each phase, k_cell_order) only decides when a cell starts; the
 // results do not depend on it.
-// `cluster`: the cluster size of this launch -- S.dist_c for the main grid, 1
-// for a helper grid that runs phase 2 only on the SMs the clusters leave idle
-// (both take phase-2 cells from the same queue).
+// `crun`: the cluster size of the sub-batch's main grid (<= S.dist_c; k_cell_order
+// classified the cells for it); `cluster`: this launch's -- crun for the main
+// grid, 1 for a helper grid that runs phase 2 only on the SMs the clusters
+// leave idle (both take phase-2 cells from the same queue).
 template <typename R>
 __global__ void __launch_bounds__(kCellThreads, 1)
 k_cell_solve(DevState S, const CellDesc* __restrict__ cells, const int* __restrict__ order,
-             const int* __restrict__ nbig_p, int begin, int nbatch, int cluster) {
+             const int* __restrict__ nbig_p, int begin, int nbatch, int crun, int cluster) {
   namespace cg = cooperative_groups;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int sj;
   if (*(volatile int*)S.status & ST_ARENA) return;   // halted until the host grows the arena
-  const int C = S.dist_c;
-  const int nbig = (C > 1 && order) ? *nbig_p : 0;
-  if (C > 1 && cluster > 1) {
+  const int C = cluster;
+  const int nbig = (crun > 1 && order) ? *nbig_p : 0;
+  if (C > 1) {
     const int crank = (int)cg::this_cluster().block_rank();
     // every CTA of the cluster must have started before one writes another's shared memory
     cg::this_cluster().sync();
@@ -1407,7 +1409,7 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, const int* __restri
       const int j = sj;
       if (j >= nbig) break;
       const int cidx = order[begin + j];
-      cell_solve_dist<R>(S, cells[begin + cidx], cidx, nbatch, crank, smem_raw);
+      cell_solve_dist<R>(S, cells[begin + cidx], cidx, nbatch, crank, C, smem_raw);
       cg::this_cluster().sync();
     }
   }
@@ -1451,13 +1453,15 @@ constexpr int kOrderMax = 4096;   // largest batch sorted (larger ones keep thei
 
 // Order of the cells of each sub-batch of partition `part` (block b:
 // sub-batch b; one block for the whole partition when not staggered) and the
-// number of leading cells that a whole cluster solves.  mode 0: a cell goes
-// to a cluster if it fits the cluster layout and either does not fit one CTA
-// or its work exceeds twice the mean work per CTA (`slots` CTAs); mode 1:
+// number of leading cells that a whole cluster of C CTAs solves.  mode 0: a
+// cell goes to a cluster if it fits the cluster layout and either does not fit
+// one CTA or its work exceeds `factor` times the mean work per CTA (`slots`
+// CTAs); mode 1:
 // every cell that fits the cluster layout; mode 2: none.  Within each group
 // the cells are sorted by decreasing work (bitonic sort of (group, cost,
 // index) keys in shared memory; ties keep the index order).
-__global__ void __launch_bounds__(1024) k_cell_order(DevState S, int part, int mode, int slots) {
+__global__ void __launch_bounds__(1024) k_cell_order(DevState S, int part, int mode, int slots, int C,
+                                                     double factor) {
   __shared__ unsigned long long key[kOrderMax];
   __shared__ double red[33];
   const int b = blockIdx.x;
@@ -1478,21 +1482,21 @@ __global__ void __launch_bounds__(1024) k_cell_order(DevState S, int part, int m
     return;
   }
   const CellDesc* cells = S.cells[part];
-  const int C = S.dist_c;
   double tot[1] = {0.0};
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     int H, W;
     tot[0] += (double)cell_cost(S, cells[begin + i], &H, &W);
   }
   block_sum<1>(tot, red);
-  const double thr = 2.0 * tot[0] / (double)max(1, slots);
+  const double thr = factor * tot[0] / (double)max(1, slots);
   for (int i = threadIdx.x; i < P; i += blockDim.x) {
     unsigned long long k = 0ull;
     if (i < n) {
       int H, W;
       const unsigned int cost = cell_cost(S, cells[begin + i], &H, &W);
       const int hl = C > 0 ? (H + C - 1) / C : H;
-      const bool fits_dist = C > 1 && H >= C && W <= S.dist_cap_w && hl <= S.dist_cap_hl && hl * W <= S.dist_cap_nyl;
+      const bool fits_dist = C > 1 && C <= S.dist_c && H >= C && W <= S.dist_cap_w && hl <= S.dist_cap_hl &&
+                             hl * W <= S.dist_cap_nyl;
       const bool fits_one = H <= S.cap_side && W <= S.cap_side && H * W <= S.cap_ny;
       const bool big = mode != 2 && fits_dist && (mode == 1 || !fits_one || (double)cost > thr);
       k = ((unsigned long long)big << 62) | ((unsigned long long)cost << 30) | (0x3fffffffu - (unsigned)i);
@@ -1523,8 +1527,9 @@ __global__ void __launch_bounds__(1024) k_cell_order(DevState S, int part, int m
   if (threadIdx.x == 0) *nbig = (int)cv[0];
 }
 
-cudaError_t launch_cell_order(const DevState& S, int part, int mode, int slots, cudaStream_t st) {
-  k_cell_order<<<S.staggered ? 4 : 1, 1024, 0, st>>>(S, part, mode, slots);
+cudaError_t launch_cell_order(const DevState& S, int part, int mode, int slots, int C, double factor,
+                              cudaStream_t st) {
+  k_cell_order<<<S.staggered ? 4 : 1, 1024, 0, st>>>(S, part, mode, slots, C, factor);
   return cudaGetLastError();
 }
 
@@ -1547,9 +1552,6 @@ k_cell_solve_multi(const DevState* __restrict__ states, const CellRef* __restric
     const int* src = reinterpret_cast<const int*>(states + inst);
     int* dst = reinterpret_cast<int*>(&sS);
     for (int w = threadIdx.x; w < (int)(sizeof(DevState) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
-    __syncthreads();
-    if (threadIdx.x == 0) sS.dist_c = C;
-    __syncthreads();
   };
   const int nbig = C > 1 ? *nbig_p : 0;
   if (C > 1) {
@@ -1567,7 +1569,7 @@ k_cell_solve_multi(const DevState* __restrict__ states, const CellRef* __restric
       const CellRef rf = refs[order[j]];
       load_state(rf.inst);
       if (!(*(volatile int*)sS.status & ST_ARENA))   // the same value in every CTA of the cluster
-        cell_solve_dist<R>(sS, sS.cells[part][rf.cell], rf.pos, rf.nbatch, crank, smem_raw);
+        cell_solve_dist<R>(sS, sS.cells[part][rf.cell], rf.pos, rf.nbatch, crank, C, smem_raw);
       cg::this_cluster().sync();
     }
   }
@@ -1723,11 +1725,11 @@ int cell_resident_ctas(size_t smem, int C, int precision) {
   return n * C;
 }
 
-// One sub-batch: `nctas` persistent CTAs (a multiple of S.dist_c, at most the
-// resident ones) in clusters of S.dist_c, `smem` dynamic bytes; cluster = 1
-// launches single CTAs that run phase 2 only.
+// One sub-batch: `nctas` persistent CTAs (a multiple of `cluster`, at most the
+// resident ones) in clusters of `cluster` (the main grid: crun), `smem` dynamic
+// bytes; cluster = 1 with crun > 1 launches single CTAs that run phase 2 only.
 cudaError_t launch_cell_solve(const DevState& S, const CellDesc* cells, const int* order, const int* nbig_p,
-                              int begin, int nbatch, int precision, size_t smem, int nctas, int cluster,
+                              int begin, int nbatch, int precision, size_t smem, int nctas, int crun, int cluster,
                               cudaStream_t st) {
   const int C = std::max(1, cluster);
   cudaLaunchConfig_t cfg = {};
@@ -1744,10 +1746,10 @@ cudaError_t launch_cell_solve(const DevState& S, const CellDesc* cells, const in
   cfg.numAttrs = C > 1 ? 1 : 0;
   if (precision) {
     cudaFuncSetAttribute(k_cell_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    return cudaLaunchKernelEx(&cfg, k_cell_solve<double>, S, cells, order, nbig_p, begin, nbatch, C);
+    return cudaLaunchKernelEx(&cfg, k_cell_solve<double>, S, cells, order, nbig_p, begin, nbatch, crun, C);
   }
   cudaFuncSetAttribute(k_cell_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  return cudaLaunchKernelEx(&cfg, k_cell_solve<float>, S, cells, order, nbig_p, begin, nbatch, C);
+  return cudaLaunchKernelEx(&cfg, k_cell_solve<float>, S, cells, order, nbig_p, begin, nbatch, crun, C);
 }
 
 // One many-instance launch: order the references (k_ref_order), then `nctas`

@@ -148,10 +148,11 @@ template <typename R> __device__ __forceinline__ R dd_psi(R d) {
 }
 
 // Natural logarithm of a positive finite double by Tang's table-driven method
-// (ACM TOMS 16, 1990): x = 2^e m with m in [1, 2); c_j = 1 + j/128 is the
-// nearest to m (j = 128 moves to e + 1 with c = 1); f = m - c_j is exact;
-// r = f / c_j as f times the rounded reciprocal (|r| <= 2^-8); log1p(r) by its
-// Taylor polynomial up to r^7 (remainder below 2^-59 relative);
+// (ACM TOMS 16, 1990): x = 2^e m with m in [0.75, 1.5) (so e = 0 on all of
+// [0.75, 1.5) and no cancellation between e log 2 and log c near x = 1);
+// c_j = 1 + j/128 is the nearest to m (j = -32..64); f = m - c_j is exact;
+// r = f / c_j as f times the rounded reciprocal (|r| <= 2^-7.6); log1p(r) by
+// its Taylor polynomial up to r^7 (remainder below 2^-56 relative);
 // log x = e log 2 + log c_j + log1p(r).  About 12 FP64 operations against the
 // library logarithm's longer sequence; the GPU test compares it with CUDA's
 // log (a few ulp).  The tables are generated by gen_log_table.py.
@@ -166,23 +167,21 @@ __device__ __forceinline__ double dd_log(double x) {
     e = -54;
   }
   e += (hi >> 20) - 1023;
-  const int mant = hi & 0x000fffff;
-  int j = ((mant >> 12) + 1) >> 1;   // the leading 7 fraction bits, rounded: 0..128
-  double m = __hiloint2double(mant | 0x3ff00000, lo);
-  if (j == 128) {
-    e += 1;
+  double m = __hiloint2double((hi & 0x000fffff) | 0x3ff00000, lo);   // [1, 2)
+  if (m >= 1.5) {
     m *= 0.5;
-    j = 0;
+    e += 1;
   }
+  const int j = __double2int_rn((m - 1.0) * 128.0);   // -32..64; m - 1 is exact
   const double f = m - (1.0 + j * 0.0078125);
-  const double r = f * kInvC[j];
+  const double r = f * kInvC[j + 32];
   double p = fma(r, 1.0 / 7.0, -1.0 / 6.0);
   p = fma(p, r, 0.2);
   p = fma(p, r, -0.25);
   p = fma(p, r, 1.0 / 3.0);
   p = fma(p, r, -0.5);
   const double l1p = fma(p, r * r, r);
-  return fma((double)e, 0.6931471805599453, kLogC[j] + l1p);
+  return fma((double)e, 0.6931471805599453, kLogC[j + 32] + l1p);
 }
 
 // mu phi(p/mu) with phi(s) = s log s - s + 1 (phi(0) = 1), in double.

@@ -40,7 +40,8 @@ class domdec_params(ctypes.Structure):
                 ("box_margin", ctypes.c_int), ("max_ny", ctypes.c_int),
                 ("arena_factor", ctypes.c_double), ("eps_init", ctypes.c_double),
                 ("profile", ctypes.c_int), ("spill_slots", ctypes.c_int),
-                ("cell_ctas", ctypes.c_int), ("cell_ti", ctypes.c_int), ("balance", ctypes.c_int)]
+                ("cell_ctas", ctypes.c_int), ("cell_ti", ctypes.c_int), ("balance", ctypes.c_int),
+                ("cell_split", ctypes.c_double)]
 
 
 class domdec_stats(ctypes.Structure):
@@ -66,6 +67,7 @@ _SIGS = {
     "domdec_default_params": (None, [ctypes.POINTER(domdec_params)]),
     "domdec_init": (_I, [ctypes.POINTER(_P), _P, _P, _I, ctypes.POINTER(domdec_params), _P, _P, _P]),
     "domdec_iterate": (_I, [_P, _I]),
+    "domdec_autotune": (_I, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
     "domdec_reset": (_I, [_P, _P, _P, _P, _P, _D]),
     "domdec_set_eps": (_I, [_P, _D]),
     "domdec_set_tolerance": (_I, [_P, _D]),
@@ -413,6 +415,14 @@ class DomDec:
     def iterate(self, n=1):
         domdec_iterate(self.h, n)
         return self
+
+    def autotune(self):
+        """Time the cell-launch candidates (cluster size, split threshold) for one
+        sweep each and keep the fastest; returns (cluster CTAs, split factor)."""
+        c = ctypes.c_int(0)
+        f = ctypes.c_double(0.0)
+        _check(lib().domdec_autotune(self.h, ctypes.byref(c), ctypes.byref(f)), "domdec_autotune")
+        return c.value, f.value
 
     def reset(self, mu, nu, alpha0=None, beta0=None, eps_init=0.0):
         """Load a new problem of the same size into this handle (domdec_reset)."""
