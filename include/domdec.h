@@ -131,6 +131,8 @@ typedef struct {
   long long arena_regrows;   /* arena growths after a sub-batch's new boxes did not fit (see arena_factor) */
   int       max_cell_iters;  /* largest iteration count of one cell solve */
   int       max_ny;          /* largest cell Y-box seen */
+  long long cluster_regroups;  /* sweeps rerun with the largest cluster size after a cell fit neither one CTA
+                                  nor the cluster size in use (see domdec_autotune) */
 } domdec_stats;
 
 /* Fill *p with the defaults (eps = lambda = 1, s = 4, err = 2e-5,
@@ -174,6 +176,18 @@ int domdec_reset(domdec_t h, const double* mu, const double* nu, const double* a
  * sweeps (they continue the alternation).  *cluster_ctas and *split_factor (if
  * not NULL) receive the choice.  Synchronises. */
 int domdec_autotune(domdec_t h, int* cluster_ctas, double* split_factor);
+
+/* Set the cell kernel's launch shape directly (for example the choice that
+ * domdec_autotune made on another handle of the same workload):
+ * cluster_ctas in {1, 2, 4, 8}, reduced to 1 when it exceeds the handle's
+ * cluster layout or the clusters that fit the GPU; split_factor > 0 (the
+ * cell_split threshold).  A sweep that meets a cell fitting neither one CTA
+ * nor a cluster of this size halts before its cell solves, and the next
+ * synchronisation reruns it with the layout's largest cluster size (counted
+ * in domdec_stats.cluster_regroups); that size stays in use.  *effective_ctas
+ * (if not NULL) receives the cluster size in use.  DOMDEC_EINVAL for other
+ * values.  Enqueues nothing. */
+int domdec_set_launch(domdec_t h, int cluster_ctas, double split_factor, int* effective_ctas);
 
 /* Run n_sweeps partition sweeps (A, B, A, ... continuing the alternation of
  * earlier calls).  Enqueues only; errors found on the device are reported by

@@ -88,6 +88,7 @@ struct domdec_s {
   long long slot = 0;
   unsigned long long maxit_seen = 0;  // maxit-cell counter at the previous domdec_sync
   long long arena_regrows = 0;        // arena growths after a halted sub-batch
+  long long regroups = 0;             // switches to the largest cluster after a halted sweep
   int sticky = 0;
   int last_batch = 0;
   double eps0 = 0.0, err0 = 0.0;           // eps and err given at domdec_init (restored by domdec_reset)
@@ -174,7 +175,8 @@ int check_params(const domdec_params* p, int N) {
 
 int enqueue_sweep(domdec_s* h, int part, long long slot0, int first);
 int batches_per_sweep(domdec_s* h, int part);
-int recover_arena(domdec_s* h);
+int recover_halt(domdec_s* h, int st);
+void set_cluster(domdec_s* h, int C);
 
 int read_status(domdec_s* h) {
   // slot 63 of the pinned buffer is reserved for the status word
@@ -185,10 +187,12 @@ int read_status(domdec_s* h) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
     if (e != cudaSuccess) return fail(h, DOMDEC_ECUDA);
     st = *hs;
-    if (st != ST_ARENA) break;
-    // a sub-batch's new boxes did not fit: grow the arena and rerun what did not run
-    if (attempt >= 4) return fail(h, DOMDEC_EARENA);
-    const int rc = recover_arena(h);
+    if (st != ST_ARENA && st != ST_REGROUP) break;
+    // halted sweeps: a sub-batch's new boxes did not fit (grow the arena) or a
+    // cell needs a larger cluster (switch to the layout's largest); then rerun
+    // what did not run
+    if (attempt >= 4) return fail(h, st == ST_ARENA ? DOMDEC_EARENA : DOMDEC_ETOOBIG);
+    const int rc = recover_halt(h, st);
     if (rc) return fail(h, rc);
   }
   if (st & ST_BADINPUT) return fail(h, DOMDEC_EINVAL);
@@ -222,30 +226,37 @@ int ensure_arena(domdec_s* h) {
   return DOMDEC_OK;
 }
 
-// Grow the arena of a handle halted by the reservation of k_decide (the state
-// is that after the last completed sub-batch), clear the halt and enqueue the
-// sub-batches that were skipped: the device's decision count says how many of
+// Resume a handle whose enqueued sweeps halted (the state is that after the
+// last completed sub-batch): ST_ARENA (the reservation of k_decide) grows the
+// arena, ST_REGROUP (k_cell_order) switches the cell launches to the layout's
+// largest cluster size; then the halt is cleared and the sub-batches that did
+// not run are enqueued again -- the device's decision count says how many of
 // the enqueued sub-batches completed.
-int recover_arena(domdec_s* h) {
+int recover_halt(domdec_s* h, int st) {
   unsigned long long done = 0, live = 0;
   cudaError_t e = cudaMemcpyAsync(&done, h->S.slotctr, sizeof(done), cudaMemcpyDeviceToHost, h->st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&live, h->S.head, sizeof(live), cudaMemcpyDeviceToHost, h->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
   if (e != cudaSuccess) return DOMDEC_ECUDA;
-  const long long ncap = std::max(2 * h->S.cap, 4 * (long long)live + 1024);
-  double *a0 = nullptr, *a1 = nullptr;
-  if (cudaMalloc(&a0, ncap * sizeof(double)) != cudaSuccess) return DOMDEC_ENOMEM;
-  if (cudaMalloc(&a1, ncap * sizeof(double)) != cudaSuccess) { cudaFree(a0); return DOMDEC_ENOMEM; }
-  if (launch_regrow(h->S, a0, a1, h->d_newoff, h->st) != cudaSuccess) return DOMDEC_ECUDA;
-  if (cudaStreamSynchronize(h->st) != cudaSuccess) return DOMDEC_ECUDA;
-  for (auto& q : h->allocs)
-    if (q == h->S.arena[0] || q == h->S.arena[1]) { cudaFree(q); q = nullptr; }
-  h->allocs.push_back(a0);
-  h->allocs.push_back(a1);
-  h->S.arena[0] = a0;
-  h->S.arena[1] = a1;
-  h->S.cap = ncap;
-  ++h->arena_regrows;
+  if (st == ST_REGROUP) {
+    set_cluster(h, h->S.dist_c);
+    ++h->regroups;
+  } else {
+    const long long ncap = std::max(2 * h->S.cap, 4 * (long long)live + 1024);
+    double *a0 = nullptr, *a1 = nullptr;
+    if (cudaMalloc(&a0, ncap * sizeof(double)) != cudaSuccess) return DOMDEC_ENOMEM;
+    if (cudaMalloc(&a1, ncap * sizeof(double)) != cudaSuccess) { cudaFree(a0); return DOMDEC_ENOMEM; }
+    if (launch_regrow(h->S, a0, a1, h->d_newoff, h->st) != cudaSuccess) return DOMDEC_ECUDA;
+    if (cudaStreamSynchronize(h->st) != cudaSuccess) return DOMDEC_ECUDA;
+    for (auto& q : h->allocs)
+      if (q == h->S.arena[0] || q == h->S.arena[1]) { cudaFree(q); q = nullptr; }
+    h->allocs.push_back(a0);
+    h->allocs.push_back(a1);
+    h->S.arena[0] = a0;
+    h->S.arena[1] = a1;
+    h->S.cap = ncap;
+    ++h->arena_regrows;
+  }
   if (cudaMemsetAsync(h->S.status, 0, sizeof(int), h->st) != cudaSuccess) return DOMDEC_ECUDA;
   // the enqueued sweeps, oldest first: find the first sub-batch that did not run
   long long cum = 0;
@@ -641,7 +652,7 @@ int domdec_init(domdec_t* out, const double* mu, const double* nu, int N, const 
   } while (0)
   double *dmu, *dnu, *dlogmu, *dlognu, *dmuinu;
   DD_ALLOC(dmu, n); DD_ALLOC(dnu, n); DD_ALLOC(dlogmu, n); DD_ALLOC(dlognu, n);
-  DD_ALLOC(S.alpha, n); DD_ALLOC(S.PX, n); DD_ALLOC(S.PY, n); DD_ALLOC(S.PXnew, n); DD_ALLOC(S.dPY, n);
+  DD_ALLOC(S.alpha, n); DD_ALLOC(S.PX, n); DD_ALLOC(S.PY, n); DD_ALLOC(S.PXnew, n); DD_ALLOC(S.dPY, n); DD_ALLOC(S.alphanew, n);
   DD_ALLOC(S.Cc, h->nbasic); DD_ALLOC(S.Hh, h->nbasic); DD_ALLOC(dmuinu, h->nbasic);
   DD_ALLOC(h->d_mumass, h->nbasic);
   DD_ALLOC(S.box, h->nbasic);
@@ -758,6 +769,18 @@ int domdec_autotune(domdec_t h, int* cluster_ctas, double* split_factor) {
   h->split = pick.f;
   if (cluster_ctas) *cluster_ctas = h->crun;
   if (split_factor) *split_factor = h->split;
+  return DOMDEC_OK;
+}
+
+int domdec_set_launch(domdec_t h, int cluster_ctas, double split_factor, int* effective_ctas) {
+  if (!h) return DOMDEC_EINVAL;
+  if (h->sticky) return DOMDEC_ESTATE;
+  if ((cluster_ctas != 1 && cluster_ctas != 2 && cluster_ctas != 4 && cluster_ctas != 8) ||
+      !(split_factor > 0.0) || std::isinf(split_factor))
+    return DOMDEC_EINVAL;
+  set_cluster(h, cluster_ctas);
+  h->split = split_factor;
+  if (effective_ctas) *effective_ctas = h->crun;
   return DOMDEC_OK;
 }
 
@@ -980,6 +1003,7 @@ int domdec_get_stats(domdec_t h, domdec_stats* s) {
   s->lse_terms = (long long)c[7];
   s->box_points = (long long)c[8];
   s->arena_regrows = h->arena_regrows;
+  s->cluster_regroups = h->regroups;
   s->max_cell_iters = (int)c[5];
   s->max_ny = (int)c[6];
   s->box_entries = (long long)h->h_pinned[4];

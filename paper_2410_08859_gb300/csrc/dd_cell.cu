@@ -588,7 +588,7 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
       int x = (cd.i0 + r) * N + cd.j0 + c;
       int xi1 = cd.i0 + r - xc1, xi2 = cd.j0 + c - xc2;
       double a = (double)av_c[t];
-      S.alpha[x] = eps * (A + a + 2.0 * q * (double)(D1 * xi1 + D2 * xi2));
+      S.alphanew[x] = eps * (A + a + 2.0 * q * (double)(D1 * xi1 + D2 * xi2));
       if (bal) {
         // av_n holds the X-half of the final beta (computed before the loop stopped)
         const int qd = 2 * (r >= s) + (c >= s);
@@ -861,15 +861,7 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
       o.mass[q4] = hsd[8 + q4];
       o.Ht[q4] = bi >= 0 ? hsd[q4] - hsd[8 + q4] + S.muinu[bi] : 0.0;
     }
-    *out = o;
-    atomicAdd(S.counters + 0, (unsigned long long)it);
-    atomicAdd(S.counters + 1, 1ull);
-    if (o.status == CELL_MAXIT) atomicAdd(S.counters + 2, 1ull);
-    atomicMax(S.counters + 5, (unsigned long long)it);
-    atomicMax(S.counters + 6, (unsigned long long)ny);
-    atomicAdd(S.counters + 8, (unsigned long long)ny);
-    atomicAdd(S.counters + 7, (unsigned long long)it *
-                                  (unsigned long long)(nx1 * W * nx2 + H * W * nx1 + H * nx2 * W + nx * H));
+    *out = o;   // the decision kernel adds the sub-batch's counters
     if (nonfinite) atomicOr(S.status, ST_NONFINITE);
   }
 }
@@ -1232,7 +1224,7 @@ __device__ __forceinline__ void cell_solve_dist(const DevState& S, const CellDes
       const int r = t / nx2, c = t - r * nx2;
       const int x = (cd.i0 + r) * N + cd.j0 + c;
       const int xi1 = cd.i0 + r - xc1, xi2 = cd.j0 + c - xc2;
-      S.alpha[x] = eps * (A + (double)av_c[t] + 2.0 * q * (double)(D1 * xi1 + D2 * xi2));
+      S.alphanew[x] = eps * (A + (double)av_c[t] + 2.0 * q * (double)(D1 * xi1 + D2 * xi2));
       const double p1 = (double)dd_ex2((lm[t] + av_c[t]) * L2E + Wv[t]);
       S.PXnew[x] = p1;
       const double p0 = S.PX[x];
@@ -1363,15 +1355,7 @@ __device__ __forceinline__ void cell_solve_dist(const DevState& S, const CellDes
     o.mass[q4] = hsd[8 + q4];
     o.Ht[q4] = bi >= 0 ? hsd[q4] - hsd[8 + q4] + S.muinu[bi] : 0.0;
   }
-  *out = o;
-  atomicAdd(S.counters + 0, (unsigned long long)it);
-  atomicAdd(S.counters + 1, 1ull);
-  if (o.status == CELL_MAXIT) atomicAdd(S.counters + 2, 1ull);
-  atomicMax(S.counters + 5, (unsigned long long)it);
-  atomicMax(S.counters + 6, (unsigned long long)(H * W));
-  atomicAdd(S.counters + 8, (unsigned long long)(H * W));
-  atomicAdd(S.counters + 7, (unsigned long long)it *
-                                (unsigned long long)(nx1 * W * nx2 + H * W * nx1 + H * nx2 * W + nx * H));
+  *out = o;   // the decision kernel adds the sub-batch's counters
   if (nonfinite) atomicOr(S.status, ST_NONFINITE);
 }
 
@@ -1393,7 +1377,11 @@ k_cell_solve(DevState S, const CellDesc* __restrict__ cells, const int* __restri
   namespace cg = cooperative_groups;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int sj;
-  if (*(volatile int*)S.status & ST_ARENA) return;   // halted until the host grows the arena
+  if (*(volatile int*)S.status & ST_HALT) {   // halted until the host reruns the sub-batch
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nbatch; j += gridDim.x * blockDim.x)
+      S.cout[j].status = CELL_SKIPPED;
+    return;
+  }
   const int C = cluster;
   const int nbig = (crun > 1 && order) ? *nbig_p : 0;
   if (C > 1) {
@@ -1449,6 +1437,14 @@ __device__ __forceinline__ unsigned int cell_cost(const DevState& S, const CellD
   return (unsigned int)min(c + 1, 0x7fffffffLL);
 }
 
+// Whether a cell with Y box H x W fits a cluster of the layout's largest size
+// (S.dist_c CTAs, each holding a block of ceil(H / dist_c) rows).
+__device__ __forceinline__ bool fits_layout(const DevState& S, int H, int W) {
+  if (S.dist_c < 2) return false;
+  const int hl = (H + S.dist_c - 1) / S.dist_c;
+  return H >= S.dist_c && W <= S.dist_cap_w && hl <= S.dist_cap_hl && hl * W <= S.dist_cap_nyl;
+}
+
 constexpr int kOrderMax = 4096;   // largest batch sorted (larger ones keep their index order)
 
 // Order of the cells of each sub-batch of partition `part` (block b:
@@ -1470,6 +1466,7 @@ __global__ void __launch_bounds__(1024) k_cell_order(DevState S, int part, int m
   const int n = end - begin;
   int* out = S.order[part] + begin;
   int* nbig = S.nbig + part * 4 + b;
+  if (*(volatile int*)S.status & ST_HALT) return;   // the sweep's cell launches solve nothing
   if (n <= 0) {
     if (threadIdx.x == 0) *nbig = 0;
     return;
@@ -1499,6 +1496,7 @@ __global__ void __launch_bounds__(1024) k_cell_order(DevState S, int part, int m
                              hl * W <= S.dist_cap_nyl;
       const bool fits_one = H <= S.cap_side && W <= S.cap_side && H * W <= S.cap_ny;
       const bool big = mode != 2 && fits_dist && (mode == 1 || !fits_one || (double)cost > thr);
+      if (!fits_one && !big && fits_layout(S, H, W) && (mode == 2 || C < S.dist_c)) atomicOr(S.status, ST_REGROUP);
       k = ((unsigned long long)big << 62) | ((unsigned long long)cost << 30) | (0x3fffffffu - (unsigned)i);
     }
     key[i] = k;
@@ -1552,6 +1550,15 @@ k_cell_solve_multi(const DevState* __restrict__ states, const CellRef* __restric
     const int* src = reinterpret_cast<const int*>(states + inst);
     int* dst = reinterpret_cast<int*>(&sS);
     for (int w = threadIdx.x; w < (int)(sizeof(DevState) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
+    __syncthreads();
+  };
+  // a halted instance (status read once per reference, the same in every CTA
+  // of a cluster) solves nothing: its cell is marked skipped
+  auto halted = [&](const CellRef& rf) {
+    if (!(*(volatile int*)sS.status & ST_HALT)) return false;
+    if (threadIdx.x == 0 && (C == 1 || (int)cg::this_cluster().block_rank() == 0))
+      sS.cout[rf.pos].status = CELL_SKIPPED;
+    return true;
   };
   const int nbig = C > 1 ? *nbig_p : 0;
   if (C > 1) {
@@ -1568,8 +1575,7 @@ k_cell_solve_multi(const DevState* __restrict__ states, const CellRef* __restric
       if (j >= nbig) break;
       const CellRef rf = refs[order[j]];
       load_state(rf.inst);
-      if (!(*(volatile int*)sS.status & ST_ARENA))   // the same value in every CTA of the cluster
-        cell_solve_dist<R>(sS, sS.cells[part][rf.cell], rf.pos, rf.nbatch, crank, C, smem_raw);
+      if (!halted(rf)) cell_solve_dist<R>(sS, sS.cells[part][rf.cell], rf.pos, rf.nbatch, crank, C, smem_raw);
       cg::this_cluster().sync();
     }
   }
@@ -1582,7 +1588,7 @@ k_cell_solve_multi(const DevState* __restrict__ states, const CellRef* __restric
     if (j >= nref) break;
     const CellRef rf = refs[order ? order[j] : j];
     load_state(rf.inst);
-    if (!(*(volatile int*)sS.status & ST_ARENA)) cell_solve_body<R>(sS, sS.cells[part][rf.cell], rf.pos, rf.nbatch, smem_raw);
+    if (!halted(rf)) cell_solve_body<R>(sS, sS.cells[part][rf.cell], rf.pos, rf.nbatch, smem_raw);
   }
 }
 
@@ -1625,6 +1631,7 @@ k_ref_order(const DevState* __restrict__ states, const CellRef* __restrict__ ref
                              hl * W <= S.dist_cap_nyl;
       const bool fits_one = H <= S.cap_side && W <= S.cap_side && H * W <= S.cap_ny;
       const bool big = fits_dist && (!fits_one || (double)cost > thr);
+      if (!fits_one && !big && fits_layout(S, H, W) && C < S.dist_c) atomicOr(S.status, ST_REGROUP);
       k = ((unsigned long long)big << 62) | ((unsigned long long)cost << 30) | (0x3fffffffu - (unsigned)i);
     }
     rkey[i] = k;

@@ -9,14 +9,20 @@
 #define DD_LN2 0.6931471805599453
 
 // ---------------------------------------------------------------- status codes
-// Per-cell status written by the cell kernel.
-enum { CELL_OK = 0, CELL_MAXIT = 1, CELL_EMPTY = 2, CELL_TOOBIG = 3, CELL_NONFINITE = 4 };
-// Bits of the handle's device status word.  ST_ARENA: a sub-batch's new boxes
-// would not fit the arena; the decision kernel set it before any state
-// changed, and every later sweep kernel leaves the state untouched until the
-// host has grown the arena and re-enqueued the sub-batches that did not run.
+// Per-cell status written by the cell kernel (CELL_SKIPPED: the launch found
+// the handle halted and solved nothing).
+enum { CELL_OK = 0, CELL_MAXIT = 1, CELL_EMPTY = 2, CELL_TOOBIG = 3, CELL_NONFINITE = 4, CELL_SKIPPED = 5 };
+// Bits of the handle's device status word.  Two of them halt the enqueued
+// sweeps (ST_HALT): every later sweep kernel leaves the state untouched until
+// the host has handled the cause and re-enqueued the sub-batches that did not
+// run.  ST_ARENA: a sub-batch's new boxes would not fit the arena (set by the
+// decision kernel before any state changed; the host grows the arena).
+// ST_REGROUP: a cell fits neither one CTA nor a cluster of the launch's size
+// but does fit the layout's largest cluster (set by the ordering kernel before
+// the sub-batch's cell solve; the host switches to that cluster size).
 // ST_ARENA_LOST: the allocation guard of the mixing kernel fired (state lost).
-enum { ST_TOOBIG = 1, ST_ARENA = 2, ST_EMPTY = 4, ST_NONFINITE = 8, ST_BADINPUT = 16, ST_ARENA_LOST = 32 };
+enum { ST_TOOBIG = 1, ST_ARENA = 2, ST_EMPTY = 4, ST_NONFINITE = 8, ST_BADINPUT = 16, ST_ARENA_LOST = 32,
+       ST_REGROUP = 64, ST_HALT = ST_ARENA | ST_REGROUP };
 
 // ------------------------------------------------------------------ geometry
 // One composite cell: its X box [i0, i0+nx1) x [j0, j0+nx2) (always a
@@ -63,6 +69,8 @@ struct DevState {
   const double *mu, *nu, *logmu, *lognu;
   double* muinu;                // muinu[i] = |mu_i| |nu|
   double *alpha, *PX, *PY, *PXnew, *dPY;
+  double* alphanew;             // the cell solves' new alpha on X_J, committed by the mixing kernel
+                                // (so a halted sub-batch is solved again from the same alpha)
   double *Cc, *Hh;
   BoxRec* box;
   double* arena[2];

@@ -26,7 +26,9 @@ __device__ __forceinline__ void decide_body(const DevState& S, const CellDesc* _
                                             int nbatch, int bid, int nblk) {
   __shared__ double red[33 * 5];
   __shared__ bool is_last;
-  if (*(volatile int*)S.status & ST_ARENA) return;   // halted until the host grows the arena
+  __shared__ unsigned long long smax[2];   // largest iteration count and Y box of the sub-batch
+  if (*(volatile int*)S.status & ST_HALT) return;   // halted until the host reruns the sub-batch
+  if (threadIdx.x == 0) smax[0] = smax[1] = 0ull;
   const int n = S.N * S.N;
   const double lam = S.lam, eps = S.eps, th_s = 1.0 / nbatch;
   double v[5] = {0, 0, 0, 0, 0};
@@ -65,7 +67,10 @@ __device__ __forceinline__ void decide_body(const DevState& S, const CellDesc* _
   if (!is_last) return;
   __threadfence();
   // last block: fixed-order reduction of the block partials and the per-cell terms
-  double tot[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  // tot[9..13]: the sub-batch's cell-solve counters (iterations, solves, solves
+  // stopped at maxit, exp terms, Y-box points), added to the handle's counters
+  // only when the sub-batch goes ahead (a halted one is solved again later)
+  double tot[14] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   for (int b = threadIdx.x; b < nblk; b += blockDim.x)
     for (int k = 0; k < 5; ++k) tot[k] += ((volatile double*)S.red)[b * 5 + k];
   for (int j = threadIdx.x; j < nbatch; j += blockDim.x) {
@@ -80,9 +85,19 @@ __device__ __forceinline__ void decide_body(const DevState& S, const CellDesc* _
     }
     tot[6] += o.dKX[0];
     tot[7] += o.dKX[1];
+    const double it = (double)o.iters, ny = (double)o.H * o.W;
+    const double nx1 = cd.nx1, nx2 = cd.nx2;
+    tot[9] += it;
+    tot[10] += 1.0;
+    tot[11] += o.status == CELL_MAXIT ? 1.0 : 0.0;
+    // exp terms of one iteration: the two separable passes of each half
+    tot[12] += it * (nx1 * nx2 * o.W + ny * nx1 + nx2 * ny + nx1 * nx2 * o.H);
+    tot[13] += ny;
+    atomicMax(&smax[0], (unsigned long long)o.iters);
+    atomicMax(&smax[1], (unsigned long long)(o.H * o.W));
   }
-  __shared__ double red8[33 * 9];
-  block_sum<9>(tot, red8);
+  __shared__ double red14[33 * 14];
+  block_sum<14>(tot, red14);
   if (threadIdx.x != 0) return;
   // reserve the arena space of the sub-batch's new boxes before anything changes
   if ((double)*S.head + tot[8] > (double)S.cap) {
@@ -92,6 +107,13 @@ __device__ __forceinline__ void decide_body(const DevState& S, const CellDesc* _
     if (S.queue) { S.queue[0] = 0u; S.queue[1] = 0u; }
     return;
   }
+  atomicAdd(S.counters + 0, (unsigned long long)tot[9]);
+  atomicAdd(S.counters + 1, (unsigned long long)tot[10]);
+  atomicAdd(S.counters + 2, (unsigned long long)tot[11]);
+  atomicAdd(S.counters + 7, (unsigned long long)tot[12]);
+  atomicAdd(S.counters + 8, (unsigned long long)tot[13]);
+  atomicMax(S.counters + 5, smax[0]);
+  atomicMax(S.counters + 6, smax[1]);
   const double dL = tot[5], dKX1 = tot[6], dKXs = tot[7];
   const double E0 = tot[4] + lam * tot[0] + lam * tot[1];
   const double dg = dL + lam * dKX1 + lam * tot[2];          // E(1) - E
@@ -168,7 +190,7 @@ constexpr double kLineGtol = 1e-12, kLineXtol = 1e-12, kLinePfloor = 1e-300;
 __global__ void __launch_bounds__(512)
 k_line_eval(DevState S, const CellDesc* __restrict__ cells, int begin, int nbatch, int first, double* partials) {
   __shared__ double red[33 * 4];
-  if (S.line[5] != 0.0 || (*(volatile int*)S.status & ST_ARENA)) return;   // uniform across blocks
+  if (S.line[5] != 0.0 || (*(volatile int*)S.status & ST_HALT)) return;   // uniform across blocks
   const double z = first ? 1.0 : S.line[2], lo = S.line[6];
   double v[4] = {0.0, 0.0, 0.0, 0.0};
   auto term = [&](double p0, double d, double m) {
@@ -202,7 +224,7 @@ k_line_eval(DevState S, const CellDesc* __restrict__ cells, int begin, int nbatc
 
 // One step of the search from the sums of the last evaluation (one thread).
 __global__ void k_line_step(DevState S, int first, int last) {
-  if (threadIdx.x != 0 || S.line[5] != 0.0 || (*(volatile int*)S.status & ST_ARENA)) return;
+  if (threadIdx.x != 0 || S.line[5] != 0.0 || (*(volatile int*)S.status & ST_HALT)) return;
   double* L = S.line;
   const double lam = S.lam;
   const double g = L[7] + lam * L[12], h = lam * L[13], scale = fabs(L[7]) + lam * L[14];
@@ -241,7 +263,7 @@ __device__ __forceinline__ void apply_body(const DevState& S, const CellDesc cd,
   __shared__ long long noff;
   __shared__ int nbox[4];
   const CellOut o = S.cout[pos];
-  if (o.status == CELL_EMPTY || o.status == CELL_TOOBIG) return;
+  if (o.status == CELL_EMPTY || o.status == CELL_TOOBIG || o.status == CELL_SKIPPED) return;
   const int N = S.N, H = o.H, W = o.W, ny = H * W;
   const int tid = threadIdx.x;
   // dP_Y of the sub-batch back to zero on this cell's box (each quadrant CTA a quarter)
@@ -250,7 +272,7 @@ __device__ __forceinline__ void apply_body(const DevState& S, const CellDesc cd,
     S.dPY[(o.k0 + kk) * N + o.l0 + ll] = 0.0;
   }
   const int bi = cd.mem[q];
-  if (bi < 0 || (*(volatile int*)S.status & ST_ARENA)) return;
+  if (bi < 0 || (*(volatile int*)S.status & ST_HALT)) return;
   const double th = *S.theta, thr = S.thr;
   double* arena = S.arena[*S.cur];
   int nst;
@@ -317,7 +339,7 @@ __device__ __forceinline__ void apply_body(const DevState& S, const CellDesc cd,
       arena[noff + u] = v;
     }
   }
-  // P_X on the quadrant's pixels
+  // P_X on the quadrant's pixels, and the cell's new alpha there
   const int s = S.s, hr = q >> 1, hc = q & 1;
   const int rb = hr * s, re = min(cd.nx1, rb + s), cb = hc * s, ce = min(cd.nx2, cb + s);
   const int qw = ce - cb;
@@ -325,6 +347,7 @@ __device__ __forceinline__ void apply_body(const DevState& S, const CellDesc cd,
     int r = rb + t / qw, c = cb + (t - (t / qw) * qw);
     int x = (cd.i0 + r) * N + cd.j0 + c;
     S.PX[x] = (1.0 - th) * S.PX[x] + th * S.PXnew[x];
+    S.alpha[x] = S.alphanew[x];
   }
 }
 

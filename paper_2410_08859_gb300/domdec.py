@@ -51,7 +51,7 @@ class domdec_stats(ctypes.Structure):
                 ("box_entries", ctypes.c_longlong), ("lse_terms", ctypes.c_longlong),
                 ("box_points", ctypes.c_longlong), ("arena_regrows", ctypes.c_longlong),
                 ("max_cell_iters", ctypes.c_int),
-                ("max_ny", ctypes.c_int)]
+                ("max_ny", ctypes.c_int), ("cluster_regroups", ctypes.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -68,6 +68,7 @@ _SIGS = {
     "domdec_init": (_I, [ctypes.POINTER(_P), _P, _P, _I, ctypes.POINTER(domdec_params), _P, _P, _P]),
     "domdec_iterate": (_I, [_P, _I]),
     "domdec_autotune": (_I, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+    "domdec_set_launch": (_I, [_P, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_int)]),
     "domdec_reset": (_I, [_P, _P, _P, _P, _P, _D]),
     "domdec_set_eps": (_I, [_P, _D]),
     "domdec_set_tolerance": (_I, [_P, _D]),
@@ -423,6 +424,13 @@ class DomDec:
         f = ctypes.c_double(0.0)
         _check(lib().domdec_autotune(self.h, ctypes.byref(c), ctypes.byref(f)), "domdec_autotune")
         return c.value, f.value
+
+    def set_launch(self, cluster_ctas, split):
+        """Set the cell launch shape (domdec_set_launch); returns the cluster size in use."""
+        c = ctypes.c_int(0)
+        _check(lib().domdec_set_launch(self.h, int(cluster_ctas), float(split), ctypes.byref(c)),
+               "domdec_set_launch")
+        return c.value
 
     def reset(self, mu, nu, alpha0=None, beta0=None, eps_init=0.0):
         """Load a new problem of the same size into this handle (domdec_reset)."""

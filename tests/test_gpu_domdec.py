@@ -505,10 +505,59 @@ def test_arena_overflow_grows_and_reruns(dd, precision):
     if precision == "fp64":   # FP32 iteration counts may differ by round-off in P_Y's atomic sums
         assert small.stats()["cell_iters"] == ref.stats()["cell_iters"]
     assert small.stats()["sweeps"] == ref.stats()["sweeps"] == 4
-    assert abs(small.score()[0] - ref.score()[0]) <= 1e-12 * abs(ref.score()[0])
+    tol = 1e-12 if precision == "fp64" else 1e-6
+    assert abs(small.score()[0] - ref.score()[0]) <= tol * abs(ref.score()[0])
     small.iterate(2)
     ref.iterate(2)
     assert small.sync() in (0, 1) and ref.sync() in (0, 1)
-    assert abs(small.score()[0] - ref.score()[0]) <= 1e-12 * abs(ref.score()[0])
+    assert abs(small.score()[0] - ref.score()[0]) <= tol * abs(ref.score()[0])
     for g in (ref, small):
         g.close()
+
+
+def test_autotune_keeps_the_iterates(dd):
+    """domdec_autotune times one sweep per candidate launch shape (cluster size,
+    split threshold) and keeps the fastest: in FP64 the cell results do not
+    depend on the launch shape, so the tuned handle follows the untuned one
+    sweep for sweep (same decisions, iteration counts and state)."""
+    mu, nu = inputs.mixture_small(N=64, seed=1050)
+    eps, lam = (2 / 64) ** 2, 1.0
+    g = dd.DomDec(mu, nu, eps, lam, 8, precision="fp64")
+    ref = dd.DomDec(mu, nu, eps, lam, 8, precision="fp64")
+    C, f = g.autotune()
+    assert C in (1, 2, 4, 8) and f in (0.5, 1.0, 2.0)
+    n = g.stats()["sweeps"]
+    assert n >= 1
+    g.iterate(2)
+    ref.iterate(n + 2)
+    assert g.sync() in (0, 1) and ref.sync() in (0, 1)
+    np.testing.assert_array_equal(g.decisions()[:, 3], ref.decisions()[:, 3])
+    assert g.stats()["cell_iters"] == ref.stats()["cell_iters"]
+    assert abs(g.score()[0] - ref.score()[0]) <= 1e-12 * abs(ref.score()[0])
+    PX1, PY1 = g.marginals()
+    PX2, PY2 = ref.marginals()
+    assert np.abs(PY1 - PY2).sum() <= 1e-12 * PY2.sum()
+    for h in (g, ref):
+        h.close()
+
+
+def test_too_small_launch_cluster_regroups(dd):
+    """A launch shape that cannot hold the cells (one CTA per cell while every
+    box exceeds max_ny = 256 and no spill slot exists): the sweep halts before
+    its cell solves, the next synchronisation reruns it with the layout's
+    largest cluster -- the same sweeps as the oracle, no error."""
+    mu, nu = inputs.mixture_small(N=32, seed=1000)
+    geo = odd.Geometry(32, 4)
+    mu, nu = mu.ravel(), nu.ravel()
+    eps = (1 / 32) ** 2
+    st = odd.init_product(geo, mu, nu, eps, 1.0)
+    g = dd.DomDec(mu, nu, eps, 1.0, 4, precision="fp64", max_ny=256, spill_slots=-1)
+    assert g.set_launch(1, 2.0) == 1
+    for k in range(2):
+        odd.sweep(st, "AB"[k], "staggered")
+        g.iterate(1)
+        assert g.sync() in (0, 1)
+        compare_state(g, st, 1e-10, 1e-10, 1e-8, tol_box=1e-8)
+    assert g.stats()["cluster_regroups"] >= 1
+    assert g.stats()["sweeps"] == 2
+    g.close()
