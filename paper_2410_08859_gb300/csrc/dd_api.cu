@@ -663,7 +663,7 @@ int domdec_init(domdec_t* out, const double* mu, const double* nu, int N, const 
   DD_ALLOC(S.nut, (size_t)std::max(1, mb) * 4 * S.cap_nut);
   DD_ALLOC(S.theta, 1); DD_ALLOC(S.declog, 4 * LOGCAP); DD_ALLOC(S.counters, NCOUNT);
   DD_ALLOC(S.slotctr, 1);
-  DD_ALLOC(S.status, 1); DD_ALLOC(S.red, 2 * 152 * 5 + 8); DD_ALLOC(S.red_count, 1);
+  DD_ALLOC(S.status, 1); DD_ALLOC(S.red, kRedBlocks * 5 + 8); DD_ALLOC(S.red_count, 1);
   DD_ALLOC(h->d_newoff, h->nbasic + 1); DD_ALLOC(h->d_scratch, 64);
   DD_ALLOC(h->d_partials, kRedBlocks * 8);
   DD_ALLOC(h->S.line, 16); DD_ALLOC(h->d_numom, 8);

@@ -63,6 +63,55 @@ __device__ __forceinline__ R lse2_1d(F src, int M, R ctr, R q2, R shift, bool us
   return mx + dd_lg2(acc);
 }
 
+// Epilogue statistics of one target over the sources m in [b, e):
+// with v_m = src(m) - q2 (m - ctr)^2 (log2 units) returns L = log2 sum_m 2^{v_m}
+// and the means m1 = <f1>, m2 = <f2> under the weights 2^{v_m - L}, where
+// f1(m, d), f2(m, d) take the source index and d = m - ctr.  With use_shift,
+// `shift` is an upper bound of L (the full-range log-sum-exp of the same
+// terms): one pass of exponentials against it, and only if that sum leaves
+// [1e-30, 1e30] (the sub-range holds a negligible share) the exact pass
+// against the maximum.  Without a shift the maximum is found first.
+template <typename R, typename F, typename G1, typename G2>
+__device__ __forceinline__ R lse_moments(F src, G1 f1, G2 f2, int b, int e, R ctr, R q2, R shift, bool use_shift,
+                                         R& m1, R& m2) {
+  R sh = shift;
+  if (!use_shift) {
+    R mx = -dd_inf<R>();
+    R d = R(b) - ctr;
+    for (int m = b; m < e; ++m, d += R(1)) mx = max(mx, src(m) - q2 * d * d);
+    if (!(mx > -dd_inf<R>())) {
+      m1 = m2 = R(0);
+      return mx;
+    }
+    sh = mx;
+  }
+  for (int pass = 0;; ++pass) {
+    R sw = R(0), sa = R(0), sd = R(0);
+    R d = R(b) - ctr;
+    for (int m = b; m < e; ++m, d += R(1)) {
+      const R w = dd_ex2(src(m) - q2 * d * d - sh);
+      sw += w;
+      sa += w * f1(m, d);
+      sd += w * f2(m, d);
+    }
+    if (!use_shift || pass == 1 || (sw >= R(1e-30) && sw <= R(1e30))) {
+      const R isw = R(1) / sw;
+      m1 = sa * isw;
+      m2 = sd * isw;
+      return sh + dd_lg2(sw);
+    }
+    // the shift was far from L: the exact pass against the maximum
+    R mx = -dd_inf<R>();
+    d = R(b) - ctr;
+    for (int m = b; m < e; ++m, d += R(1)) mx = max(mx, src(m) - q2 * d * d);
+    if (!(mx > -dd_inf<R>())) {
+      m1 = m2 = R(0);
+      return mx;
+    }
+    sh = mx;
+  }
+}
+
 // Partial sum of 2^{src(m) - q2 (m - ctr)^2 - shift} over m = part, part + P, ...
 // (four independent accumulators to keep several ex2 in flight).
 template <typename R, typename F>
@@ -628,30 +677,24 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
     tmp.slot = slot;
     nut = cell_nut(S, tmp, cidx, &nst);
   }
-  R* Te = T;                 // epilogue scratch spans T, U, bl, lrho, Zv
+  R* Te = T;                 // epilogue scratch spans T, U, bl, lrho (and Zv for the widest boxes)
   R* Ma = T + nx1 * W;
   R* Md = Ma + nx1 * W;
+  // Zv (the final Z) serves as the shift of the quadrant sums unless Md reaches it
+  const bool zok = Md + nx1 * W <= Zv;
   for (int hc = 0; hc < nhc; ++hc) {
     const int cb = hc * s, ce = min(nx2, cb + s);
     // rows of X_J against columns of B_J, restricted to the column half hc
     for (int t = gtid; t < nx1 * W; t += gthr) {
       int r = t / W, ll = t - r * W;
       const R* row = xa_c + r * nx2;
-      R ctr = R(ll + offc);
-      R T2 = lse2_1d<R>([&](int m) { return row[cb + m]; }, ce - cb, ctr - R(cb), q2, R(0), false);
-      R sw = 0, sa = 0, sd = 0;
-      for (int c = cb; c < ce; ++c) {
-        R d = R(c) - ctr;
-        R w = dd_ex2(row[c] - q2 * d * d - T2);
-        sw += w;
-        sa += w * (av_c[r * nx2 + c] - qR * d * d);
-        R dt = d + R(D2);
-        sd += w * dt * dt;
-      }
-      R isw = R(1) / sw;
+      R ma, md;
+      const R T2 = lse_moments<R>(
+          [&](int m) { return row[m]; }, [&](int m, R d) { return av_c[r * nx2 + m] - qR * d * d; },
+          [&](int, R d) { return (d + R(D2)) * (d + R(D2)); }, cb, ce, R(ll + offc), q2, R(0), false, ma, md);
       Te[t] = T2;
-      Ma[t] = sa * isw;
-      Md[t] = sd * isw;
+      Ma[t] = ma;
+      Md[t] = md;
     }
     csync();
     for (int u = gtid; u < ny; u += gthr) {
@@ -659,24 +702,21 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
       int y = (k0 + kk) * N + l0 + ll;
       R ctr = R(kk + offr);
       double nuy = S.nu[y];
+      // Z of the last iteration: the log-sum-exp over all rows of the full-row
+      // T, an upper bound of every quadrant's sum at this y
+      const R zsh = zok ? Zv[u] : R(0);
       for (int hr = 0; hr < nhr; ++hr) {
         const int rb = hr * s, re = min(nx1, rb + s);
-        R P2 = lse2_1d<R>([&](int m) { return Te[(rb + m) * W + ll]; }, re - rb, ctr - R(rb), q2, R(0), false);
-        R sw = 0, sa = 0, sd = 0;
-        for (int r = rb; r < re; ++r) {
-          R d = R(r) - ctr;
-          R w = dd_ex2(Te[r * W + ll] - q2 * d * d - P2);
-          sw += w;
-          sa += w * (Ma[r * W + ll] - qR * d * d);
-          R dt = d + R(D1);
-          sd += w * (dt * dt + Md[r * W + ll]);
-        }
-        R isw = R(1) / sw;
+        R ma, md;
+        const R P2 = lse_moments<R>(
+            [&](int m) { return Te[m * W + ll]; }, [&](int m, R d) { return Ma[m * W + ll] - qR * d * d; },
+            [&](int m, R d) { return (d + R(D1)) * (d + R(D1)) + Md[m * W + ll]; }, rb, re, ctr, q2, zsh, zok, ma,
+            md);
         const int qd = 2 * hr + hc;
         R nt = R(nuy) * dd_ex2(bv[u] * L2E + P2);
         nut[qd * nst + u] = (double)nt;
-        hs[qd] += nt * (sa * isw + bv[u]);
-        hs[4 + qd] += nt * (sd * isw);
+        hs[qd] += nt * (ma + bv[u]);
+        hs[4 + qd] += nt * md;
         hs[8 + qd] += nt;
       }
     }
@@ -1257,27 +1297,20 @@ __device__ __forceinline__ void cell_solve_dist(const DevState& S, const CellDes
   R* Te = T;
   R* Ma = T + nx1 * W;
   R* Md = Ma + nx1 * W;
+  const bool zok = Md + nx1 * W <= Zv;   // Zv (the final Z, own rows) is intact: the quadrant sums' shift
   for (int hc = 0; hc < nhc; ++hc) {
     const int cb = hc * s, ce = min(nx2, cb + s);
     for (int t = gtid; t < nx1 * W; t += gthr) {
       const int r = t / W, ll = t - r * W;
       const R* row = xa_c + r * nx2;
-      const R ctr = R(ll + offc);
-      const R T2 = lse2_1d<R>([&](int m) { return row[cb + m]; }, ce - cb, ctr - R(cb), q2, R(0), false);
-      R sw = 0, sa = 0, sd = 0;
-      for (int c = cb; c < ce; ++c) {
-        const R d = R(c) - ctr;
-        const R w = dd_ex2(row[c] - q2 * d * d - T2);
-        sw += w;
-        sa += w * (av_c[r * nx2 + c] - qR * d * d);
-        const R dt = d + R(D2);
-        sd += w * dt * dt;
-      }
-      const R isw = R(1) / sw;
+      R ma, md;
+      const R T2 = lse_moments<R>(
+          [&](int m) { return row[m]; }, [&](int m, R d) { return av_c[r * nx2 + m] - qR * d * d; },
+          [&](int, R d) { return (d + R(D2)) * (d + R(D2)); }, cb, ce, R(ll + offc), q2, R(0), false, ma, md);
       for (int rk = 0; rk < C; ++rk) {
         *cl.map_shared_rank(Te + t, rk) = T2;
-        *cl.map_shared_rank(Ma + t, rk) = sa * isw;
-        *cl.map_shared_rank(Md + t, rk) = sd * isw;
+        *cl.map_shared_rank(Ma + t, rk) = ma;
+        *cl.map_shared_rank(Md + t, rk) = md;
       }
     }
     csync();
@@ -1287,24 +1320,19 @@ __device__ __forceinline__ void cell_solve_dist(const DevState& S, const CellDes
       const int y = (k0 + kk) * N + l0 + ll;
       const R ctr = R(kk + offr);
       const double nuy = S.nu[y];
+      const R zsh = zok ? Zv[ul] : R(0);   // the final Z: an upper bound of every quadrant's sum
       for (int hr = 0; hr < nhr; ++hr) {
         const int rb = hr * s, re = min(nx1, rb + s);
-        const R P2 = lse2_1d<R>([&](int m) { return Te[(rb + m) * W + ll]; }, re - rb, ctr - R(rb), q2, R(0), false);
-        R sw = 0, sa = 0, sd = 0;
-        for (int r = rb; r < re; ++r) {
-          const R d = R(r) - ctr;
-          const R w = dd_ex2(Te[r * W + ll] - q2 * d * d - P2);
-          sw += w;
-          sa += w * (Ma[r * W + ll] - qR * d * d);
-          const R dt = d + R(D1);
-          sd += w * (dt * dt + Md[r * W + ll]);
-        }
-        const R isw = R(1) / sw;
+        R ma, md;
+        const R P2 = lse_moments<R>(
+            [&](int m) { return Te[m * W + ll]; }, [&](int m, R d) { return Ma[m * W + ll] - qR * d * d; },
+            [&](int m, R d) { return (d + R(D1)) * (d + R(D1)) + Md[m * W + ll]; }, rb, re, ctr, q2, zsh, zok, ma,
+            md);
         const int qd = 2 * hr + hc;
         const R ntv = R(nuy) * dd_ex2(bv[ul] * L2E + P2);
         nut[qd * nst + u] = (double)ntv;
-        hs[qd] += ntv * (sa * isw + bv[ul]);
-        hs[4 + qd] += ntv * (sd * isw);
+        hs[qd] += ntv * (ma + bv[ul]);
+        hs[4 + qd] += ntv * md;
         hs[8 + qd] += ntv;
       }
     }

@@ -245,7 +245,9 @@ __device__ __forceinline__ void block_sum(T (&v)[K], T* scratch) {
 // Two-stage grid reduction (deterministic): each of G blocks writes its K
 // block sums to partials[blockIdx.x * K + k]; k_sum_partials then adds the G
 // rows in block order.  With G = 1 the single block writes the result itself.
-constexpr int kRedBlocks = 2 * 152;
+// G is at most kRedBlocks, a fixed grid (two blocks per SM of GB300's 152 SMs)
+// that sizes the partial buffers; it is not a device query and any SM count works.
+constexpr int kRedBlocks = 304;
 inline int red_blocks(long long n, int threads, const double* partials) {
   if (!partials) return 1;
   long long g = (n + threads - 1) / threads;

@@ -276,7 +276,10 @@ __device__ __forceinline__ void apply_body(const DevState& S, const CellDesc cd,
   const double th = *S.theta, thr = S.thr;
   double* arena = S.arena[*S.cur];
   int nst;
-  const double* nut = cell_nut(S, o, pos, &nst) + (long long)q * nst;
+  // the new marginal of this quadrant; the first pass overwrites it with the mixed
+  // value (nothing reads it after this kernel), which the second pass copies
+  double* nut = cell_nut(S, o, pos, &nst);
+  nut += (long long)q * nst;
   if (tid == 0) {
     ob = S.box[bi];
     bb[0] = 1 << 30; bb[1] = -1; bb[2] = 1 << 30; bb[3] = -1;
@@ -291,6 +294,7 @@ __device__ __forceinline__ void apply_body(const DevState& S, const CellDesc cd,
     double old = (a >= 0 && c >= 0 && a < b.H && c < b.W) ? arena[b.off + (long long)a * b.W + c] : 0.0;
     double v = (1.0 - th) * old + th * nut[u];
     if (v < thr) v = 0.0;
+    nut[u] = v;
     const double dl = v - old;
     if (v > 0.0) {
       lb0 = min(lb0, kk); lb1 = max(lb1, kk);
@@ -331,12 +335,8 @@ __device__ __forceinline__ void apply_body(const DevState& S, const CellDesc cd,
     const int nk0 = nbox[0], nl0 = nbox[1], nH = nbox[2], nW = nbox[3];
     for (int u = tid; u < nH * nW; u += blockDim.x) {
       int a = u / nW, c = u - a * nW;
-      int y1 = nk0 + a, y2 = nl0 + c;
-      int oa = y1 - b.k0, oc = y2 - b.l0;
-      double old = (oa >= 0 && oc >= 0 && oa < b.H && oc < b.W) ? arena[b.off + (long long)oa * b.W + oc] : 0.0;
-      double v = (1.0 - th) * old + th * nut[(y1 - o.k0) * W + (y2 - o.l0)];
-      if (v < thr) v = 0.0;
-      arena[noff + u] = v;
+      const int y1 = nk0 + a, y2 = nl0 + c;
+      arena[noff + u] = nut[(y1 - o.k0) * W + (y2 - o.l0)];
     }
   }
   // P_X on the quadrant's pixels, and the cell's new alpha there
@@ -550,10 +550,11 @@ __global__ void k_log_nu_beta(const double* __restrict__ lognu, const double* __
 //         is the FP64 value computed and compared, so the box is the one of
 //         the FP64 test;
 // mode 1: values on the box (dense over X_i), C_i, H_i, P_Y.
+constexpr int kInitChunk = 128;   // box columns per pass of the dual-initialised fill
 __global__ void __launch_bounds__(256)
 k_init_duals(DevState S, const double* __restrict__ alpha0, const double* __restrict__ beta0,
              double eps0, int mode, const float* __restrict__ gf) {
-  extern __shared__ double tsm[];   // s * N doubles, then s * N floats (mode 0)
+  extern __shared__ double tsm[];   // mode 0: s * N doubles, then s * N floats; mode 1: 3 s kInitChunk doubles
   __shared__ int bb[4];
   __shared__ double red[33 * 2];
   const int i = blockIdx.x, s = S.s, N = S.N, I = i / S.nb, J = i % S.nb;
@@ -625,23 +626,67 @@ k_init_duals(DevState S, const double* __restrict__ alpha0, const double* __rest
       S.box[i] = b;
     }
   } else {
-    BoxRec b = S.box[i];
+    // Separable evaluation on the box (|x - y|^2 splits over the axes), in
+    // column chunks of kInitChunk: per row r of X_i and column l of the chunk
+    //   T1(r, l) = log sum_c exp(alpha0/eps0 + log mu - q (c - l)^2)  (c over the columns of X_i)
+    // with the conditional means of (c - l)^2 and alpha0/eps0 under those terms;
+    // per box point y = (k, l) the sum over the rows r of X_i then gives
+    //   nu_i(y) = nu(y) exp(beta0/eps0) sum_r exp(T1 - q (r - k)^2),
+    //   sum_x c pi = h^2 sum_r w_r ((r - k)^2 + E[(c - l)^2]),  sum_x pi log(pi / mu nu) likewise.
+    // s exponentials per box point instead of s^2.
+    double* T1 = tsm;
+    double* M2 = T1 + s * kInitChunk;
+    double* MA = M2 + s * kInitChunk;
+    const BoxRec b = S.box[i];
     double v[2] = {0.0, 0.0};
-    for (int u = threadIdx.x; u < b.H * b.W; u += blockDim.x) {
-      int k = b.k0 + u / b.W, l = b.l0 + u % b.W, y = k * N + l;
-      double by = beta0[y], nuy = S.nu[y];
-      double acc = 0.0, cacc = 0.0, hacc = 0.0;
-      for (int t = 0; t < s * s; ++t) {
-        int r = r0 + t / s, c = c0 + t % s, x = r * N + c;
-        double cc = S.h * S.h * (double)((r - k) * (r - k) + (c - l) * (c - l));
-        double lr = (alpha0[x] + by - cc) / eps0;
-        double p = exp(lr) * S.mu[x] * nuy;
-        acc += p; cacc += cc * p; hacc += p * lr - p;
+    const double ie0 = 1.0 / eps0;
+    for (int lc = 0; lc < b.W; lc += kInitChunk) {
+      const int wc = min(kInitChunk, b.W - lc);
+      for (int t = threadIdx.x; t < s * wc; t += blockDim.x) {
+        const int r = t / wc, l = b.l0 + lc + t % wc;
+        double mx = -INFINITY;
+        for (int c = 0; c < s; ++c) {
+          const int x = (r0 + r) * N + c0 + c;
+          const double d = c0 + c - l;
+          mx = fmax(mx, alpha0[x] * ie0 + S.logmu[x] - q * d * d);
+        }
+        double a = 0.0, a2 = 0.0, aa = 0.0;
+        for (int c = 0; c < s; ++c) {
+          const int x = (r0 + r) * N + c0 + c;
+          const double d = c0 + c - l;
+          const double w = exp(alpha0[x] * ie0 + S.logmu[x] - q * d * d - mx);
+          a += w; a2 += w * d * d; aa += w * (alpha0[x] * ie0);
+        }
+        T1[r * kInitChunk + t % wc] = mx + log(a);
+        M2[r * kInitChunk + t % wc] = a2 / a;
+        MA[r * kInitChunk + t % wc] = aa / a;
       }
-      double val = acc < S.thr ? 0.0 : acc;
-      arena[b.off + u] = val;
-      if (val != 0.0) atomicAdd(S.PY + y, val);
-      v[0] += cacc; v[1] += hacc;
+      __syncthreads();
+      for (int u = threadIdx.x; u < b.H * wc; u += blockDim.x) {
+        const int kk = u / wc, lj = u % wc;
+        const int k = b.k0 + kk, l = b.l0 + lc + lj, y = k * N + l;
+        double mx = -INFINITY;
+        for (int r = 0; r < s; ++r) {
+          const double d = r0 + r - k;
+          mx = fmax(mx, T1[r * kInitChunk + lj] - q * d * d);
+        }
+        double a = 0.0, ac = 0.0, aa = 0.0;
+        for (int r = 0; r < s; ++r) {
+          const double d = r0 + r - k;
+          const double w = exp(T1[r * kInitChunk + lj] - q * d * d - mx);
+          a += w; ac += w * (d * d + M2[r * kInitChunk + lj]); aa += w * MA[r * kInitChunk + lj];
+        }
+        const double by = beta0[y] * ie0;
+        const double acc = S.nu[y] * exp(by + mx) * a;   // nu_i(y) = sum_x pi(x, y)
+        const double val = acc < S.thr ? 0.0 : acc;
+        arena[b.off + kk * b.W + lc + lj] = val;
+        if (val != 0.0) atomicAdd(S.PY + y, val);
+        const double cc = S.h * S.h * ac / a;   // E[c] under pi(., y)
+        v[0] += cc * acc;
+        // sum_x pi (log(pi / (mu nu)) - 1), log(pi / (mu nu)) = (alpha0 + beta0 - c)/eps0
+        v[1] += acc * (aa / a + by - cc * ie0 - 1.0);
+      }
+      __syncthreads();
     }
     block_sum<2>(v, red);
     if (threadIdx.x == 0) {
@@ -706,7 +751,7 @@ k_cert(DevState S, const double* z, double* beta_out, double* out) {
 
 // ======================================================= host launch wrappers
 cudaError_t launch_decide(const DevState& S, const CellDesc* cells, int begin, int nbatch, cudaStream_t st) {
-  int nblk = 2 * 152;
+  int nblk = kRedBlocks;
   int n = S.N * S.N;
   if (n < nblk * 512) nblk = (n + 511) / 512;
   if (nblk < 1) nblk = 1;
@@ -729,7 +774,7 @@ cudaError_t launch_line_search(const DevState& S, const CellDesc* cells, int beg
 }
 cudaError_t launch_decide_multi(const DevState* states, int ninst, int maxn, int part, int sub, cudaStream_t st) {
   int nblk = (maxn * maxn + 511) / 512;
-  if (nblk > 2 * 152) nblk = 2 * 152;
+  if (nblk > kRedBlocks) nblk = kRedBlocks;
   if (nblk < 1) nblk = 1;
   k_decide_multi<<<dim3(nblk, ninst), 512, 0, st>>>(states, part, sub);
   return cudaGetLastError();
@@ -815,7 +860,9 @@ cudaError_t launch_init_duals_boxes(const DevState& S, const double* alpha0, con
 cudaError_t launch_init_duals_fill(const DevState& S, const double* alpha0, const double* beta0, double eps0,
                                    const double* w, long long* newoff, cudaStream_t st) {
   k_set_offsets<<<(S.nbasic + 255) / 256, 256, 0, st>>>(S, newoff);
-  k_init_duals<<<S.nbasic, 256, 0, st>>>(S, alpha0, beta0, eps0, 1, nullptr);
+  const size_t sm = 3 * sizeof(double) * (size_t)S.s * kInitChunk;
+  cudaFuncSetAttribute(k_init_duals, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max(sm, (size_t)S.s * S.N * (sizeof(double) + sizeof(float))));
+  k_init_duals<<<S.nbasic, 256, sm, st>>>(S, alpha0, beta0, eps0, 1, nullptr);
   k_px_duals<<<(S.N * S.N + 255) / 256, 256, 0, st>>>(S, alpha0, w, eps0);
   return cudaGetLastError();
 }
