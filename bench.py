@@ -47,10 +47,11 @@ sys.path.insert(0, ROOT)
 METRIC = "time to stated primal-dual gap and cell-iters/s vs full Sinkhorn on one GB300"
 UNIT = "cell-iters/s"
 GAP_TARGET = 1e-5
-# dram read + write bytes of one cell-kernel launch from an ncu capture of the
-# current kernel in this configuration (profiles/); None: not captured since
-# the kernel last changed
-CELL_KERNEL_DRAM_BYTES = {}
+# dram read + write bytes of one cell-kernel launch (main grid, one staggered
+# sub-batch) from an ncu capture of the current kernel in this configuration
+# (profiles/cell_solve_lognormal1024.md); a size without an entry: not captured
+# since the kernel last changed (reported as null)
+CELL_KERNEL_DRAM_BYTES = {1024: 53298176 + 8162304}
 
 
 def peaks_file():

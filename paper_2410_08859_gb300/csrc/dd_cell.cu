@@ -63,37 +63,50 @@ __device__ __forceinline__ R lse2_1d(F src, int M, R ctr, R q2, R shift, bool us
   return mx + dd_lg2(acc);
 }
 
-// Epilogue statistics of one target over the sources m in [b, e):
-// with v_m = src(m) - q2 (m - ctr)^2 (log2 units) returns L = log2 sum_m 2^{v_m}
-// and the means m1 = <f1>, m2 = <f2> under the weights 2^{v_m - L}, where
-// f1(m, d), f2(m, d) take the source index and d = m - ctr.  With use_shift,
-// `shift` is an upper bound of L (the full-range log-sum-exp of the same
-// terms): one pass of exponentials against it, and only if that sum leaves
-// [1e-30, 1e30] (the sub-range holds a negligible share) the exact pass
-// against the maximum.  Without a shift the maximum is found first.
-template <typename R, typename F, typename G1, typename G2>
-__device__ __forceinline__ R lse_moments(F src, G1 f1, G2 f2, int b, int e, R ctr, R q2, R shift, bool use_shift,
-                                         R& m1, R& m2) {
-  R sh = shift;
-  if (!use_shift) {
+// One pass of the epilogue statistics against the shift sh: over m in [b, e),
+// with d = m - ctr and w = 2^{src(m) - q2 d^2 - sh}, the sums of w,
+// w (A(m) - qR d^2) and w ((d + D)^2 + B(m)).
+template <typename R, typename F, typename GA, typename GB>
+__device__ __forceinline__ void moments_pass(F src, GA A, GB B, R qR, R D, int b, int e, R ctr, R q2, R sh, R& sw,
+                                             R& sa, R& sd) {
+  sw = sa = sd = R(0);
+  R d = R(b) - ctr;
+  for (int m = b; m < e; ++m, d += R(1)) {
+    const R w = dd_ex2(src(m) - q2 * d * d - sh);
+    sw += w;
+    sa += w * (A(m) - qR * d * d);
+    sd += w * ((d + D) * (d + D) + B(m));
+  }
+}
+
+// Epilogue statistics of one target over the sources m in [b, e): with
+// v_m = src(m) - q2 (m - ctr)^2 (log2 units) returns L = log2 sum_m 2^{v_m} and
+// the means m1 = <A(m) - qR d^2>, m2 = <(d + D)^2 + B(m)> under the weights
+// 2^{v_m - L} (d = m - ctr).  With use_shift, `shift` is an upper bound of L
+// (the full-range log-sum-exp of the same terms): one pass of exponentials
+// against it, and only if that sum leaves [1e-30, 1e30] (the sub-range holds a
+// negligible share) the exact pass against the maximum.  Without a shift the
+// maximum is found first.
+template <typename R, typename F, typename GA, typename GB>
+__device__ __forceinline__ R lse_moments(F src, GA A, GB B, R qR, R D, int b, int e, R ctr, R q2, R shift,
+                                         bool use_shift, R& m1, R& m2) {
+  auto maxpass = [&]() {
     R mx = -dd_inf<R>();
     R d = R(b) - ctr;
     for (int m = b; m < e; ++m, d += R(1)) mx = max(mx, src(m) - q2 * d * d);
-    if (!(mx > -dd_inf<R>())) {
+    return mx;
+  };
+  R sh = shift;
+  if (!use_shift) {
+    sh = maxpass();
+    if (!(sh > -dd_inf<R>())) {
       m1 = m2 = R(0);
-      return mx;
+      return sh;
     }
-    sh = mx;
   }
   for (int pass = 0;; ++pass) {
-    R sw = R(0), sa = R(0), sd = R(0);
-    R d = R(b) - ctr;
-    for (int m = b; m < e; ++m, d += R(1)) {
-      const R w = dd_ex2(src(m) - q2 * d * d - sh);
-      sw += w;
-      sa += w * f1(m, d);
-      sd += w * f2(m, d);
-    }
+    R sw, sa, sd;
+    moments_pass<R>(src, A, B, qR, D, b, e, ctr, q2, sh, sw, sa, sd);
     if (!use_shift || pass == 1 || (sw >= R(1e-30) && sw <= R(1e30))) {
       const R isw = R(1) / sw;
       m1 = sa * isw;
@@ -101,36 +114,32 @@ __device__ __forceinline__ R lse_moments(F src, G1 f1, G2 f2, int b, int e, R ct
       return sh + dd_lg2(sw);
     }
     // the shift was far from L: the exact pass against the maximum
-    R mx = -dd_inf<R>();
-    d = R(b) - ctr;
-    for (int m = b; m < e; ++m, d += R(1)) mx = max(mx, src(m) - q2 * d * d);
-    if (!(mx > -dd_inf<R>())) {
+    sh = maxpass();
+    if (!(sh > -dd_inf<R>())) {
       m1 = m2 = R(0);
-      return mx;
+      return sh;
     }
-    sh = mx;
   }
 }
 
 // Partial sum of 2^{src(m) - q2 (m - ctr)^2 - shift} over m = part, part + P, ...
-// (four independent accumulators to keep several ex2 in flight).
+// (eight independent accumulators to keep several ex2 in flight).
 template <typename R, typename F>
 __device__ __forceinline__ R psum2(F src, int M, R ctr, R q2, R shift, int part, int P) {
-  R a0 = R(0), a1 = R(0), a2 = R(0), a3 = R(0);
+  R a[8] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
   const R dP = R(P);
   R d = R(part) - ctr;
   int m = part;
-  for (; m + 3 * P < M; m += 4 * P) {
-    R v0 = src(m) - q2 * d * d - shift;
-    R d1 = d + dP, d2 = d1 + dP, d3 = d2 + dP;
-    R v1 = src(m + P) - q2 * d1 * d1 - shift;
-    R v2 = src(m + 2 * P) - q2 * d2 * d2 - shift;
-    R v3 = src(m + 3 * P) - q2 * d3 * d3 - shift;
-    a0 += dd_ex2(v0); a1 += dd_ex2(v1); a2 += dd_ex2(v2); a3 += dd_ex2(v3);
-    d = d3 + dP;
+  for (; m + 7 * P < M; m += 8 * P) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const R dk = d + R(k) * dP;
+      a[k] += dd_ex2(src(m + k * P) - q2 * dk * dk - shift);
+    }
+    d += R(8) * dP;
   }
-  for (; m < M; m += P, d += dP) a0 += dd_ex2(src(m) - q2 * d * d - shift);
-  return (a0 + a1) + (a2 + a3);
+  for (; m < M; m += P, d += dP) a[0] += dd_ex2(src(m) - q2 * d * d - shift);
+  return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
 }
 
 template <typename R, typename F>
@@ -689,9 +698,9 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
       int r = t / W, ll = t - r * W;
       const R* row = xa_c + r * nx2;
       R ma, md;
-      const R T2 = lse_moments<R>(
-          [&](int m) { return row[m]; }, [&](int m, R d) { return av_c[r * nx2 + m] - qR * d * d; },
-          [&](int, R d) { return (d + R(D2)) * (d + R(D2)); }, cb, ce, R(ll + offc), q2, R(0), false, ma, md);
+      const R T2 = lse_moments<R>([&](int m) { return row[m]; }, [&](int m) { return av_c[r * nx2 + m]; },
+                                  [&](int) { return R(0); }, qR, R(D2), cb, ce, R(ll + offc), q2, R(0), false, ma,
+                                  md);
       Te[t] = T2;
       Ma[t] = ma;
       Md[t] = md;
@@ -709,9 +718,8 @@ __device__ __forceinline__ void cell_solve_body(const DevState& S, const CellDes
         const int rb = hr * s, re = min(nx1, rb + s);
         R ma, md;
         const R P2 = lse_moments<R>(
-            [&](int m) { return Te[m * W + ll]; }, [&](int m, R d) { return Ma[m * W + ll] - qR * d * d; },
-            [&](int m, R d) { return (d + R(D1)) * (d + R(D1)) + Md[m * W + ll]; }, rb, re, ctr, q2, zsh, zok, ma,
-            md);
+            [&](int m) { return Te[m * W + ll]; }, [&](int m) { return Ma[m * W + ll]; },
+            [&](int m) { return Md[m * W + ll]; }, qR, R(D1), rb, re, ctr, q2, zsh, zok, ma, md);
         const int qd = 2 * hr + hc;
         R nt = R(nuy) * dd_ex2(bv[u] * L2E + P2);
         nut[qd * nst + u] = (double)nt;
@@ -1304,9 +1312,9 @@ __device__ __forceinline__ void cell_solve_dist(const DevState& S, const CellDes
       const int r = t / W, ll = t - r * W;
       const R* row = xa_c + r * nx2;
       R ma, md;
-      const R T2 = lse_moments<R>(
-          [&](int m) { return row[m]; }, [&](int m, R d) { return av_c[r * nx2 + m] - qR * d * d; },
-          [&](int, R d) { return (d + R(D2)) * (d + R(D2)); }, cb, ce, R(ll + offc), q2, R(0), false, ma, md);
+      const R T2 = lse_moments<R>([&](int m) { return row[m]; }, [&](int m) { return av_c[r * nx2 + m]; },
+                                  [&](int) { return R(0); }, qR, R(D2), cb, ce, R(ll + offc), q2, R(0), false, ma,
+                                  md);
       for (int rk = 0; rk < C; ++rk) {
         *cl.map_shared_rank(Te + t, rk) = T2;
         *cl.map_shared_rank(Ma + t, rk) = ma;
@@ -1325,9 +1333,8 @@ __device__ __forceinline__ void cell_solve_dist(const DevState& S, const CellDes
         const int rb = hr * s, re = min(nx1, rb + s);
         R ma, md;
         const R P2 = lse_moments<R>(
-            [&](int m) { return Te[m * W + ll]; }, [&](int m, R d) { return Ma[m * W + ll] - qR * d * d; },
-            [&](int m, R d) { return (d + R(D1)) * (d + R(D1)) + Md[m * W + ll]; }, rb, re, ctr, q2, zsh, zok, ma,
-            md);
+            [&](int m) { return Te[m * W + ll]; }, [&](int m) { return Ma[m * W + ll]; },
+            [&](int m) { return Md[m * W + ll]; }, qR, R(D1), rb, re, ctr, q2, zsh, zok, ma, md);
         const int qd = 2 * hr + hc;
         const R ntv = R(nuy) * dd_ex2(bv[ul] * L2E + P2);
         nut[qd * nst + u] = (double)ntv;

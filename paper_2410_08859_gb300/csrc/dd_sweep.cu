@@ -551,10 +551,11 @@ __global__ void k_log_nu_beta(const double* __restrict__ lognu, const double* __
 //         the FP64 test;
 // mode 1: values on the box (dense over X_i), C_i, H_i, P_Y.
 constexpr int kInitChunk = 128;   // box columns per pass of the dual-initialised fill
-__global__ void __launch_bounds__(256)
+constexpr int kInitBand = 2048;   // band pixels listed per basic cell by the box test
+__global__ void __launch_bounds__(1024)
 k_init_duals(DevState S, const double* __restrict__ alpha0, const double* __restrict__ beta0,
              double eps0, int mode, const float* __restrict__ gf) {
-  extern __shared__ double tsm[];   // mode 0: s * N doubles, then s * N floats; mode 1: 3 s kInitChunk doubles
+  extern __shared__ double tsm[];   // mode 0: see init_box_smem; mode 1: 3 s kInitChunk doubles
   __shared__ int bb[4];
   __shared__ double red[33 * 2];
   const int i = blockIdx.x, s = S.s, N = S.N, I = i / S.nb, J = i % S.nb;
@@ -562,57 +563,124 @@ k_init_duals(DevState S, const double* __restrict__ alpha0, const double* __rest
   const double q = S.h * S.h / eps0;
   double* arena = S.arena[*S.cur];
   if (mode == 0) {
+    // shared: T(r, l) in double (only the columns flagged below) | T in float | X values in
+    // float | column flags | list of the pixels in the band of the float test
     float* tsmf = reinterpret_cast<float*>(tsm + s * N);
-    // T(r, l) = log sum_{c in cols(X_i)} exp(alpha0/eps0 + log mu - q (c - l)^2), r in rows(X_i)
-    for (int t = threadIdx.x; t < s * N; t += blockDim.x) {
-      int r = t / N, l = t % N;
-      double mx = -INFINITY;
-      for (int c = 0; c < s; ++c) {
-        int x = (r0 + r) * N + c0 + c;
-        double d = c0 + c - l;
-        mx = fmax(mx, alpha0[x] / eps0 + S.logmu[x] - q * d * d);
-      }
-      double acc = 0.0;
-      for (int c = 0; c < s; ++c) {
-        int x = (r0 + r) * N + c0 + c;
-        double d = c0 + c - l;
-        acc += exp(alpha0[x] / eps0 + S.logmu[x] - q * d * d - mx);
-      }
-      tsm[t] = mx + log(acc);
-      tsmf[t] = (float)tsm[t];
+    float* xvf = tsmf + s * N;
+    unsigned char* colflag = reinterpret_cast<unsigned char*>(xvf + s * s);
+    int* band = reinterpret_cast<int*>(colflag + ((N + 15) & ~15));
+    __shared__ int nband;
+    const double ie0 = 1.0 / eps0;
+    const float qf = (float)q, L2E = (float)DD_LOG2E, LN2 = (float)DD_LN2;
+    for (int t = threadIdx.x; t < s * s; t += blockDim.x) {
+      const int x = (r0 + t / s) * N + c0 + t % s;
+      xvf[t] = (float)(alpha0[x] * ie0 + S.logmu[x]);
     }
-    if (threadIdx.x == 0) { bb[0] = 1 << 30; bb[1] = -1; bb[2] = 1 << 30; bb[3] = -1; }
+    for (int l = threadIdx.x; l < N; l += blockDim.x) colflag[l] = 0;
+    if (threadIdx.x == 0) { nband = 0; bb[0] = 1 << 30; bb[1] = -1; bb[2] = 1 << 30; bb[3] = -1; }
+    __syncthreads();
+    // float T(r, l) = log sum_{c in cols(X_i)} exp(alpha0/eps0 + log mu - q (c - l)^2)
+    for (int t = threadIdx.x; t < s * N; t += blockDim.x) {
+      const int r = t / N, l = t - (t / N) * N;
+      float mx = -INFINITY;
+      for (int c = 0; c < s; ++c) {
+        const float d = (float)(c0 + c - l);
+        mx = fmaxf(mx, xvf[r * s + c] - qf * d * d);
+      }
+      float acc = 0.0f;
+      for (int c = 0; c < s; ++c) {
+        const float d = (float)(c0 + c - l);
+        acc += dd_ex2((xvf[r * s + c] - qf * d * d - mx) * L2E);
+      }
+      tsmf[t] = mx + dd_lg2(acc) * LN2;
+    }
     __syncthreads();
     int lb[4] = {1 << 30, -1, 1 << 30, -1};
     const double lthr = log(S.thr);
-    const float lthrf = (float)lthr, qf = (float)q, L2E = (float)DD_LOG2E;
+    const float lthrf = (float)lthr;
+    auto keep = [&](int k, int l) {
+      lb[0] = min(lb[0], k); lb[1] = max(lb[1], k); lb[2] = min(lb[2], l); lb[3] = max(lb[3], l);
+    };
+    // the float test of every pixel; `band` collects those it cannot decide
     for (int y = threadIdx.x; y < N * N; y += blockDim.x) {
-      int k = y / N, l = y % N;
-      // float value and its error bound (a few ulps of the magnitudes that cancel)
+      const int k = y / N, l = y - (y / N) * N;
       float mxf = -INFINITY, big = fabsf(gf[y]);
       for (int r = 0; r < s; ++r) {
         const float d = (float)(r0 + r - k), v = tsmf[r * N + l];
         mxf = fmaxf(mxf, v - qf * d * d);
         big = fmaxf(big, fabsf(v) + qf * d * d);
       }
+      // float value and its error bound (a few ulps of the magnitudes that cancel; the
+      // float X values and T add ~1e-7 of the same magnitudes)
+      const float band_w = 0.5f + 1e-5f * big;
+      const float lo = gf[y] + mxf;   // log nu_i(y) lies in [lo, lo + log s]
+      if (lo + dd_lg2((float)s) * LN2 < lthrf - band_w) continue;   // clearly below the threshold
       float accf = 0.0f;
       for (int r = 0; r < s; ++r) {
         const float d = (float)(r0 + r - k);
         accf += dd_ex2((tsmf[r * N + l] - qf * d * d - mxf) * L2E);
       }
-      const float lvf = gf[y] + mxf + dd_lg2(accf) * (float)DD_LN2;
-      const float band = 0.5f + 1e-5f * big;
-      bool in = lvf >= lthrf + band;
-      if (!in && lvf > lthrf - band) {
-        double mx = -INFINITY;
-        for (int r = 0; r < s; ++r) { double d = r0 + r - k; mx = fmax(mx, tsm[r * N + l] - q * d * d); }
-        double acc = 0.0;
-        for (int r = 0; r < s; ++r) { double d = r0 + r - k; acc += exp(tsm[r * N + l] - q * d * d - mx); }
-        const double lv = S.lognu[y] + beta0[y] / eps0 + mx + log(acc);
-        in = lv >= lthr;
+      const float lvf = lo + dd_lg2(accf) * LN2;
+      if (lvf >= lthrf + band_w) {
+        keep(k, l);
+      } else if (lvf > lthrf - band_w) {
+        colflag[l] = 1;
+        const int j = atomicAdd(&nband, 1);
+        if (j < kInitBand) band[j] = y;
       }
-      if (in) {
-        lb[0] = min(lb[0], k); lb[1] = max(lb[1], k); lb[2] = min(lb[2], l); lb[3] = max(lb[3], l);
+    }
+    __syncthreads();
+    // double T on the flagged columns
+    for (int t = threadIdx.x; t < s * N; t += blockDim.x) {
+      const int r = t / N, l = t - (t / N) * N;
+      if (!colflag[l]) continue;
+      double mx = -INFINITY;
+      for (int c = 0; c < s; ++c) {
+        const int x = (r0 + r) * N + c0 + c;
+        const double d = c0 + c - l;
+        mx = fmax(mx, alpha0[x] * ie0 + S.logmu[x] - q * d * d);
+      }
+      double acc = 0.0;
+      for (int c = 0; c < s; ++c) {
+        const int x = (r0 + r) * N + c0 + c;
+        const double d = c0 + c - l;
+        acc += exp(alpha0[x] * ie0 + S.logmu[x] - q * d * d - mx);
+      }
+      tsm[t] = mx + log(acc);
+    }
+    __syncthreads();
+    // the double test of the band pixels (rescanning all pixels if the list overflowed)
+    auto dtest = [&](int y) {
+      const int k = y / N, l = y - (y / N) * N;
+      double mx = -INFINITY;
+      for (int r = 0; r < s; ++r) { const double d = r0 + r - k; mx = fmax(mx, tsm[r * N + l] - q * d * d); }
+      double acc = 0.0;
+      for (int r = 0; r < s; ++r) { const double d = r0 + r - k; acc += exp(tsm[r * N + l] - q * d * d - mx); }
+      if (S.lognu[y] + beta0[y] * ie0 + mx + log(acc) >= lthr) keep(k, l);
+    };
+    const int nb = nband;
+    if (nb <= kInitBand) {
+      for (int j = threadIdx.x; j < nb; j += blockDim.x) dtest(band[j]);
+    } else {
+      for (int y = threadIdx.x; y < N * N; y += blockDim.x) {
+        const int k = y / N, l = y - (y / N) * N;
+        if (!colflag[l]) continue;
+        float mxf = -INFINITY, big = fabsf(gf[y]);
+        for (int r = 0; r < s; ++r) {
+          const float d = (float)(r0 + r - k), v = tsmf[r * N + l];
+          mxf = fmaxf(mxf, v - qf * d * d);
+          big = fmaxf(big, fabsf(v) + qf * d * d);
+        }
+        const float band_w = 0.5f + 1e-5f * big;
+        const float lo = gf[y] + mxf;
+        if (lo + dd_lg2((float)s) * LN2 < lthrf - band_w) continue;
+        float accf = 0.0f;
+        for (int r = 0; r < s; ++r) {
+          const float d = (float)(r0 + r - k);
+          accf += dd_ex2((tsmf[r * N + l] - qf * d * d - mxf) * L2E);
+        }
+        const float lvf = lo + dd_lg2(accf) * LN2;
+        if (lvf < lthrf + band_w && lvf > lthrf - band_w) dtest(y);
       }
     }
     lb[0] = warp_min(lb[0]); lb[1] = warp_max(lb[1]); lb[2] = warp_min(lb[2]); lb[3] = warp_max(lb[3]);
@@ -844,6 +912,11 @@ cudaError_t launch_init_product_fill(const DevState& S, double* nu_mom, double* 
   return cudaGetLastError();
 }
 // gscratch: N*N floats of device scratch
+// dynamic shared memory of the box test (mode 0 of k_init_duals)
+static size_t init_box_smem(int s, int N) {
+  return (size_t)s * N * (sizeof(double) + sizeof(float)) + (size_t)s * s * sizeof(float) + ((N + 15) & ~15) +
+         kInitBand * sizeof(int);
+}
 cudaError_t launch_init_duals_boxes(const DevState& S, const double* alpha0, const double* beta0, double eps0,
                                     double* nu_mom, double* mumass, long long* newoff, float* gscratch,
                                     cudaStream_t st) {
@@ -851,9 +924,9 @@ cudaError_t launch_init_duals_boxes(const DevState& S, const double* alpha0, con
   k_basic_masses<<<S.nbasic, 256, 0, st>>>(S, nu_mom, mumass);
   const int n = S.N * S.N;
   k_log_nu_beta<<<(n + 255) / 256, 256, 0, st>>>(S.lognu, beta0, eps0, n, gscratch);
-  size_t sm = (size_t)S.s * S.N * (sizeof(double) + sizeof(float));
+  const size_t sm = init_box_smem(S.s, S.N);
   cudaFuncSetAttribute(k_init_duals, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_init_duals<<<S.nbasic, 256, sm, st>>>(S, alpha0, beta0, eps0, 0, gscratch);
+  k_init_duals<<<S.nbasic, 1024, sm, st>>>(S, alpha0, beta0, eps0, 0, gscratch);
   k_scan_boxes<<<1, 1024, 0, st>>>(S, newoff);
   return cudaGetLastError();
 }
@@ -861,7 +934,7 @@ cudaError_t launch_init_duals_fill(const DevState& S, const double* alpha0, cons
                                    const double* w, long long* newoff, cudaStream_t st) {
   k_set_offsets<<<(S.nbasic + 255) / 256, 256, 0, st>>>(S, newoff);
   const size_t sm = 3 * sizeof(double) * (size_t)S.s * kInitChunk;
-  cudaFuncSetAttribute(k_init_duals, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max(sm, (size_t)S.s * S.N * (sizeof(double) + sizeof(float))));
+  cudaFuncSetAttribute(k_init_duals, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max(sm, init_box_smem(S.s, S.N)));
   k_init_duals<<<S.nbasic, 256, sm, st>>>(S, alpha0, beta0, eps0, 1, nullptr);
   k_px_duals<<<(S.N * S.N + 255) / 256, 256, 0, st>>>(S, alpha0, w, eps0);
   return cudaGetLastError();

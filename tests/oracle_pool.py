@@ -55,9 +55,9 @@ def _trajectory(args):
 
 def mixture_trajectories(specs, sweeps):
     """Oracle runs (pi0 = mu x nu, staggered, default tolerances) of independent
-    problems (N, s, seed, eps, lam), one worker process each: per problem the
-    decision log and the state after every sweep."""
-    jobs = [(N, s, seed, eps, lam, sweeps) for N, s, eps, lam, seed in specs]
+    problems (N, s, eps, lam, seed), sweeps[j] sweeps of problem j, one worker
+    process each: per problem the decision log and the state after every sweep."""
+    jobs = [(N, s, seed, eps, lam, k) for (N, s, eps, lam, seed), k in zip(specs, sweeps)]
     ctx = mp.get_context("spawn")
     with ctx.Pool(min(len(jobs), max(1, os.cpu_count() or 1))) as pool:
         return pool.map(_trajectory, jobs, chunksize=1)

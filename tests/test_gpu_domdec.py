@@ -498,11 +498,14 @@ def test_reset_reuses_the_handle(dd, with_duals):
 def test_batch_instances_match_their_oracle_runs(dd):
     """Many-instance batching against the oracle: four different problems
     (64 x 64 with s = 8 and lam = 1; 32 x 32, lam = 5; the ragged 24 x 24 with
-    s = 3; 16 x 16) swept together in FP64; after every sweep each instance
-    has its own oracle run's decisions, cell iteration counts and state."""
+    s = 3; 16 x 16) swept together in FP64 for two sweeps; after every sweep
+    each instance has its own oracle run's decisions, cell iteration counts and
+    state (the 64 x 64 instance after the first)."""
     specs = [(64, 8, (2 / 64) ** 2, 1.0, 1030), (32, 4, (1 / 32) ** 2, 5.0, 1031),
              (24, 3, (1 / 24) ** 2, 0.5, 1032), (16, 2, (2 / 16) ** 2, 1.0, 1033)]
-    trajs = oracle_pool.mixture_trajectories(specs, 2)   # the oracle runs, one process per problem
+    # the oracle runs, one process per problem; the 64 x 64 one (dense 256 x 4096 cell
+    # problems from pi0 = mu x nu, minutes of NumPy per sweep) for the first sweep only
+    trajs = oracle_pool.mixture_trajectories(specs, [1, 2, 2, 2])
     hs = []
     for N, s, eps, lam, seed in specs:
         mu, nu = inputs.mixture_small(N=N, seed=seed)
@@ -514,6 +517,8 @@ def test_batch_instances_match_their_oracle_runs(dd):
         B.iterate(1)
         assert B.sync() in (0, 1)
         for j, g in enumerate(hs):
+            if k >= len(trajs[j]):
+                continue
             log, st = trajs[j][k]
             dec = g.decisions()
             assert len(dec) == nrec[j] + len(log)
