@@ -149,6 +149,10 @@ void domdec_default_params(domdec_params* p);
  *   alpha0, beta0 != NULL    : pi0 = exp((alpha0 (+) beta0 - c)/eps_init) mu x nu,
  *                             e.g. the duals of a global Sinkhorn warm start
  *                             (Section 5.3, "Sinkhorn warm start"); N*N doubles each.
+ *                             The box test of this plan keeps s*N doubles and
+ *                             s*N floats per basic cell in shared memory
+ *                             (about 12 s N bytes: N <= 1024 at s = 16 on GB300's
+ *                             227 KB); larger s*N returns DOMDEC_ECUDA.
  * `stream` is a cudaStream_t (NULL = legacy default stream); all later work of
  * the handle is enqueued there.  Synchronises.  *out is NULL on failure. */
 int domdec_init(domdec_t* out, const double* mu, const double* nu, int N,
