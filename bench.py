@@ -35,7 +35,7 @@ import subprocess
 import sys
 import time
 
-# the CPU baseline (the FP64 oracle) is reported on one thread: keep BLAS to one
+# every FP64 oracle process of the CPU baseline runs single-threaded: keep BLAS to one thread
 for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_v, "1")
 
