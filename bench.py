@@ -675,7 +675,9 @@ def main():
     roofline = roofline_of(d, pk, N, peaks_meas)
 
     extras, cpu, e2e = {}, None, None
-    want = set() if args.no_extras else set(args.extras.split(",")) if args.extras != "all" else \
+    # the other configurations, e2e and the CPU baseline at N = 1 only (under torchrun the
+    # other ranks' GPUs would wait meanwhile)
+    want = set() if args.no_extras or world > 1 else set(args.extras.split(",")) if args.extras != "all" else \
         {"configs", "ttg", "mix32", "batch64", "grad512", "fp32fp64", "e2e", "cpu"}
     if "e2e" in want:
         e2e = e2e_reset(dd, torch, mu, nu, a0, b0, spec, lam)
