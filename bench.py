@@ -520,7 +520,7 @@ def e2e_reset(dd, torch, mu, nu, a0, b0, spec, lam, steps=3, sweeps=8):
         its += g.stats()["cell_iters"]
     te = time.perf_counter() - t0
     g.close()
-    return {"value": its / te, "unit": UNIT, "h2d_bytes_per_step": 4 * N * N * 8,
+    return {"value": its / te, "unit": UNIT, "cell_iters": its, "seconds": te, "h2d_bytes_per_step": 4 * N * N * 8,
             "d2h_bytes_per_step": 2 * N * N * 8 + 6 * 8,
             "step": f"domdec_reset from pinned host mu, nu, alpha0, beta0 + {sweeps} sweeps + score + "
                     "P_X, P_Y to pinned host memory, one reused handle"}
@@ -667,6 +667,13 @@ def main():
     # kernels of the timed region: per sweep one ordering kernel, per sub-batch the cell solve,
     # decision and mixing kernels, three compaction kernels (one timed class)
     launches = int(d["kn"][0] + d["kn"][1] + d["kn"][2] + 4 * d["kn"][3])
+    # end to end through the C ABI with host buffers, on every rank: summed work over the
+    # slowest rank's time, like the device figure
+    e2e = None
+    if not args.no_extras and (args.extras == "all" or "e2e" in args.extras.split(",")):
+        e2e = e2e_reset(dd, torch, mu, nu, a0, b0, spec, lam)
+        its_e, ms_e = aggregate_ranks(float(e2e["cell_iters"]), 1000.0 * e2e["seconds"], world, "cuda")
+        e2e.update(value=its_e / (ms_e / 1000.0), cell_iters=int(its_e), seconds=ms_e / 1000.0)
     if rank != 0:
         if world > 1:
             dist.barrier()
@@ -674,13 +681,11 @@ def main():
         return
     roofline = roofline_of(d, pk, N, peaks_meas)
 
-    extras, cpu, e2e = {}, None, None
-    # the other configurations, e2e and the CPU baseline at N = 1 only (under torchrun the
-    # other ranks' GPUs would wait meanwhile)
+    extras, cpu = {}, None
+    # the other configurations and the CPU baseline at N = 1 only (under torchrun the other
+    # ranks' GPUs would wait meanwhile)
     want = set() if args.no_extras or world > 1 else set(args.extras.split(",")) if args.extras != "all" else \
-        {"configs", "ttg", "mix32", "batch64", "grad512", "fp32fp64", "e2e", "cpu"}
-    if "e2e" in want:
-        e2e = e2e_reset(dd, torch, mu, nu, a0, b0, spec, lam)
+        {"configs", "ttg", "mix32", "batch64", "grad512", "fp32fp64", "cpu"}
     configs = {}
     if "configs" in want:
         configs["blobs256"] = {f"lam={lm:g}": sweep_config(dd, torch, "blobs256", lm, args.steps, args.warmup,
